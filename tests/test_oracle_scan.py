@@ -1,0 +1,165 @@
+"""Pins for the oracle's scan (Sec. 5) -- CPU only."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from tests._pins import assert_close, fd_vjp
+
+RNG = np.random.default_rng(777)
+
+
+def test_add_scan_is_cumsum_and_adjoint_is_suffix_sum():
+    # Sec. 5.3.1: the adjoint of a +-scan is the reversed +-scan of the reversed ybar.
+    x = RNG.uniform(-1, 1, 500)
+    yb = RNG.standard_normal(500)
+    assert_close(oracle.scan_fwd("add", x), np.cumsum(x), rtol=1e-12, atol=1e-12)
+    assert_close(oracle.scan_vjp("add", x, yb), np.cumsum(yb[::-1])[::-1], rtol=1e-12, atol=1e-12)
+    # all-ones adjoint: n - i exactly
+    n = 1000
+    xb = oracle.scan_vjp("add", np.zeros(n), np.ones(n))
+    assert np.array_equal(xb, n - np.arange(n, dtype=np.float64))
+
+
+def test_mul_scan_is_cumprod():
+    x = RNG.uniform(0.9, 1.1, 400)
+    x[[17, 200]] = 0.0
+    assert_close(oracle.scan_fwd("mul", x), np.cumprod(x), rtol=1e-12, atol=0)
+
+
+def test_mul_scan_adjoint_brute_force():
+    # xbar_i = sum_{k >= i} ybar_k * prod_{j <= k, j != i} x_j
+    n = 30
+    for zeros in ([], [5], [5, 9], [0], [n - 1]):
+        x = RNG.uniform(0.5, 1.5, n)
+        x[zeros] = 0.0
+        yb = RNG.standard_normal(n)
+        brute = np.zeros(n)
+        for i in range(n):
+            for k in range(i, n):
+                brute[i] += yb[k] * np.prod(np.delete(x[:k + 1], i))
+        assert_close(oracle.scan_vjp("mul", x, yb), brute, rtol=1e-11, atol=1e-13)
+
+
+def lin_scan_textbook(bc):
+    out = np.zeros_like(bc)
+    Y, C = 0.0, 1.0
+    for i, (b, c) in enumerate(bc):
+        Y = c * Y + b
+        C = c * C
+        out[i] = (Y, C)
+    return out
+
+
+def test_lin_scan_is_the_textbook_recurrence():
+    bc = np.stack([RNG.standard_normal(300), RNG.uniform(0.95, 1.05, 300)], 1)
+    assert_close(oracle.scan_fwd("lin", bc), lin_scan_textbook(bc), rtol=1e-12, atol=1e-12)
+
+
+def test_lin_with_unit_coefficients_is_a_plus_scan():
+    b = RNG.standard_normal(200)
+    bc = np.stack([b, np.ones(200)], 1)
+    yb = np.stack([RNG.standard_normal(200), np.zeros(200)], 1)
+    assert_close(oracle.scan_fwd("lin", bc)[:, 0], np.cumsum(b), rtol=1e-12, atol=1e-12)
+    assert_close(oracle.scan_vjp("lin", bc, yb)[:, 0], oracle.scan_vjp("add", b, yb[:, 0]),
+                 rtol=1e-12, atol=1e-12)
+
+
+def test_lin_adjoint_textbook_recurrence():
+    # Textbook adjoint of Y_i = c_i Y_{i-1} + b_i, C_i = c_i C_{i-1}:
+    #   lam_i = ybar_i + c_{i+1} lam_{i+1}   (both components)
+    #   bbar_i = lam_i.Y,  cbar_i = lam_i.Y * Y_{i-1} + lam_i.C * C_{i-1}, (Y_{-1}, C_{-1}) = (0, 1)
+    n = 100
+    bc = np.stack([RNG.standard_normal(n), RNG.uniform(0.9, 1.1, n)], 1)
+    yb = RNG.standard_normal((n, 2))
+    Ys = lin_scan_textbook(bc)
+    lam = np.zeros((n, 2))
+    for i in range(n - 1, -1, -1):
+        lam[i] = yb[i] + (bc[i + 1, 1] * lam[i + 1] if i + 1 < n else 0)
+    prev = np.vstack([[0.0, 1.0], Ys[:-1]])
+    expect = np.stack([lam[:, 0], lam[:, 0] * prev[:, 0] + lam[:, 1] * prev[:, 1]], 1)
+    assert_close(oracle.scan_vjp("lin", bc, yb), expect, rtol=1e-11, atol=1e-12)
+
+
+def test_mm2_scan_is_the_running_matrix_product():
+    m = RNG.uniform(-1, 1, (40, 4))
+    acc = np.eye(2)
+    ref = []
+    for a in m:
+        acc = acc @ a.reshape(2, 2)
+        ref.append(acc.reshape(-1))
+    assert_close(oracle.scan_fwd("mm2", m), np.array(ref), rtol=1e-12, atol=1e-15)
+
+
+def lin_as_mm2(bc):
+    # M_i = [[c_i, 0], [b_i, 1]]: P_i = M_0 ... M_i = [[C_i, 0], [Y_i, 1]]
+    b, c = bc[:, 0], bc[:, 1]
+    z, o = np.zeros_like(b), np.ones_like(b)
+    return np.stack([c, z, b, o], 1)
+
+
+def test_mm2_crosschecks_lin_forward_and_adjoint():
+    n = 80
+    bc = np.stack([RNG.standard_normal(n), RNG.uniform(0.9, 1.1, n)], 1)
+    P = oracle.scan_fwd("mm2", lin_as_mm2(bc))
+    L = oracle.scan_fwd("lin", bc)
+    assert_close(P[:, 2], L[:, 0], rtol=1e-12, atol=1e-12)
+    assert_close(P[:, 0], L[:, 1], rtol=1e-12, atol=1e-12)
+    assert np.all(P[:, 1] == 0) and np.all(P[:, 3] == 1)
+    # adjoint: lin outputs (Y, C) are P[1][0] and P[0][0]; lin inputs (b, c) are M[1][0] and M[0][0].
+    yb = RNG.standard_normal((n, 2))
+    Pb = np.zeros((n, 4))
+    Pb[:, 2] = yb[:, 0]
+    Pb[:, 0] = yb[:, 1]
+    Mb = oracle.scan_vjp("mm2", lin_as_mm2(bc), Pb)
+    Lb = oracle.scan_vjp("lin", bc, yb)
+    assert_close(Mb[:, 2], Lb[:, 0], rtol=1e-11, atol=1e-12)
+    assert_close(Mb[:, 0], Lb[:, 1], rtol=1e-11, atol=1e-12)
+
+
+def test_mm2_diagonal_is_two_mul_scans():
+    n = 60
+    a, d = RNG.uniform(0.5, 1.5, n), RNG.uniform(0.5, 1.5, n)
+    z = np.zeros(n)
+    m = np.stack([a, z, z, d], 1)
+    yb = RNG.standard_normal((n, 4))
+    P = oracle.scan_fwd("mm2", m)
+    assert_close(P[:, 0], np.cumprod(a), rtol=1e-12)
+    assert_close(P[:, 3], np.cumprod(d), rtol=1e-12)
+    Mb = oracle.scan_vjp("mm2", m, yb)
+    assert_close(Mb[:, 0], oracle.scan_vjp("mul", a, yb[:, 0]), rtol=1e-11, atol=1e-12)
+    assert_close(Mb[:, 3], oracle.scan_vjp("mul", d, yb[:, 3]), rtol=1e-11, atol=1e-12)
+
+
+def test_mm2_scan_last_equals_reduce():
+    m = RNG.uniform(-1, 1, (33, 4))
+    assert_close(oracle.scan_fwd("mm2", m)[-1], oracle.reduce_fwd("mm2", m), rtol=0, atol=0)
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4)])
+def test_scan_vjp_finite_differences(op, d):
+    n = 20
+    shape = (n,) if d == 1 else (n, d)
+    x = RNG.uniform(0.6, 1.3, shape)
+    yb = RNG.standard_normal(shape)
+    assert_close(oracle.scan_vjp(op, x, yb), fd_vjp(lambda z: oracle.scan_fwd(op, z), x, yb),
+                 rtol=1e-6, atol=1e-7)
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4)])
+def test_scan_dot_product(op, d):
+    n = 64
+    shape = (n,) if d == 1 else (n, d)
+    x = RNG.uniform(0.6, 1.3, shape)
+    v = RNG.standard_normal(shape)
+    u = RNG.standard_normal(shape)
+    jv = oracle.scan_jvp(op, x, v)
+    jtu = oracle.scan_vjp(op, x, u)
+    assert_close(np.sum(jv * u), np.sum(v * jtu), rtol=1e-10, atol=1e-10)
+
+
+def test_scan_empty_and_single():
+    assert oracle.scan_fwd("add", []).shape == (0,)
+    assert_close(oracle.scan_vjp("mul", [3.0], [2.0]), [2.0])
+    assert_close(oracle.scan_vjp("mm2", np.ones((1, 4)), [[1, 2, 3, 4]]), [[1, 2, 3, 4]])
