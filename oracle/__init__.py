@@ -60,6 +60,7 @@ def _load():
                 "oracle_reduce_mul_lifted": [i64, p, p, p],
                 "oracle_scan_fwd": [i32, i64, p, p],
                 "oracle_scan_vjp": [i32, i64, p, p, p],
+                "oracle_scan_vjp_rbar": [i32, i64, p, p, p, p],
                 "oracle_scan_jvp": [i32, i64, p, p, p],
                 "oracle_hist_fwd": [i32, i64, i64, p, p, p, p, p],
                 "oracle_hist_vjp": [i32, i64, i64, p, p, p, p, p, p],
@@ -157,6 +158,18 @@ def scan_vjp(op, x, ybar):
     xb = np.zeros(_shape(n, d))
     _load().oracle_scan_vjp(OPS[op], n, _p(x), _p(yb), _p(xb))
     return xb
+
+
+def scan_vjp_rbar(op, x, ybar):
+    """Returns (xbar, rbar): rbar[i] is the adjoint of the scan result y[i] (Sec. 5.1's rs-bar)."""
+    d = ARITY[op]
+    x = _f64(x, d)
+    n = x.shape[0]
+    yb = _f64(ybar, d)
+    xb = np.zeros(_shape(n, d))
+    rb = np.zeros(_shape(n, d))
+    _load().oracle_scan_vjp_rbar(OPS[op], n, _p(x), _p(yb), _p(xb), _p(rb))
+    return xb, rb
 
 
 def scan_jvp(op, x, xdot):

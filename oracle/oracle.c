@@ -290,9 +290,11 @@ void oracle_scan_fwd(int op, int64_t n, const double *x, double *y) {
  *   for i = n-1 .. 1:  rb[i-1] += d(rs[i-1] (.) as[i])/d rs[i-1] * rb[i]
  *                      ab[i]    = d(rs[i-1] (.) as[i])/d as[i]   * rb[i]
  *   ab[0] = rb[0]
- * (MIN/MAX are not scan operators here.)
+ * (MIN/MAX are not scan operators here.)  rbar, when not NULL, receives the
+ * final rb: the adjoint of each scan result rs[i] (lambda_i).
  */
-void oracle_scan_vjp(int op, int64_t n, const double *x, const double *ybar, double *xbar) {
+void oracle_scan_vjp_rbar(int op, int64_t n, const double *x, const double *ybar, double *xbar,
+                          double *rbar) {
     int d = arity(op);
     if (n <= 0) return;
     double *rs = (double *)malloc(sizeof(double) * d * (size_t)n);
@@ -306,8 +308,13 @@ void oracle_scan_vjp(int op, int64_t n, const double *x, const double *ybar, dou
         memcpy(xbar + i * d, yb, sizeof(double) * d);
     }
     memcpy(xbar, rb, sizeof(double) * d);
+    if (rbar) memcpy(rbar, rb, sizeof(double) * d * (size_t)n);
     free(rs);
     free(rb);
+}
+
+void oracle_scan_vjp(int op, int64_t n, const double *x, const double *ybar, double *xbar) {
+    oracle_scan_vjp_rbar(op, n, x, ybar, xbar, NULL);
 }
 
 /* Tangent propagation through the scan loop. */

@@ -163,3 +163,19 @@ def test_scan_empty_and_single():
     assert oracle.scan_fwd("add", []).shape == (0,)
     assert_close(oracle.scan_vjp("mul", [3.0], [2.0]), [2.0])
     assert_close(oracle.scan_vjp("mm2", np.ones((1, 4)), [[1, 2, 3, 4]]), [[1, 2, 3, 4]])
+
+
+def test_scan_rbar_is_the_adjoint_of_the_scan_result():
+    # rbar_i = d<ybar, y>/d y_i through the later outputs: for + it is the
+    # suffix sum of ybar, for * the textbook recurrence lam_i = yb_i + x_{i+1} lam_{i+1}.
+    n = 50
+    x = RNG.uniform(0.8, 1.2, n)
+    yb = RNG.standard_normal(n)
+    xb, rb = oracle.scan_vjp_rbar("add", x, yb)
+    assert_close(rb, np.cumsum(yb[::-1])[::-1], rtol=1e-12, atol=1e-12)
+    xb, rb = oracle.scan_vjp_rbar("mul", x, yb)
+    lam = np.zeros(n)
+    for i in range(n - 1, -1, -1):
+        lam[i] = yb[i] + (x[i + 1] * lam[i + 1] if i + 1 < n else 0.0)
+    assert_close(rb, lam, rtol=1e-12, atol=1e-12)
+    assert_close(xb, oracle.scan_vjp("mul", x, yb), rtol=0, atol=0)
