@@ -1,0 +1,383 @@
+"""Benchmark: reverse-mode AD of reduce_by_index with the specialised operators.
+
+Workload (the paper's reduce-by-index evaluation shape, Sec. 6.1.2, with the
+histogram sizes 31 / 401 / 50,000 plus 10M): fp32, n = 50M values with
+uniform int32 bin indices, for every m in {31, 401, 50000, 10M} and every
+operator in {* (values ~U(0.5,1.5), 1% exact zeros), min, max (values on 1024
+exact levels)}.  One step = the differentiated program for all twelve
+(operator, m) instances: the lifted forward pass (histogram + residuals) and
+the vjp w.r.t. the values given a histogram adjoint ~N(0,1).
+
+Metric: vjp elements/s = (12 x 50M) / step time, whole job over all GPUs
+(replicas: every rank runs the full workload on its own GPU).  Also reported:
+the HBM roofline fraction of the dominant kernel, the AD overhead
+(differentiated / original primal time) per instance, an end-to-end number
+through the C ABI with host buffers, and the fp64 oracle timed on the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N = 50_000_000
+BINS = (31, 401, 50_000, 10_000_000)
+OPS = ("mul", "min", "max")
+METRIC = "vjp elements/s & % HBM roofline; AD overhead = vjp time / primal time"
+WORKLOAD = ("reduce_by_index specialisations fp32: n=50M uniform int32 bins, m in {31,401,50000,10M}, "
+            "ops * (1% zeros), min, max (1024 levels); lifted forward + vjp per (op, m)")
+# our kernels launched per API call (see csrc/hist.cu)
+LAUNCHES = {("fwd", "mul"): 3, ("vjp", "mul"): 1, ("fwd", "min"): 3, ("vjp", "min"): 2,
+            ("fwd", "max"): 3, ("vjp", "max"): 2, ("prim", "mul"): 2, ("prim", "min"): 2, ("prim", "max"): 2}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=N, help="elements per instance (default: the full 50M)")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_inputs(n, seed=1):
+    """Keys per m and values per operator (numpy, host), drawn by the seeded generators."""
+    from paper_2310_03568_gb300 import synth
+    g = synth.rng(seed)
+    keys = {m: synth.keys_uniform(g, n, m) for m in BINS}
+    vals = {op: synth.hist_spec_values(g, op, n, 1, np.float32) for op in OPS}
+    hbar = {m: synth.normal(g, m) for m in BINS}
+    return keys, vals, hbar
+
+
+def read_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------- our arm ----
+def run_ours(args, world, rank, local):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2310_03568_gb300 import adcomb
+    from paper_2310_03568_gb300.build import build
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    adcomb.lib()
+    n = args.n
+    keys_h, vals_h, hbar_h = make_inputs(n)
+    dev = torch.device("cuda", local)
+    keys = {m: torch.from_numpy(keys_h[m]).to(dev) for m in BINS}
+    vals = {op: torch.from_numpy(vals_h[op]).to(dev) for op in OPS}
+    hbar = {m: torch.from_numpy(hbar_h[m]).to(dev) for m in BINS}
+    hist = {m: torch.empty(m, dtype=torch.float32, device=dev) for m in BINS}
+    saved = {(op, m): torch.empty(max(adcomb.saved_bytes("hist", op, torch.float32, n, m), 16), dtype=torch.uint8,
+                                  device=dev) for op in OPS for m in BINS}
+    vbar = torch.empty(n, dtype=torch.float32, device=dev)
+    wsb = max(adcomb.workspace_bytes("hist", op, torch.float32, n, m) for op in OPS for m in BINS)
+    ws = adcomb.Workspace()
+    ws.get(wsb, dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for m in BINS:
+            for op in OPS:
+                if ev is not None:
+                    ev[(op, m, "fwd")][0].record(stream)
+                adcomb.hist_fwd(op, m, keys[m], vals[op], None, hist[m], saved[(op, m)], ws=ws)
+                if ev is not None:
+                    ev[(op, m, "fwd")][1].record(stream)
+                adcomb.hist_vjp(op, m, keys[m], vals[op], None, hist[m], saved[(op, m)], hbar[m], valsbar=vbar,
+                                ws=ws)
+                if ev is not None:
+                    ev[(op, m, "vjp")][1].record(stream)
+
+    def primal():
+        """The original (non-lifted) primal of every instance, for the AD overhead."""
+        out = {}
+        for m in BINS:
+            for op in OPS:
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                adcomb.hist_primal(op, m, keys[m], vals[op], None, hist[m], ws=ws)
+                b.record(stream)
+                out[(op, m)] = (a, b)
+        return out
+
+    def new_events():
+        ev = {}
+        for op in OPS:
+            for m in BINS:
+                f0, f1, v1 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+                ev[(op, m, "fwd")] = (f0, f1)
+                ev[(op, m, "vjp")] = (f1, v1)  # the vjp starts where the fwd ends
+        return ev
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    time.sleep(0.3)
+    events = [new_events() for _ in range(args.steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for i in range(args.steps):
+        step(events[i])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    per = {k: [ev[k][0].elapsed_time(ev[k][1]) for ev in events] for k in events[0]}
+    step_ms = t0.elapsed_time(t1) / args.steps
+    elapsed = torch.tensor([step_ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(elapsed, op=dist.ReduceOp.MAX)
+    step_ms = float(elapsed.item())
+
+    # primal (original program) timing for the AD overhead
+    for _ in range(2):
+        primal()
+    torch.cuda.synchronize()
+    prim_ms = {k: [] for k in per if k[2] == "fwd"}
+    for _ in range(3):
+        ev = primal()
+        torch.cuda.synchronize()
+        for (op, m), (a, b) in ev.items():
+            prim_ms[(op, m, "fwd")].append(a.elapsed_time(b))
+    ad = {f"{op}/{m}": round((statistics.mean(per[(op, m, "fwd")]) + statistics.mean(per[(op, m, "vjp")])) /
+                             statistics.mean(prim_ms[(op, m, "fwd")]), 2) for op in OPS for m in BINS}
+
+    # dominant call and its roofline: algorithmic bytes per launch
+    call_ms = {k: statistics.mean(v) for k, v in per.items()}
+    dom = max(call_ms, key=call_ms.get)
+    op_d, m_d, ph_d = dom
+    alg = {"fwd": 8 * n, "vjp": {"mul": 12 * n, "min": 4 * n, "max": 4 * n}[op_d]}[ph_d]
+    peak, peak_kind = read_peaks()
+    achieved = alg / (call_ms[dom] * 1e-3) / 1e9
+    total_elems = world * len(BINS) * len(OPS) * n
+    value = total_elems / (step_ms * 1e-3)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world)
+    launches = args.steps * sum(LAUNCHES[("fwd", op)] + LAUNCHES[("vjp", op)] for op in OPS) * len(BINS)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(n, keys_h, vals_h, hbar_h)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (seeded numpy, shapes of the paper's Sec. 6.1.2)",
+            "config": {"workload": WORKLOAD, "n": n, "bins": list(BINS), "ops": list(OPS),
+                       "instances_per_step": len(BINS) * len(OPS), "parallelism": f"replicas x{world}",
+                       "l2": "inputs larger than L2 (200 MB keys + 200 MB values per instance); no flush"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": f"hist_{ph_d} {op_d} m={m_d}", "algorithmic_bytes": alg,
+                         "peak_source": f"{peak_kind} hbm_gbs"},
+            "ad_overhead": ad,
+            "per_call_ms": {f"{op}/{m}/{ph}": round(v, 4) for (op, m, ph), v in call_ms.items()},
+            "primal_ms": {f"{op}/{m}": round(statistics.mean(v), 4) for (op, m, _), v in prim_ms.items()},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
+    """Same metric through the C-ABI calls with host buffers: H2D of every
+    instance's inputs and D2H of its results inside the timed region."""
+    import torch
+
+    from paper_2310_03568_gb300 import adcomb
+    pin_k = {m: torch.from_numpy(keys_h[m]).pin_memory() for m in BINS}
+    pin_v = {op: torch.from_numpy(vals_h[op]).pin_memory() for op in OPS}
+    pin_h = {m: torch.from_numpy(hbar_h[m]).pin_memory() for m in BINS}
+    out_h = {m: torch.empty(m, dtype=torch.float32).pin_memory() for m in BINS}
+    out_v = torch.empty(n, dtype=torch.float32).pin_memory()
+    k_d = torch.empty(n, dtype=torch.int32, device=dev)
+    v_d = torch.empty(n, dtype=torch.float32, device=dev)
+    hb_d = {m: torch.empty(m, dtype=torch.float32, device=dev) for m in BINS}
+    vbar = torch.empty(n, dtype=torch.float32, device=dev)
+    h2d = d2h = 0
+
+    def step():
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        for m in BINS:
+            k_d.copy_(pin_k[m], non_blocking=True)
+            hb_d[m].copy_(pin_h[m], non_blocking=True)
+            h2d += 4 * n + 4 * m
+            for op in OPS:
+                v_d.copy_(pin_v[op], non_blocking=True)
+                h2d += 4 * n
+                adcomb.hist_fwd(op, m, k_d, v_d, None, hist[m], saved[(op, m)], ws=ws)
+                adcomb.hist_vjp(op, m, k_d, v_d, None, hist[m], saved[(op, m)], hb_d[m], valsbar=vbar, ws=ws)
+                out_h[m].copy_(hist[m], non_blocking=True)
+                out_v.copy_(vbar, non_blocking=True)
+                d2h += 4 * m + 4 * n
+
+    step()
+    torch.cuda.synchronize()
+    steps = max(1, min(args.steps, 3))
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        step()
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    return {"value": world * len(BINS) * len(OPS) * n / (ms * 1e-3), "unit": "elements/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+
+
+# ------------------------------------------------------------ cpu oracle ----
+SAMPLE = 4_000_000
+
+
+def cpu_baseline(n, keys_h, vals_h, hbar_h, sample=SAMPLE):
+    """The fp64 oracle, as it stands, on the first `sample` elements of every
+    instance (single-threaded by definition: sequential semantics)."""
+    import oracle
+    s = min(sample, n)
+    t = time.perf_counter()
+    for m in BINS:
+        k = keys_h[m][:s]
+        for op in OPS:
+            v = vals_h[op][:s]
+            oracle.hist_fwd(op, m, k, v)
+            oracle.hist_vjp(op, m, k, v, hbar_h[m])
+    dt = time.perf_counter() - t
+    return {"value": len(BINS) * len(OPS) * s / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {s} of the {n} elements of each of the 12 (op, m) instances; forward + vjp, fp64",
+            "seconds": dt}
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the fp64 oracle timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    n = args.n
+    s = min(SAMPLE // 2, n)
+    keys_h, vals_h, hbar_h = make_inputs(s)
+    for _ in range(min(args.warmup, 1)):
+        cpu_baseline(s, keys_h, vals_h, hbar_h, sample=min(s, 200_000))
+    times = []
+    for _ in range(args.steps):
+        r = cpu_baseline(s, keys_h, vals_h, hbar_h, sample=s)
+        times.append(r["seconds"])
+    ms = 1e3 * statistics.mean(times)
+    value = len(BINS) * len(OPS) * s / (ms * 1e-3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n": n, "sample_per_instance": s},
+        "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
+                         "sample": f"{s} elements of each of the 12 (op, m) instances per step; forward + vjp"},
+        "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

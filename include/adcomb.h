@@ -1,0 +1,209 @@
+/*
+ * libadcomb -- reverse-mode AD of reduce, scan and reduce-by-index on GB300.
+ *
+ * C ABI over hand-written sm_103a CUDA kernels.  Every entry point follows a
+ * definition of "Reverse-Mode AD of Reduce-by-Index and Scan in Futhark"
+ * (arXiv 2310.03568); the citation is given per function.  "vjp" is the
+ * paper's vector-Jacobian product (Sec. 2.2): given the adjoint of the result,
+ * return the adjoint of the inputs.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ *  Pointers.  Every array argument is a DEVICE pointer on the current CUDA
+ *    device, owned by the caller.  The library never allocates, frees or
+ *    synchronises (except adc_check_device_error, which says so); all work is
+ *    queued asynchronously on `stream` (a cudaStream_t passed as void*, NULL
+ *    means the legacy default stream).  Arrays must be 16-byte aligned.
+ *  Element layout.  fp32 (ADC_F32) or fp64 (ADC_F64) as chosen by `dtype`.
+ *    Tuple operators use AoS:
+ *      ADC_OP_LIN : element (b, c), the function x -> b + c*x; the operator is
+ *                   (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)        (Fig. 8, linFnComp)
+ *      ADC_OP_MM2 : element (a, b, c, d) = row-major [[a, b], [c, d]];
+ *                   X . Y = X * Y                                  (Fig. 8, matMul2x2)
+ *    so an element is 1, 2 or 4 scalars ("arity" below).
+ *  Keys.  int32; keys outside [0, m) are ignored (Sec. 4) and their values
+ *    receive adjoint 0 (Fig. 4).
+ *  Workspace.  `ws` is caller-owned device scratch of at least
+ *    adc_workspace_bytes(...) bytes; the library zeroes the parts it needs
+ *    inside each call (cudaMemsetAsync).  One workspace must not be used by
+ *    two calls that may run concurrently.
+ *  Saved residuals.  `saved` is caller-owned device memory of at least
+ *    adc_saved_bytes(...) bytes, written by a *_fwd call and read by the
+ *    matching *_vjp call (the "primal trace" of Sec. 2.2).  Its content is
+ *    listed per operator below.
+ *  accumulate.  0: the adjoint output is overwritten; 1: the contribution is
+ *    added to it (the paper's "+=", Eq. 1).
+ *  Errors.  Status codes only; nothing is thrown across the ABI.  Argument
+ *    errors are detected on the host before anything is queued.  Device-side
+ *    waits are bounded; a wait that expires records ADC_ERR_TIMEOUT in the
+ *    workspace, read back by adc_check_device_error.
+ *  Edge cases.  n = 0 is valid: a reduce returns the neutral element, a
+ *    histogram equals hist0 (or the neutral element), nothing is written to
+ *    adjoints of length 0.
+ */
+#ifndef ADCOMB_H
+#define ADCOMB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ADC_OP_ADD = 0,   /* +                                   */
+    ADC_OP_MUL = 1,   /* *  (with zero counting, Fig. 3)     */
+    ADC_OP_MIN = 2,   /* min (lifted with the argmin index)  */
+    ADC_OP_MAX = 3,   /* max (lifted with the argmax index)  */
+    ADC_OP_LIN = 4,   /* linFnComp on (b, c) pairs           */
+    ADC_OP_MM2 = 5    /* 2x2 matrix product                  */
+} adc_op;
+
+typedef enum { ADC_F32 = 0, ADC_F64 = 1 } adc_dtype;
+
+typedef enum {
+    ADC_OK = 0,
+    ADC_ERR_INVALID_ARG = 1,  /* null/misaligned pointer, negative size, bad enum      */
+    ADC_ERR_UNSUPPORTED = 2,  /* operator not defined for this combinator (e.g. MM2 histogram) */
+    ADC_ERR_WORKSPACE = 3,    /* workspace or saved buffer smaller than required      */
+    ADC_ERR_CUDA = 4,         /* a CUDA call or kernel launch failed                  */
+    ADC_ERR_TIMEOUT = 5       /* a bounded device-side wait expired                   */
+} adc_status;
+
+typedef enum { ADC_REDUCE = 0, ADC_SCAN = 1, ADC_HIST = 2 } adc_kind;
+
+/* Human-readable name of a status code (static string). */
+const char *adc_status_string(adc_status s);
+
+/* Library version string (static). */
+const char *adc_version(void);
+
+/*
+ * Bytes of workspace / saved residuals required by the given call shape.
+ * m is ignored for reduce and scan.  Returns 0 for unsupported combinations
+ * (the entry point then reports ADC_ERR_UNSUPPORTED).
+ */
+size_t adc_workspace_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m);
+size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m);
+
+/* ---------------------------------------------------------------- reduce --
+ * y = reduce (.) e [x_0 .. x_{n-1}]                              (Sec. 3.1)
+ *   x     : [n] elements (arity per op)          y : one element
+ *   saved : ADD -- unused
+ *           MIN/MAX -- int32 k, the index of the selected element, lowest
+ *                   index among equal values, n if none     (Sec. 3.2.2)
+ *           MUL -- int32 n0 (number of zeros) then one scalar y>0, the product
+ *                  of the non-zeros (Fig. 3's lifted primal)
+ *           LIN/MM2 -- per-tile exclusive prefix and suffix partials used by
+ *                  the general rule (Fig. 2)
+ *   ops: ADD, MUL, MIN, MAX, LIN, MM2.  MIN/MAX need n < 2^31.
+ */
+adc_status adc_reduce_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
+                          void *saved, void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * xbar (+)= d y / d x ^T ybar                                     (Sec. 3)
+ *   ADD     : xbar_i = ybar                                      (Sec. 3.2.1)
+ *   MIN/MAX : xbar_k = ybar at the saved index k, 0 elsewhere    (Sec. 3.2.2)
+ *   MUL     : three-case rule of Fig. 3 (division by x_i when there is no zero)
+ *   LIN/MM2 : xbar_i = d(l_i . x_i . r_i)/dx_i ybar with l_i, r_i the exclusive
+ *             prefix / suffix (Eq. red-adj, Fig. 2); for MM2 xbar_i = l_i^T ybar r_i^T
+ *   x, y and saved are the fwd call's input, output and residuals; ybar is one
+ *   element in device memory.
+ */
+adc_status adc_reduce_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, const void *y,
+                          const void *saved, const void *ybar, void *xbar, int accumulate,
+                          void *ws, size_t ws_bytes, void *stream);
+
+/* ------------------------------------------------------------------ scan --
+ * Inclusive scan y_i = x_0 . x_1 . ... . x_i                      (Sec. 5.1)
+ *   x, y : [n] elements.  ops: ADD, MUL, LIN, MM2.
+ */
+adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * xbar (+)= d y / d x ^T ybar by the rule of Fig. 7: the backward linear
+ * recurrence lambda_i = ybar_i + c_{i+1} lambda_{i+1},
+ * c_{i+1} = d(y_i . x_{i+1})/d y_i, solved by one reverse scan of linear-function
+ * composition, fused with the map xbar_i = d(y_{i-1} . x_i)/d x_i lambda_i
+ * (y_{-1} = e).  The Jacobians are block-diagonal with equal blocks (RBDS,
+ * Sec. 5.3.4): a scalar c for ADD/MUL/LIN, M_{i+1}^T for MM2.
+ *   x, y : the fwd call's input and output; ybar, xbar : [n] elements.
+ */
+adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, const void *y,
+                        const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes,
+                        void *stream);
+
+/* ------------------------------------------------------- reduce_by_index --
+ * hist = reduce_by_index hist0 (.) e keys vals                    (Sec. 4)
+ *   keys : [n] int32, vals : [n] elements, hist0 : [m] elements or NULL for the
+ *   neutral element, hist : [m] elements (output).
+ *   saved : ADD -- unused
+ *           MIN/MAX -- int32 is[m]: per bin the index of the selected value
+ *                   (lowest index on ties), n when the bin is empty or hist0
+ *                   won (hist0 wins ties)             (Sec. 4.2.2, Fig. 5)
+ *           MUL -- int32 n0[m] zero counts, then p[m] products of the non-zeros
+ *                   (Sec. 4.2.3)
+ *           LIN -- the stable sort permutation, the sorted keys and the sorted
+ *                   values (general rule, Fig. 4)
+ *   ops: ADD, MUL, MIN, MAX, LIN (LIN is not commutative: the fold follows the
+ *   index order within each bin, computed through a stable sort).  MM2 is
+ *   ADC_ERR_UNSUPPORTED.  Requires 1 <= m < 2^31 and n < 2^31.
+ *   saved == NULL (MUL, MIN, MAX only) computes the ORIGINAL, un-lifted primal
+ *   instead -- the plain product per bin with zeros included, or the plain
+ *   min/max value -- and keeps no residuals, so no vjp can follow.  This is the
+ *   program whose time the AD overhead of Sec. 6.1.4 is measured against.
+ */
+adc_status adc_hist_fwd(adc_op op, adc_dtype dtype, int64_t n, int64_t m, const int32_t *keys,
+                        const void *vals, const void *hist0, void *hist, void *saved, void *ws,
+                        size_t ws_bytes, void *stream);
+
+/*
+ * valsbar (+)= d hist / d vals ^T histbar and, when hist0bar is not NULL,
+ * hist0bar (+)= d hist / d hist0 ^T histbar.
+ *   ADD     : valsbar_i = histbar[k_i]                           (Sec. 4.2.1)
+ *   MIN/MAX : valsbar[is[j]] = histbar[j]                        (Fig. 5)
+ *   MUL     : per-bin zero-count rule                            (Sec. 4.2.3)
+ *   LIN     : sorted segmented forward and reverse scans, then
+ *             d(l_i . v_i . r_i)/dv_i histbar[k_i], scattered back (Fig. 4)
+ *   hist and saved are the fwd call's output and residuals.
+ */
+adc_status adc_hist_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t m, const int32_t *keys,
+                        const void *vals, const void *hist0, const void *hist, const void *saved,
+                        const void *histbar, void *valsbar, void *hist0bar, int accumulate,
+                        void *ws, size_t ws_bytes, void *stream);
+
+/* ----------------------------------------------------------- diagnostics --
+ * Waits for `stream`, reads the workspace's device error word and returns
+ * ADC_OK or the recorded error (ADC_ERR_TIMEOUT).  This call synchronises.
+ */
+adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream);
+
+/*
+ * Bound on device-side spin iterations (each iteration polls once and sleeps
+ * about 100 ns); default 1 << 22.  Values < 1 restore the default.
+ */
+void adc_set_spin_limit(int64_t iterations);
+
+/*
+ * Fault-injection hook for tests: the scan tile with this claim index
+ * publishes nothing, so every tile that looks back across it must give up
+ * after the spin limit and report ADC_ERR_TIMEOUT.  -1 (the default) disables.
+ */
+void adc_debug_set_stall_tile(int64_t tile);
+
+/*
+ * Test hook: force the forward histogram strategy of ADD/MUL/MIN/MAX
+ * (0: per-warp shared-memory copies, 1: one shared-memory copy per block,
+ * 2: global atomics) where the histogram fits it; -1 (default) chooses
+ * automatically from m and the operator.
+ */
+void adc_debug_force_hist_strategy(int strategy);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADCOMB_H */

@@ -1,0 +1,249 @@
+"""Thin ctypes binding of libadcomb (include/adcomb.h).
+
+Argument marshalling only: every step runs in the library's CUDA kernels.
+torch supplies device memory and the current stream.  The library is loaded on
+first use; if it is missing or cannot be loaded this module raises -- there is
+no CPU fallback.
+
+Names and argument order follow the C ABI: ``reduce_fwd``, ``reduce_vjp``,
+``scan_fwd``, ``scan_vjp``, ``hist_fwd``, ``hist_vjp`` (plus workspace and
+saved-buffer queries).  Tensors are CUDA tensors; tuple operators take
+``[n, 2]`` (lin: ``(b, c)``) or ``[n, 4]`` (mm2: row-major 2x2) tensors.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadcomb.so")
+
+OPS = {"add": 0, "mul": 1, "min": 2, "max": 3, "lin": 4, "mm2": 5}
+ARITY = {"add": 1, "mul": 1, "min": 1, "max": 1, "lin": 2, "mm2": 4}
+DTYPES = {torch.float32: 0, torch.float64: 1}
+KIND = {"reduce": 0, "scan": 1, "hist": 2}
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too small", 4: "CUDA error",
+          5: "device wait expired"}
+
+
+class AdcError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn}: status {code} ({STATUS.get(code, '?')})")
+        self.code = code
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load libadcomb.so (build it first with paper_2310_03568_gb300.build.build())."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libadcomb.so not found at {LIB_PATH}; run the build first")
+            L = ctypes.CDLL(LIB_PATH)
+            i32, i64, sz, p = ctypes.c_int, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+            sig = {
+                "adc_workspace_bytes": ([i32, i32, i32, i64, i64], sz),
+                "adc_saved_bytes": ([i32, i32, i32, i64, i64], sz),
+                "adc_reduce_fwd": ([i32, i32, i64, p, p, p, p, sz, p], i32),
+                "adc_reduce_vjp": ([i32, i32, i64, p, p, p, p, p, i32, p, sz, p], i32),
+                "adc_scan_fwd": ([i32, i32, i64, p, p, p, sz, p], i32),
+                "adc_scan_vjp": ([i32, i32, i64, p, p, p, p, i32, p, sz, p], i32),
+                "adc_hist_fwd": ([i32, i32, i64, i64, p, p, p, p, p, p, sz, p], i32),
+                "adc_hist_vjp": ([i32, i32, i64, i64, p, p, p, p, p, p, p, p, i32, p, sz, p], i32),
+                "adc_check_device_error": ([p, sz, p], i32),
+                "adc_set_spin_limit": ([i64], None),
+                "adc_debug_set_stall_tile": ([i64], None),
+                "adc_debug_force_hist_strategy": ([i32], None),
+                "adc_status_string": ([i32], ctypes.c_char_p),
+                "adc_version": ([], ctypes.c_char_p),
+            }
+            for name, (args, res) in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _check(fn, code):
+    if code != 0:
+        raise AdcError(fn, code)
+
+
+def _dt(t):
+    try:
+        return DTYPES[t.dtype]
+    except KeyError:
+        raise TypeError(f"unsupported dtype {t.dtype}") from None
+
+
+class Workspace:
+    """Caller-owned device scratch, grown on demand (torch allocation)."""
+
+    def __init__(self, device=None):
+        self.device = device
+        self.buf = None
+
+    def get(self, nbytes, device):
+        nbytes = max(int(nbytes), 256)
+        if self.buf is None or self.buf.numel() < nbytes or self.buf.device != device:
+            self.buf = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        return self.buf
+
+
+_default_ws = {}
+
+
+def default_workspace(device):
+    key = (device.type, device.index)
+    if key not in _default_ws:
+        _default_ws[key] = Workspace()
+    return _default_ws[key]
+
+
+def workspace_bytes(kind, op, dtype, n, m=0):
+    return int(lib().adc_workspace_bytes(KIND[kind], OPS[op], DTYPES[dtype], int(n), int(m)))
+
+
+def saved_bytes(kind, op, dtype, n, m=0):
+    return int(lib().adc_saved_bytes(KIND[kind], OPS[op], DTYPES[dtype], int(n), int(m)))
+
+
+def _n(x, op):
+    return x.shape[0] if x.dim() > 0 else 1
+
+
+def _ws(kind, op, x, n, m, ws):
+    need = workspace_bytes(kind, op, x.dtype, n, m)
+    w = (ws or default_workspace(x.device)).get(need, x.device)
+    return w, w.numel()
+
+
+# ---------------------------------------------------------------- reduce ----
+def reduce_fwd(op, x, y=None, saved=None, ws=None, stream=None):
+    """Returns (y, saved).  y has shape [] (scalars) or [d]."""
+    n = x.shape[0]
+    d = ARITY[op]
+    if y is None:
+        y = torch.empty((d,) if d > 1 else (1,), dtype=x.dtype, device=x.device)
+    if saved is None:
+        saved = torch.empty(max(saved_bytes("reduce", op, x.dtype, n), 16), dtype=torch.uint8, device=x.device)
+    w, wb = _ws("reduce", op, x, n, 0, ws)
+    _check("adc_reduce_fwd", lib().adc_reduce_fwd(OPS[op], _dt(x), n, _ptr(x), _ptr(y), _ptr(saved), _ptr(w), wb,
+                                                   _stream(stream)))
+    return y, saved
+
+
+def reduce_vjp(op, x, y, saved, ybar, xbar=None, accumulate=False, ws=None, stream=None):
+    n = x.shape[0]
+    if xbar is None:
+        xbar = torch.empty_like(x)
+    w, wb = _ws("reduce", op, x, n, 0, ws)
+    _check("adc_reduce_vjp", lib().adc_reduce_vjp(OPS[op], _dt(x), n, _ptr(x), _ptr(y), _ptr(saved), _ptr(ybar),
+                                                   _ptr(xbar), int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return xbar
+
+
+# ------------------------------------------------------------------ scan ----
+def scan_fwd(op, x, y=None, ws=None, stream=None):
+    n = x.shape[0]
+    if y is None:
+        y = torch.empty_like(x)
+    w, wb = _ws("scan", op, x, n, 0, ws)
+    _check("adc_scan_fwd", lib().adc_scan_fwd(OPS[op], _dt(x), n, _ptr(x), _ptr(y), _ptr(w), wb, _stream(stream)))
+    return y
+
+
+def scan_vjp(op, x, y, ybar, xbar=None, accumulate=False, ws=None, stream=None):
+    n = ybar.shape[0]
+    if xbar is None:
+        xbar = torch.empty_like(ybar)
+    w, wb = _ws("scan", op, ybar, n, 0, ws)
+    _check("adc_scan_vjp", lib().adc_scan_vjp(OPS[op], _dt(ybar), n, _ptr(x), _ptr(y), _ptr(ybar), _ptr(xbar),
+                                               int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return xbar
+
+
+# ------------------------------------------------------- reduce_by_index ----
+def hist_fwd(op, m, keys, vals, hist0=None, hist=None, saved=None, ws=None, stream=None):
+    """Returns (hist, saved)."""
+    n = keys.shape[0]
+    d = ARITY[op]
+    if hist is None:
+        hist = torch.empty((m, d) if d > 1 else (m,), dtype=vals.dtype, device=vals.device)
+    if saved is None:
+        saved = torch.empty(max(saved_bytes("hist", op, vals.dtype, n, m), 16), dtype=torch.uint8,
+                            device=vals.device)
+    w, wb = _ws("hist", op, vals, n, m, ws)
+    _check("adc_hist_fwd", lib().adc_hist_fwd(OPS[op], _dt(vals), n, int(m), _ptr(keys), _ptr(vals), _ptr(hist0),
+                                               _ptr(hist), _ptr(saved), _ptr(w), wb, _stream(stream)))
+    return hist, saved
+
+
+def hist_primal(op, m, keys, vals, hist0=None, hist=None, ws=None, stream=None):
+    """The original, un-lifted primal (no residuals): adc_hist_fwd with saved = NULL."""
+    n = keys.shape[0]
+    d = ARITY[op]
+    if hist is None:
+        hist = torch.empty((m, d) if d > 1 else (m,), dtype=vals.dtype, device=vals.device)
+    w, wb = _ws("hist", op, vals, n, m, ws)
+    _check("adc_hist_fwd", lib().adc_hist_fwd(OPS[op], _dt(vals), n, int(m), _ptr(keys), _ptr(vals), _ptr(hist0),
+                                               _ptr(hist), None, _ptr(w), wb, _stream(stream)))
+    return hist
+
+
+def hist_vjp(op, m, keys, vals, hist0, hist, saved, histbar, valsbar=None, hist0bar=None, want_hist0bar=False,
+             accumulate=False, ws=None, stream=None):
+    """Returns (valsbar, hist0bar or None)."""
+    n = keys.shape[0]
+    if valsbar is None:
+        valsbar = torch.empty_like(vals)
+    if hist0bar is None and want_hist0bar:
+        hist0bar = torch.empty_like(histbar)
+    w, wb = _ws("hist", op, histbar, n, m, ws)
+    _check("adc_hist_vjp", lib().adc_hist_vjp(OPS[op], _dt(histbar), n, int(m), _ptr(keys), _ptr(vals), _ptr(hist0),
+                                               _ptr(hist), _ptr(saved), _ptr(histbar), _ptr(valsbar), _ptr(hist0bar),
+                                               int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return valsbar, hist0bar
+
+
+# -------------------------------------------------------------- controls ----
+def check_device_error(ws, stream=None):
+    w = ws.buf if isinstance(ws, Workspace) else ws
+    return int(lib().adc_check_device_error(_ptr(w), w.numel(), _stream(stream)))
+
+
+def set_spin_limit(iterations):
+    lib().adc_set_spin_limit(int(iterations))
+
+
+def debug_set_stall_tile(tile):
+    lib().adc_debug_set_stall_tile(int(tile))
+
+
+def debug_force_hist_strategy(strategy):
+    lib().adc_debug_force_hist_strategy(int(strategy))
+
+
+def status_string(code):
+    return lib().adc_status_string(int(code)).decode()
+
+
+def version():
+    return lib().adc_version().decode()

@@ -1,0 +1,203 @@
+// libadcomb C ABI: argument validation, workspace checks and dispatch.
+// Every entry point validates on the host, zeroes the workspace header (error
+// word and launch counters) on the stream, then queues its kernels.
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace adc {
+
+static long long g_spin_limit = 1ll << 22;
+static long long g_stall_tile = -1;
+
+DevCtl make_ctl(void *ws, int slot) {
+    DevCtl c;
+    c.err = static_cast<unsigned *>(ws);
+    c.counter = counter_slot(ws, slot);
+    c.spin_limit = g_spin_limit;
+    c.stall_tile = g_stall_tile;
+    return c;
+}
+
+int num_sms() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 132;
+    if (cache[dev] == 0) {
+        int v = 0;
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        cache[dev] = v > 0 ? v : 132;
+    }
+    return cache[dev];
+}
+
+adc_status check_launch() { return cudaGetLastError() == cudaSuccess ? ADC_OK : ADC_ERR_CUDA; }
+
+}  // namespace adc
+
+using namespace adc;
+
+namespace {
+
+bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_MM2; }
+bool valid_dt(adc_dtype dt) { return dt == ADC_F32 || dt == ADC_F64; }
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+// Array argument: NULL only when empty; 16-byte aligned otherwise.
+bool arr_ok(const void *p, int64_t count) { return count == 0 || (p != nullptr && aligned(p, 16)); }
+// Single-element argument: non-NULL, aligned to its scalar type.
+bool one_ok(const void *p, adc_dtype dt) { return p != nullptr && aligned(p, dt == ADC_F64 ? 8 : 4); }
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+adc_status prologue(void *ws, size_t ws_bytes, size_t need, cudaStream_t s) {
+    if (ws == nullptr || !aligned(ws, 256)) return ADC_ERR_INVALID_ARG;
+    if (ws_bytes < need) return ADC_ERR_WORKSPACE;
+    if (cudaMemsetAsync(ws, 0, kWsHeader, s) != cudaSuccess) return ADC_ERR_CUDA;
+    return ADC_OK;
+}
+
+constexpr int64_t kIdxMax = 0x7fffffffll;
+
+}  // namespace
+
+extern "C" {
+
+const char *adc_status_string(adc_status s) {
+    switch (s) {
+    case ADC_OK: return "ok";
+    case ADC_ERR_INVALID_ARG: return "invalid argument";
+    case ADC_ERR_UNSUPPORTED: return "unsupported operator for this combinator";
+    case ADC_ERR_WORKSPACE: return "workspace or saved buffer too small";
+    case ADC_ERR_CUDA: return "CUDA error";
+    case ADC_ERR_TIMEOUT: return "bounded device wait expired";
+    default: return "unknown status";
+    }
+}
+
+const char *adc_version(void) { return "libadcomb 0.1 (sm_103a)"; }
+
+size_t adc_workspace_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return 0;
+    switch (kind) {
+    case ADC_REDUCE: return reduce_ws_bytes(op, dt, n);
+    case ADC_SCAN:
+        if (op == ADC_OP_MIN || op == ADC_OP_MAX) return 0;
+        return scan_ws_bytes(op, dt, n);
+    case ADC_HIST:
+        if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
+        return hist_ws_bytes(op, dt, n, m);
+    default: return 0;
+    }
+}
+
+size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return 0;
+    switch (kind) {
+    case ADC_REDUCE: return reduce_saved_bytes(op, dt, n);
+    case ADC_SCAN: return 16;  // scans keep no residuals beyond x and y
+    case ADC_HIST:
+        if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
+        return hist_saved_bytes(op, dt, n, m);
+    default: return 0;
+    }
+}
+
+adc_status adc_reduce_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *saved, void *ws,
+                          size_t ws_bytes, void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
+    if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && n >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(x, n) || !one_ok(y, dt)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, reduce_ws_bytes(op, dt, n), s);
+    if (st != ADC_OK) return st;
+    return reduce_fwd(op, dt, n, x, y, saved, ws, s);
+}
+
+adc_status adc_reduce_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *saved,
+                          const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
+    if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && n >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(xbar, n) || !one_ok(ybar, dt)) return ADC_ERR_INVALID_ARG;
+    if ((op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2) && !arr_ok(x, n)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    (void)y;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, reduce_ws_bytes(op, dt, n), s);
+    if (st != ADC_OK) return st;
+    return reduce_vjp(op, dt, n, x, y, saved, ybar, xbar, accumulate ? 1 : 0, ws, s);
+}
+
+adc_status adc_scan_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *ws, size_t ws_bytes,
+                        void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MIN || op == ADC_OP_MAX) return ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(x, n) || !arr_ok(y, n)) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, scan_ws_bytes(op, dt, n), s);
+    if (st != ADC_OK) return st;
+    return scan_fwd(op, dt, n, x, y, ws, s);
+}
+
+adc_status adc_scan_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *ybar,
+                        void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MIN || op == ADC_OP_MAX) return ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(ybar, n) || !arr_ok(xbar, n)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (!arr_ok(x, n) || !arr_ok(y, n))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, scan_ws_bytes(op, dt, n), s);
+    if (st != ADC_OK) return st;
+    return scan_vjp(op, dt, n, x, y, ybar, xbar, accumulate ? 1 : 0, ws, s);
+}
+
+adc_status adc_hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                        const void *hist0, void *hist, void *saved, void *ws, size_t ws_bytes, void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0 || m < 1) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MM2) return ADC_ERR_UNSUPPORTED;
+    if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(keys, n) || !arr_ok(vals, n) || !arr_ok(hist, m)) return ADC_ERR_INVALID_ARG;
+    if (hist0 != nullptr && !aligned(hist0, 16)) return ADC_ERR_INVALID_ARG;
+    // saved == NULL selects the original (un-lifted) primal for MUL/MIN/MAX
+    if (op == ADC_OP_LIN && saved == nullptr) return ADC_ERR_INVALID_ARG;
+    if (saved != nullptr && !aligned(saved, 16)) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, hist_ws_bytes(op, dt, n, m), s);
+    if (st != ADC_OK) return st;
+    return hist_fwd(op, dt, n, m, keys, vals, hist0, hist, saved, ws, s);
+}
+
+adc_status adc_hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                        const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
+                        void *hist0bar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    if (!valid_op(op) || !valid_dt(dt) || n < 0 || m < 1) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MM2) return ADC_ERR_UNSUPPORTED;
+    if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(histbar, m) || !arr_ok(valsbar, n)) return ADC_ERR_INVALID_ARG;
+    if ((op == ADC_OP_ADD || op == ADC_OP_MUL) && !arr_ok(keys, n)) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MUL && !arr_ok(vals, n)) return ADC_ERR_INVALID_ARG;
+    if ((hist0 != nullptr && !aligned(hist0, 16)) || (hist0bar != nullptr && !aligned(hist0bar, 16)))
+        return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, hist_ws_bytes(op, dt, n, m), s);
+    if (st != ADC_OK) return st;
+    return hist_vjp(op, dt, n, m, keys, vals, hist0, hist, saved, histbar, valsbar, hist0bar, accumulate ? 1 : 0, ws,
+                    s);
+}
+
+adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream) {
+    if (ws == nullptr || ws_bytes < kWsHeader) return ADC_ERR_INVALID_ARG;
+    unsigned word = 0;
+    if (cudaStreamSynchronize(as_stream(stream)) != cudaSuccess) return ADC_ERR_CUDA;
+    if (cudaMemcpy(&word, ws, sizeof(word), cudaMemcpyDeviceToHost) != cudaSuccess) return ADC_ERR_CUDA;
+    return word ? ADC_ERR_TIMEOUT : ADC_OK;
+}
+
+void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1ll << 22) : iterations; }
+
+void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
+
+}  // extern "C"

@@ -1,0 +1,799 @@
+// reduce_by_index with the specialised operators (Sec. 4.2) and their vjps.
+//
+// Forward strategies (Sec. 4.2.6 lists the design space; chosen per call):
+//   SMEM_WARP : one private sub-histogram per warp in shared memory (8 copies
+//               per block), shared-memory atomics, one flush per block into
+//               the global result -- for histograms of up to a few KB.
+//   SMEM_BLOCK: one sub-histogram per 1024-thread block filling most of the
+//               SM's shared memory -- for histograms up to ~200 KB.
+//   GLOBAL    : atomics directly on the global table (L2-resident for
+//               m up to ~1e7 fp32).
+// Operators and their atomics:
+//   ADD     : native float/double atomic add.
+//   MIN/MAX : fp32 value and int32 index packed into one 64-bit key
+//             (order-preserving value bits << 32 | index, the index inverted
+//             for max) so that Fig. 5's lifted min^L (smaller index wins
+//             ties) is ONE native 64-bit atomicMin/atomicMax; a plain read of
+//             the current key skips the atomic when it cannot win (the table
+//             only moves one way, so a stale read is safe).  fp64 uses two
+//             phases: the value by 64-bit atomicMin on its ordered bits, then
+//             the lowest index among elements equal to it.
+//   MUL     : (zero count, product of non-zeros) per bin (Sec. 4.2.3): integer
+//             atomicAdd for zeros, compare-and-swap multiply for the rest.
+// The initial histogram is decoupled as in Sec. 4: the atomics build the
+// histogram of the values from the neutral element and a finalising map folds
+// hist0 in (hist0 wins min/max ties, acting as index -1).
+#include "common.cuh"
+#include "internal.h"
+#include "tile_io.cuh"
+
+namespace adc {
+
+enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2 };
+
+// ------------------------------------------------------------ element loop --
+// Calls f(key, value, index) for every element, grid-stride over 4-element
+// vectors (128-bit key loads), two vectors in flight per thread.
+template <typename T, class F>
+__device__ __forceinline__ void for_each_elem(const int32_t *__restrict__ keys, const T *__restrict__ vals,
+                                              const int64_t n, F &&f) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nv = n / 4;
+    int64_t v = gtid;
+    for (; v + stride < nv; v += 2 * stride) {
+        const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        const int4 k1 = __ldcs(reinterpret_cast<const int4 *>(keys) + v + stride);
+        T a[4], b[4];
+        load_chunk(vals, v * 4, n, a, T(0));
+        load_chunk(vals, (v + stride) * 4, n, b, T(0));
+        f(k0.x, a[0], 4 * v);
+        f(k0.y, a[1], 4 * v + 1);
+        f(k0.z, a[2], 4 * v + 2);
+        f(k0.w, a[3], 4 * v + 3);
+        const int64_t w = v + stride;
+        f(k1.x, b[0], 4 * w);
+        f(k1.y, b[1], 4 * w + 1);
+        f(k1.z, b[2], 4 * w + 2);
+        f(k1.w, b[3], 4 * w + 3);
+    }
+    if (v < nv) {
+        const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        T a[4];
+        load_chunk(vals, v * 4, n, a, T(0));
+        f(k0.x, a[0], 4 * v);
+        f(k0.y, a[1], 4 * v + 1);
+        f(k0.z, a[2], 4 * v + 2);
+        f(k0.w, a[3], 4 * v + 3);
+    }
+    for (int64_t i = nv * 4 + gtid; i < n; i += stride) f(keys[i], vals[i], i);
+}
+
+__device__ __forceinline__ bool in_range(int32_t k, int64_t m) { return (uint32_t)k < (uint64_t)m; }
+
+// ----------------------------------------------------------------- packing --
+template <bool MAX> struct Pack {
+    static constexpr unsigned long long kEmpty = MAX ? 0ull : ~0ull;
+    static __device__ __forceinline__ unsigned long long key(float v, int64_t i) {
+        const uint32_t idx = MAX ? (0xffffffffu - (uint32_t)i) : (uint32_t)i;
+        return ((unsigned long long)ordered_key(v) << 32) | idx;
+    }
+    static __device__ __forceinline__ int64_t index(unsigned long long k) {
+        const uint32_t lo = (uint32_t)k;
+        return MAX ? (int64_t)(0xffffffffu - lo) : (int64_t)lo;
+    }
+    static __device__ __forceinline__ bool better(unsigned long long a, unsigned long long b) {
+        return MAX ? a > b : a < b;
+    }
+    static __device__ __forceinline__ void update(unsigned long long *p, unsigned long long k) {
+        if (better(k, __ldcg(p))) {
+            if (MAX) atomicMax(p, k);
+            else atomicMin(p, k);
+        }
+    }
+    static __device__ __forceinline__ void update_smem(unsigned long long *p, unsigned long long k) {
+        if (better(k, *reinterpret_cast<volatile unsigned long long *>(p))) {
+            if (MAX) atomicMax(p, k);
+            else atomicMin(p, k);
+        }
+    }
+};
+
+// ===================================================================== ADD ==
+template <typename T>
+__global__ void k_hist_init(T *__restrict__ h, const T *__restrict__ h0, const int64_t m, const T e) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        h[j] = h0 ? h0[j] : e;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_hist_add_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                const int R, T *__restrict__ hist) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sh = reinterpret_cast<T *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) sh[j] = T(0);
+    __syncthreads();
+    T *mine = sh + (int64_t)((threadIdx.x >> 5) % R) * m;
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (in_range(k, m)) atomicAdd(mine + k, v);
+    });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+        T s = T(0);
+        for (int r = 0; r < R; ++r) s += sh[(int64_t)r * m + j];
+        if (s != T(0)) atomicAdd(hist + j, s);
+    }
+}
+
+template <typename T>
+__global__ void k_hist_add_global(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n,
+                                  const int64_t m, T *__restrict__ hist) {
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (in_range(k, m)) atomicAdd(hist + k, v);
+    });
+}
+
+// ========================================================== MIN/MAX fp32 ==
+template <bool MAX>
+__global__ void k_pack_init(unsigned long long *__restrict__ tab, const int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        tab[j] = Pack<MAX>::kEmpty;
+}
+
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_hist_sel_smem(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                const int R, unsigned long long *__restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *sh = reinterpret_cast<unsigned long long *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) sh[j] = Pack<MAX>::kEmpty;
+    __syncthreads();
+    unsigned long long *mine = sh + (int64_t)((threadIdx.x >> 5) % R) * m;
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
+        if (in_range(k, m)) Pack<MAX>::update_smem(mine + k, Pack<MAX>::key(v, i));
+    });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+        unsigned long long b = Pack<MAX>::kEmpty;
+        for (int r = 0; r < R; ++r) {
+            const unsigned long long c = sh[(int64_t)r * m + j];
+            if (Pack<MAX>::better(c, b)) b = c;
+        }
+        if (b != Pack<MAX>::kEmpty) Pack<MAX>::update(tab + j, b);
+    }
+}
+
+template <bool MAX>
+__global__ void k_hist_sel_global(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n,
+                                  const int64_t m, unsigned long long *__restrict__ tab) {
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
+        if (in_range(k, m)) Pack<MAX>::update(tab + k, Pack<MAX>::key(v, i));
+    });
+}
+
+// Decode the packed table, fold hist0 in (it wins ties), write hist and is.
+template <bool MAX>
+__global__ void k_hist_sel_final(const unsigned long long *__restrict__ tab, const float *__restrict__ vals,
+                                 const float *__restrict__ h0, const int64_t m, const int64_t n,
+                                 float *__restrict__ hist, int32_t *__restrict__ is) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long key = tab[j];
+        const float neutral = MAX ? -Num<float>::inf() : Num<float>::inf();
+        float v = neutral;
+        int64_t idx = n;
+        if (key != Pack<MAX>::kEmpty) {
+            idx = Pack<MAX>::index(key);
+            v = vals[idx];
+        }
+        if (h0) {
+            const float a = h0[j];
+            if (MAX ? (a >= v) : (a <= v)) {
+                v = a;
+                idx = n;
+            }
+        }
+        hist[j] = v;
+        is[j] = (int32_t)idx;
+    }
+}
+
+// ========================================================== MIN/MAX fp64 ==
+template <bool MAX>
+__global__ void k_hist_sel64_value(const int32_t *__restrict__ keys, const double *__restrict__ vals, const int64_t n,
+                                   const int64_t m, unsigned long long *__restrict__ tv) {
+    for_each_elem(keys, vals, n, [&](int32_t k, double v, int64_t) {
+        if (!in_range(k, m)) return;
+        const unsigned long long o = ordered_key(v);
+        const unsigned long long cur = __ldcg(tv + k);
+        if (MAX ? (o > cur) : (o < cur)) {
+            if (MAX) atomicMax(tv + k, o);
+            else atomicMin(tv + k, o);
+        }
+    });
+}
+
+template <bool MAX>
+__global__ void k_hist_sel64_index(const int32_t *__restrict__ keys, const double *__restrict__ vals, const int64_t n,
+                                   const int64_t m, const unsigned long long *__restrict__ tv,
+                                   unsigned *__restrict__ ti) {
+    for_each_elem(keys, vals, n, [&](int32_t k, double v, int64_t i) {
+        if (!in_range(k, m)) return;
+        if (ordered_key(v) == tv[k] && (unsigned)i < __ldcg(ti + k)) atomicMin(ti + k, (unsigned)i);
+    });
+}
+
+__global__ void k_sel64_init(unsigned long long *__restrict__ tv, unsigned *__restrict__ ti, const int64_t m,
+                             const unsigned long long empty) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        tv[j] = empty;
+        ti[j] = 0xffffffffu;
+    }
+}
+
+template <bool MAX>
+__global__ void k_hist_sel64_final(const unsigned *__restrict__ ti, const double *__restrict__ vals,
+                                   const double *__restrict__ h0, const int64_t m, const int64_t n,
+                                   double *__restrict__ hist, int32_t *__restrict__ is) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned i = ti[j];
+        double v = MAX ? -Num<double>::inf() : Num<double>::inf();
+        int64_t idx = n;
+        if (i != 0xffffffffu) {
+            idx = i;
+            v = vals[idx];
+        }
+        if (h0) {
+            const double a = h0[j];
+            if (MAX ? (a >= v) : (a <= v)) {
+                v = a;
+                idx = n;
+            }
+        }
+        hist[j] = v;
+        is[j] = (int32_t)idx;
+    }
+}
+
+// ===================================================================== MUL ==
+template <typename T>
+__global__ void k_mul_init(int32_t *__restrict__ n0, T *__restrict__ p, const int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        n0[j] = 0;
+        p[j] = T(1);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_hist_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                const int R, int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    int32_t *sz = reinterpret_cast<int32_t *>(sp + (int64_t)m * R);
+    for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) {
+        sp[j] = T(1);
+        sz[j] = 0;
+    }
+    __syncthreads();
+    const int64_t off = (int64_t)((threadIdx.x >> 5) % R) * m;
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (!in_range(k, m)) return;
+        if (v == T(0)) atomicAdd(sz + off + k, 1);
+        else atomic_mul(sp + off + k, v, err);
+    });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+        T prod = T(1);
+        int32_t z = 0;
+        for (int r = 0; r < R; ++r) {
+            prod *= sp[(int64_t)r * m + j];
+            z += sz[(int64_t)r * m + j];
+        }
+        if (z) atomicAdd(n0 + j, z);
+        if (prod != T(1)) atomic_mul(p + j, prod, err);
+    }
+}
+
+template <typename T>
+__global__ void k_hist_mul_global(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n,
+                                  const int64_t m, int32_t *__restrict__ n0, T *__restrict__ p,
+                                  unsigned *__restrict__ err) {
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (!in_range(k, m)) return;
+        if (v == T(0)) atomicAdd(n0 + k, 1);
+        else atomic_mul(p + k, v, err);
+    });
+}
+
+template <typename T>
+__global__ void k_hist_mul_final(const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ h0,
+                                 const int64_t m, T *__restrict__ hist) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const T xs = n0[j] > 0 ? T(0) : p[j];
+        hist[j] = h0 ? h0[j] * xs : xs;
+    }
+}
+
+// =================================================== original primals ==
+// The un-lifted primal of Sec. 4 (the program being differentiated): the
+// plain product per bin (zeros included) and the plain min/max value.  Used
+// to measure the AD overhead; it keeps no residuals.
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_prim_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                const int R, T *__restrict__ hist, unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) sp[j] = T(1);
+    __syncthreads();
+    T *mine = sp + (int64_t)((threadIdx.x >> 5) % R) * m;
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (in_range(k, m)) atomic_mul(mine + k, v, err);
+    });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+        T prod = T(1);
+        for (int r = 0; r < R; ++r) prod *= sp[(int64_t)r * m + j];
+        if (prod != T(1)) atomic_mul(hist + j, prod, err);
+    }
+}
+
+template <typename T>
+__global__ void k_prim_mul_global(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n,
+                                  const int64_t m, T *__restrict__ hist, unsigned *__restrict__ err) {
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (in_range(k, m)) atomic_mul(hist + k, v, err);
+    });
+}
+
+template <bool MAX> struct Ord32 {
+    static constexpr uint32_t kEmpty = MAX ? 0u : 0xffffffffu;
+    static __device__ __forceinline__ bool better(uint32_t a, uint32_t b) { return MAX ? a > b : a < b; }
+    static __device__ __forceinline__ void update(uint32_t *p, uint32_t k, bool shared) {
+        const uint32_t cur = shared ? *reinterpret_cast<volatile uint32_t *>(p) : __ldcg(p);
+        if (better(k, cur)) {
+            if (MAX) atomicMax(p, k);
+            else atomicMin(p, k);
+        }
+    }
+};
+
+__device__ __forceinline__ float from_ordered(uint32_t u) {
+    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
+}
+__device__ __forceinline__ double from_ordered(unsigned long long u) {
+    return __longlong_as_double(
+        (long long)((u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u));
+}
+
+template <bool MAX>
+__global__ void k_ord32_init(uint32_t *__restrict__ tab, const int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        tab[j] = Ord32<MAX>::kEmpty;
+}
+
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_prim_sel_smem(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                const int R, uint32_t *__restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) sh[j] = Ord32<MAX>::kEmpty;
+    __syncthreads();
+    uint32_t *mine = sh + (int64_t)((threadIdx.x >> 5) % R) * m;
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t) {
+        if (in_range(k, m)) Ord32<MAX>::update(mine + k, ordered_key(v), true);
+    });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
+        uint32_t b = Ord32<MAX>::kEmpty;
+        for (int r = 0; r < R; ++r) {
+            const uint32_t c = sh[(int64_t)r * m + j];
+            if (Ord32<MAX>::better(c, b)) b = c;
+        }
+        if (b != Ord32<MAX>::kEmpty) Ord32<MAX>::update(tab + j, b, false);
+    }
+}
+
+template <bool MAX>
+__global__ void k_prim_sel_global(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n,
+                                  const int64_t m, uint32_t *__restrict__ tab) {
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t) {
+        if (in_range(k, m)) Ord32<MAX>::update(tab + k, ordered_key(v), false);
+    });
+}
+
+template <bool MAX, typename T, typename U>
+__global__ void k_prim_sel_final(const U *__restrict__ tab, const T *__restrict__ h0, const int64_t m,
+                                 T *__restrict__ hist, const U empty) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const U key = tab[j];
+        T v = (key == empty) ? (MAX ? -Num<T>::inf() : Num<T>::inf()) : from_ordered(key);
+        if (h0) v = MAX ? (h0[j] >= v ? h0[j] : v) : (h0[j] <= v ? h0[j] : v);
+        hist[j] = v;
+    }
+}
+
+// ==================================================================== VJPs ==
+template <typename T>
+__global__ void k_fill(T *__restrict__ a, const int64_t n) {
+    constexpr int V = 16 / sizeof(T);
+    const int64_t nv = n / V;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (int64_t i = g; i < nv; i += stride) __stcs(reinterpret_cast<uint4 *>(a) + i, make_uint4(0, 0, 0, 0));
+    for (int64_t i = nv * V + g; i < n; i += stride) a[i] = T(0);
+}
+
+// Sec. 4.2.1: valsbar_i (+)= histbar[k_i] (0 for out-of-range keys).
+template <typename T>
+__global__ void k_hist_add_vjp(const int32_t *__restrict__ keys, const T *__restrict__ hb, T *__restrict__ vb,
+                               const int64_t n, const int64_t m, const int accumulate) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nv = n / 4;
+    for (int64_t v = g; v < nv; v += stride) {
+        const int4 k = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        T o[4];
+        if (accumulate) load_chunk(vb, v * 4, n, o, T(0));
+        const int kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const T gv = in_range(kk[c], m) ? __ldg(hb + kk[c]) : T(0);
+            o[c] = accumulate ? o[c] + gv : gv;
+        }
+        store_chunk(vb, v * 4, n, o);
+    }
+    for (int64_t i = nv * 4 + g; i < n; i += stride) {
+        const int32_t k = keys[i];
+        const T gv = in_range(k, m) ? hb[k] : T(0);
+        vb[i] = accumulate ? vb[i] + gv : gv;
+    }
+}
+
+// hist0bar (+)= histbar, masked per operator.
+template <typename T>
+__global__ void k_h0bar_add(const T *__restrict__ hb, T *__restrict__ h0b, const int64_t m, const int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
+        h0b[j] = accumulate ? h0b[j] + hb[j] : hb[j];
+}
+
+// Fig. 5 return sweep: valsbar[is[j]] += histbar[j]; hist0bar[j] gets histbar[j] where hist0 won.
+template <typename T>
+__global__ void k_hist_sel_vjp(const int32_t *__restrict__ is, const T *__restrict__ hb, T *__restrict__ vb,
+                               T *__restrict__ h0b, const int64_t m, const int64_t n, const int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = is[j];
+        if (i >= 0 && i < n) vb[i] += hb[j];
+        if (h0b) {
+            const T g = (i >= n) ? hb[j] : T(0);
+            h0b[j] = accumulate ? h0b[j] + g : g;
+        }
+    }
+}
+
+// Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.
+template <typename T>
+__global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__restrict__ vals,
+                               const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ h0,
+                               const T *__restrict__ hb, T *__restrict__ vb, const int64_t n, const int64_t m,
+                               const int accumulate) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    auto grad = [&](int32_t k, T v) -> T {
+        if (!in_range(k, m)) return T(0);
+        const int32_t z = __ldg(n0 + k);
+        const T pk = __ldg(p + k);
+        T d;
+        if (z == 0) d = pk / v;
+        else if (z == 1 && v == T(0)) d = pk;
+        else return T(0);
+        const T scale = h0 ? __ldg(h0 + k) * __ldg(hb + k) : __ldg(hb + k);
+        return d * scale;
+    };
+    const int64_t nv = n / 4;
+    for (int64_t v = g; v < nv; v += stride) {
+        const int4 k = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        T a[4], o[4];
+        load_chunk(vals, v * 4, n, a, T(1));
+        if (accumulate) load_chunk(vb, v * 4, n, o, T(0));
+        const int kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const T gv = grad(kk[c], a[c]);
+            o[c] = accumulate ? o[c] + gv : gv;
+        }
+        store_chunk(vb, v * 4, n, o);
+    }
+    for (int64_t i = nv * 4 + g; i < n; i += stride) {
+        const T gv = grad(keys[i], vals[i]);
+        vb[i] = accumulate ? vb[i] + gv : gv;
+    }
+}
+
+template <typename T>
+__global__ void k_h0bar_mul(const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ hb,
+                            T *__restrict__ h0b, const int64_t m, const int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const T g = (n0[j] > 0 ? T(0) : p[j]) * hb[j];
+        h0b[j] = accumulate ? h0b[j] + g : g;
+    }
+}
+
+// ================================================================== host ==
+static unsigned grid_for(int64_t work, int per_sm) {
+    int64_t g = (work + 255) / 256;
+    const int64_t cap = (int64_t)num_sms() * per_sm;
+    if (g > cap) g = cap;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// Shared-memory bytes per bin entry of the forward strategy.
+static size_t entry_bytes(adc_op op, adc_dtype dt) {
+    const size_t s = dt == ADC_F64 ? 8 : 4;
+    switch (op) {
+    case ADC_OP_ADD: return s;
+    case ADC_OP_MUL: return s + 4;
+    case ADC_OP_MIN:
+    case ADC_OP_MAX: return 8;
+    default: return 0;
+    }
+}
+
+static int g_force_strategy = -1;  // tests: force a strategy (-1: automatic)
+
+static HistStrategy pick(adc_op op, adc_dtype dt, int64_t m, int *R) {
+    const size_t e = entry_bytes(op, dt);
+    const bool sel64 = (op == ADC_OP_MIN || op == ADC_OP_MAX) && dt == ADC_F64;
+    HistStrategy s;
+    if (sel64) s = kGlobal;
+    else if ((size_t)m * e * 8 <= 24 * 1024) s = kSmemWarp;
+    else if ((size_t)m * e <= 200 * 1024) s = kSmemBlock;
+    else s = kGlobal;
+    if (g_force_strategy >= 0 && !sel64) {
+        const HistStrategy f = (HistStrategy)g_force_strategy;
+        if (f == kGlobal || (f == kSmemBlock && (size_t)m * e <= 200 * 1024) || (size_t)m * e * 8 <= 24 * 1024) s = f;
+    }
+    *R = (s == kSmemWarp) ? 8 : 1;
+    return s;
+}
+
+size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+    (void)n;
+    switch (op) {
+    case ADC_OP_ADD:
+    case ADC_OP_MUL: return kWsHeader;
+    case ADC_OP_MIN:
+    case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
+    case ADC_OP_LIN: return histgen_ws_bytes(dt, n, m);
+    default: return 0;
+    }
+}
+
+size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+    const size_t s = dt == ADC_F64 ? 8 : 4;
+    switch (op) {
+    case ADC_OP_ADD: return 16;
+    case ADC_OP_MIN:
+    case ADC_OP_MAX: return (size_t)m * 4;
+    case ADC_OP_MUL: return align_up((size_t)m * 4, 16) + (size_t)m * s;
+    case ADC_OP_LIN: return histgen_saved_bytes(dt, n, m);
+    default: return 0;
+    }
+}
+
+// Strategy for a table of `e`-byte entries (same thresholds as pick()).
+static HistStrategy pick_entry(size_t e, int64_t m, int *R) {
+    HistStrategy s;
+    if ((size_t)m * e * 8 <= 24 * 1024) s = kSmemWarp;
+    else if ((size_t)m * e <= 200 * 1024) s = kSmemBlock;
+    else s = kGlobal;
+    *R = (s == kSmemWarp) ? 8 : 1;
+    return s;
+}
+
+template <typename T>
+static adc_status hist_primal_t(adc_op op, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0,
+                                T *hist, void *ws, cudaStream_t s) {
+    char *w = static_cast<char *>(ws);
+    unsigned *err = reinterpret_cast<unsigned *>(w);
+    const unsigned gm = grid_for(m, 4);
+    const unsigned gglob = grid_for(n / 4 + 1, 8);
+    int R;
+    if (op == ADC_OP_MUL) {
+        const HistStrategy st = pick_entry(sizeof(T), m, &R);
+        k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(1));
+        if (n > 0) {
+            if (st == kGlobal) {
+                k_prim_mul_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, hist, err);
+            } else {
+                const size_t smem = (size_t)m * sizeof(T) * R;
+                if (cudaFuncSetAttribute(k_prim_mul_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                    cudaSuccess)
+                    return ADC_ERR_CUDA;
+                k_prim_mul_smem<T><<<st == kSmemWarp ? num_sms() * 4 : num_sms(), st == kSmemWarp ? 256 : 1024, smem,
+                                     s>>>(keys, vals, n, m, R, hist, err);
+            }
+        }
+        return check_launch();
+    }
+    const bool mx = op == ADC_OP_MAX;
+    if constexpr (sizeof(T) == 4) {
+        uint32_t *tab = reinterpret_cast<uint32_t *>(w + kWsHeader);
+        const HistStrategy st = pick_entry(4, m, &R);
+        if (mx) k_ord32_init<true><<<gm, 256, 0, s>>>(tab, m);
+        else k_ord32_init<false><<<gm, 256, 0, s>>>(tab, m);
+        if (n > 0) {
+            if (st == kGlobal) {
+                if (mx) k_prim_sel_global<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                else k_prim_sel_global<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+            } else {
+                auto kern = mx ? k_prim_sel_smem<true> : k_prim_sel_smem<false>;
+                const size_t smem = (size_t)m * 4 * R;
+                if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                    return ADC_ERR_CUDA;
+                kern<<<st == kSmemWarp ? num_sms() * 4 : num_sms(), st == kSmemWarp ? 256 : 1024, smem, s>>>(
+                    keys, vals, n, m, R, tab);
+            }
+        }
+        if (mx) k_prim_sel_final<true, float, uint32_t><<<gm, 256, 0, s>>>(tab, h0, m, hist, 0u);
+        else k_prim_sel_final<false, float, uint32_t><<<gm, 256, 0, s>>>(tab, h0, m, hist, 0xffffffffu);
+    } else {
+        unsigned long long *tab = reinterpret_cast<unsigned long long *>(w + kWsHeader);
+        unsigned *ti = reinterpret_cast<unsigned *>(w + kWsHeader + align_up((size_t)m * 8, 256));
+        const unsigned long long empty = mx ? 0ull : ~0ull;
+        k_sel64_init<<<gm, 256, 0, s>>>(tab, ti, m, empty);
+        if (n > 0) {
+            if (mx) k_hist_sel64_value<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+            else k_hist_sel64_value<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+        }
+        if (mx) k_prim_sel_final<true, double, unsigned long long><<<gm, 256, 0, s>>>(tab, h0, m, hist, empty);
+        else k_prim_sel_final<false, double, unsigned long long><<<gm, 256, 0, s>>>(tab, h0, m, hist, empty);
+    }
+    return check_launch();
+}
+
+template <typename T>
+static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0,
+                             T *hist, void *saved, void *ws, cudaStream_t s) {
+    char *w = static_cast<char *>(ws);
+    unsigned *err = reinterpret_cast<unsigned *>(w);
+    int R;
+    const HistStrategy st = pick(op, dt_of<T>(), m, &R);
+    const size_t e = entry_bytes(op, dt_of<T>());
+    const size_t smem = (size_t)m * e * R;
+    const unsigned gm = grid_for(m, 4);
+    const unsigned gsmem = (st == kSmemWarp) ? (unsigned)num_sms() * 4 : (unsigned)num_sms();
+    const unsigned tsmem = (st == kSmemWarp) ? 256 : 1024;
+    const unsigned gglob = grid_for(n / 4 + 1, 8);
+    if (saved == nullptr && op != ADC_OP_ADD) return hist_primal_t<T>(op, n, m, keys, vals, h0, hist, ws, s);
+    switch (op) {
+    case ADC_OP_ADD: {
+        k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(0));
+        if (n == 0) return check_launch();
+        if (st == kGlobal) {
+            k_hist_add_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, hist);
+        } else {
+            if (cudaFuncSetAttribute(k_hist_add_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                cudaSuccess)
+                return ADC_ERR_CUDA;
+            k_hist_add_smem<T><<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, hist);
+        }
+        return check_launch();
+    }
+    case ADC_OP_MUL: {
+        int32_t *n0 = static_cast<int32_t *>(saved);
+        T *p = reinterpret_cast<T *>(static_cast<char *>(saved) + align_up((size_t)m * 4, 16));
+        k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
+        if (n > 0) {
+            if (st == kGlobal) {
+                k_hist_mul_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, n0, p, err);
+            } else {
+                if (cudaFuncSetAttribute(k_hist_mul_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                    cudaSuccess)
+                    return ADC_ERR_CUDA;
+                k_hist_mul_smem<T><<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, n0, p, err);
+            }
+        }
+        k_hist_mul_final<T><<<gm, 256, 0, s>>>(n0, p, h0, m, hist);
+        return check_launch();
+    }
+    case ADC_OP_MIN:
+    case ADC_OP_MAX: {
+        const bool mx = op == ADC_OP_MAX;
+        unsigned long long *tab = reinterpret_cast<unsigned long long *>(w + kWsHeader);
+        int32_t *is = static_cast<int32_t *>(saved);
+        if constexpr (sizeof(T) == 4) {
+            if (mx) k_pack_init<true><<<gm, 256, 0, s>>>(tab, m);
+            else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
+            if (n > 0) {
+                if (st == kGlobal) {
+                    if (mx) k_hist_sel_global<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                    else k_hist_sel_global<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                } else {
+                    auto kern = mx ? k_hist_sel_smem<true> : k_hist_sel_smem<false>;
+                    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+                        cudaSuccess)
+                        return ADC_ERR_CUDA;
+                    kern<<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, tab);
+                }
+            }
+            if (mx) k_hist_sel_final<true><<<gm, 256, 0, s>>>(tab, vals, h0, m, n, hist, is);
+            else k_hist_sel_final<false><<<gm, 256, 0, s>>>(tab, vals, h0, m, n, hist, is);
+        } else {
+            unsigned *ti = reinterpret_cast<unsigned *>(w + kWsHeader + align_up((size_t)m * 8, 256));
+            k_sel64_init<<<gm, 256, 0, s>>>(tab, ti, m, mx ? 0ull : ~0ull);
+            if (n > 0) {
+                if (mx) {
+                    k_hist_sel64_value<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                    k_hist_sel64_index<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab, ti);
+                } else {
+                    k_hist_sel64_value<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                    k_hist_sel64_index<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab, ti);
+                }
+            }
+            if (mx) k_hist_sel64_final<true><<<gm, 256, 0, s>>>(ti, vals, h0, m, n, hist, is);
+            else k_hist_sel64_final<false><<<gm, 256, 0, s>>>(ti, vals, h0, m, n, hist, is);
+        }
+        return check_launch();
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+adc_status hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                    const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s) {
+    if (op == ADC_OP_LIN) return histgen_fwd(dt, n, m, keys, vals, hist0, hist, saved, ws, s);
+    if (dt == ADC_F64)
+        return hist_fwd_t<double>(op, n, m, keys, static_cast<const double *>(vals), static_cast<const double *>(hist0),
+                                  static_cast<double *>(hist), saved, ws, s);
+    return hist_fwd_t<float>(op, n, m, keys, static_cast<const float *>(vals), static_cast<const float *>(hist0),
+                             static_cast<float *>(hist), saved, ws, s);
+}
+
+template <typename T>
+static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0,
+                             const void *saved, const T *hb, T *vb, T *h0b, int acc, cudaStream_t s) {
+    const unsigned gm = grid_for(m, 4);
+    const unsigned gn = grid_for(n / 4 + 1, 8);
+    switch (op) {
+    case ADC_OP_ADD:
+        if (n > 0) k_hist_add_vjp<T><<<gn, 256, 0, s>>>(keys, hb, vb, n, m, acc);
+        if (h0b) k_h0bar_add<T><<<gm, 256, 0, s>>>(hb, h0b, m, acc);
+        return check_launch();
+    case ADC_OP_MIN:
+    case ADC_OP_MAX:
+        if (!acc && n > 0) k_fill<T><<<grid_for(n / 4 + 1, 8), 256, 0, s>>>(vb, n);
+        k_hist_sel_vjp<T><<<gm, 256, 0, s>>>(static_cast<const int32_t *>(saved), hb, vb, h0b, m, n, acc);
+        return check_launch();
+    case ADC_OP_MUL: {
+        const int32_t *n0 = static_cast<const int32_t *>(saved);
+        const T *p = reinterpret_cast<const T *>(static_cast<const char *>(saved) + align_up((size_t)m * 4, 16));
+        if (n > 0) k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, n0, p, h0, hb, vb, n, m, acc);
+        if (h0b) k_h0bar_mul<T><<<gm, 256, 0, s>>>(n0, p, hb, h0b, m, acc);
+        return check_launch();
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                    const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
+                    void *hist0bar, int accumulate, void *ws, cudaStream_t s) {
+    if (op == ADC_OP_LIN)
+        return histgen_vjp(dt, n, m, keys, vals, hist0, hist, saved, histbar, valsbar, hist0bar, accumulate, ws, s);
+    (void)hist;
+    (void)ws;
+    if (dt == ADC_F64)
+        return hist_vjp_t<double>(op, n, m, keys, static_cast<const double *>(vals),
+                                  static_cast<const double *>(hist0), saved, static_cast<const double *>(histbar),
+                                  static_cast<double *>(valsbar), static_cast<double *>(hist0bar), accumulate, s);
+    return hist_vjp_t<float>(op, n, m, keys, static_cast<const float *>(vals), static_cast<const float *>(hist0), saved,
+                             static_cast<const float *>(histbar), static_cast<float *>(valsbar),
+                             static_cast<float *>(hist0bar), accumulate, s);
+}
+
+}  // namespace adc
+
+extern "C" void adc_debug_force_hist_strategy(int s) { adc::g_force_strategy = s; }

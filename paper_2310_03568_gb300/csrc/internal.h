@@ -1,0 +1,65 @@
+// Host-side internals shared by the libadcomb translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/adcomb.h"
+
+namespace adc {
+
+struct DevCtl;
+
+// Workspace header, zeroed by every entry point before it queues work:
+// [0] device error word, [4 + 4*slot] one counter per launch of the call.
+constexpr size_t kWsHeader = 256;
+constexpr int kMaxSlots = 48;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+DevCtl make_ctl(void *ws, int slot);
+inline unsigned *counter_slot(void *ws, int slot) {
+    return reinterpret_cast<unsigned *>(static_cast<char *>(ws) + 4 + 4 * slot);
+}
+int num_sms();
+
+// Returns ADC_ERR_CUDA if the last launch failed.
+adc_status check_launch();
+
+inline int arity(adc_op op) { return op == ADC_OP_LIN ? 2 : (op == ADC_OP_MM2 ? 4 : 1); }
+inline size_t elem_bytes(adc_op op, adc_dtype dt) { return (size_t)arity(op) * (dt == ADC_F64 ? 8 : 4); }
+
+// scan.cu
+size_t scan_ws_bytes(adc_op op, adc_dtype dt, int64_t n);
+adc_status scan_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *ws, cudaStream_t s);
+adc_status scan_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *ybar,
+                    void *xbar, int accumulate, void *ws, cudaStream_t s);
+
+// reduce.cu
+size_t reduce_ws_bytes(adc_op op, adc_dtype dt, int64_t n);
+size_t reduce_saved_bytes(adc_op op, adc_dtype dt, int64_t n);
+adc_status reduce_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *saved, void *ws,
+                      cudaStream_t s);
+adc_status reduce_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *saved,
+                      const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s);
+
+// hist.cu
+size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m);
+size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m);
+adc_status hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                    const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s);
+adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                    const void *hist0, const void *hist, const void *saved, const void *histbar,
+                    void *valsbar, void *hist0bar, int accumulate, void *ws, cudaStream_t s);
+
+// sort.cu (general reduce_by_index through a stable radix sort)
+size_t histgen_ws_bytes(adc_dtype dt, int64_t n, int64_t m);
+size_t histgen_saved_bytes(adc_dtype dt, int64_t n, int64_t m);
+adc_status histgen_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                       const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s);
+adc_status histgen_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                       const void *hist0, const void *hist, const void *saved, const void *histbar,
+                       void *valsbar, void *hist0bar, int accumulate, void *ws, cudaStream_t s);
+
+}  // namespace adc

@@ -1,0 +1,310 @@
+// Scan forward passes (Sec. 5.1) and their vjps (Fig. 7 with the RBDS
+// specialisation of Sec. 5.3.4), each one decoupled-look-back launch.
+//
+// vjp: the backward recurrence lambda_i = ybar_i + lambda_{i+1} * J_{i+1} with
+// J_{i+1} = d(y_i . x_{i+1}) / d y_i is solved as a reverse scan whose element
+// is the affine map f_i(lambda) = ybar_i + lambda * J_{i+1} and whose operator
+// is composition -- the paper's lin_o of Fig. 7, written in the order the
+// reverse scan consumes elements.  The final map
+// xbar_i = d(y_{i-1} . x_i)/dx_i ^T lambda_i (y_{-1} = e) is fused into the
+// store, so a vjp reads x, y, ybar once and writes xbar once.
+#include "common.cuh"
+#include "internal.h"
+#include "scan_engine.cuh"
+#include "tile_io.cuh"
+
+namespace adc {
+
+struct NoAux {};
+
+// ------------------------------------------------------------ forward ops --
+template <typename T, int ITEMS> struct FwdAdd {
+    using State = T;
+    using Aux = NoAux;
+    const T *x;
+    T *y;
+    __device__ T identity() const { return T(0); }
+    __device__ T combine(T a, T b) const { return a + b; }
+    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, T(0)); }
+    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+};
+
+template <typename T, int ITEMS> struct FwdMul {
+    using State = T;
+    using Aux = NoAux;
+    const T *x;
+    T *y;
+    __device__ T identity() const { return T(1); }
+    __device__ T combine(T a, T b) const { return a * b; }
+    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, T(1)); }
+    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+};
+
+// linFnComp (Fig. 8): (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)
+template <typename T, int ITEMS> struct FwdLin {
+    using State = Pair<T>;
+    using Aux = NoAux;
+    const Pair<T> *x;
+    Pair<T> *y;
+    __device__ State identity() const { return {T(0), T(1)}; }
+    __device__ State combine(const State &a, const State &b) const { return {b.b + b.c * a.b, b.c * a.c}; }
+    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, identity()); }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+};
+
+template <typename T, int ITEMS> struct FwdMM2 {
+    using State = Mat2<T>;
+    using Aux = NoAux;
+    const Mat2<T> *x;
+    Mat2<T> *y;
+    __device__ State identity() const { return mat_eye<T>(); }
+    __device__ State combine(const State &a, const State &b) const { return mat_mul(a, b); }
+    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, identity()); }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+};
+
+// ---------------------------------------------------------------- vjp ops --
+// Sec. 5.3.1: the adjoint of a +-scan is a reverse +-scan of ybar.
+template <typename T, int ITEMS> struct VjpAdd {
+    using State = T;
+    using Aux = NoAux;
+    const T *ybar;
+    T *xbar;
+    int accumulate;
+    __device__ T identity() const { return T(0); }
+    __device__ T combine(T a, T b) const { return a + b; }
+    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(ybar, c0, n, st, T(0)); }
+    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const {
+        if (accumulate) {
+            T old[ITEMS], out[ITEMS];
+            load_chunk(xbar, c0, n, old, T(0));
+#pragma unroll
+            for (int k = 0; k < ITEMS; ++k) out[k] = old[k] + st[k];
+            store_chunk(xbar, c0, n, out);
+        } else {
+            store_chunk(xbar, c0, n, st);
+        }
+    }
+};
+
+// Affine map lambda -> v + c * lambda with a scalar (RBDS, q = 1) coefficient.
+template <typename T> struct AffS { T v, c; };
+template <typename T> struct AffP { T vb, vc, c; };  // 2-vector value (lin)
+
+// Fetch the coefficient source x_{i+1} for every element of the chunk:
+// xs[k] = x[c0 + k + 1] (identity beyond n).
+template <typename E, int ITEMS>
+__device__ __forceinline__ void load_next(const E *x, int64_t c0, int64_t n, E (&xs)[ITEMS], E fill) {
+    E raw[ITEMS];
+    load_chunk(x, c0, n, raw, fill);
+#pragma unroll
+    for (int k = 0; k + 1 < ITEMS; ++k) xs[k] = raw[k + 1];
+    xs[ITEMS - 1] = (c0 + ITEMS < n) ? x[c0 + ITEMS] : fill;
+}
+
+// Fetch y_{i-1} for every element: ys[k] = y[c0 + k - 1], y_{-1} = e.
+template <typename E, int ITEMS>
+__device__ __forceinline__ void load_prev(const E *y, int64_t c0, int64_t n, E (&ys)[ITEMS], E e) {
+    E raw[ITEMS];
+    load_chunk(y, c0, n, raw, e);
+#pragma unroll
+    for (int k = ITEMS - 1; k > 0; --k) ys[k] = raw[k - 1];
+    ys[0] = (c0 > 0 && c0 - 1 < n) ? y[c0 - 1] : e;
+}
+
+// Product scan: J_{i+1} = x_{i+1}; xbar_i = y_{i-1} * lambda_i.
+template <typename T, int ITEMS> struct VjpMul {
+    using State = AffS<T>;
+    struct Aux { T yprev[ITEMS]; };
+    const T *x, *y, *ybar;
+    T *xbar;
+    int accumulate;
+    __device__ State identity() const { return {T(0), T(1)}; }
+    __device__ State combine(const State &acc, const State &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
+    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
+        T yb[ITEMS], xn[ITEMS];
+        load_chunk(ybar, c0, n, yb, T(0));
+        load_next(x, c0, n, xn, T(1));
+        load_prev(y, c0, n, aux.yprev, T(1));
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k], xn[k]} : identity();
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        T out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, T(0));
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) out[k] = (accumulate ? out[k] : T(0)) + aux.yprev[k] * st[k].v;
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
+// linFnComp scan: J = diag(c_{i+1}, c_{i+1}) (Sec. 5.3.4);
+// bbar_i = lambda.b, cbar_i = lambda.b * B_{i-1} + lambda.c * C_{i-1}, (B,C)_{-1} = (0,1).
+template <typename T, int ITEMS> struct VjpLin {
+    using State = AffP<T>;
+    struct Aux { Pair<T> yprev[ITEMS]; };
+    const Pair<T> *x, *y, *ybar;
+    Pair<T> *xbar;
+    int accumulate;
+    __device__ State identity() const { return {T(0), T(0), T(1)}; }
+    __device__ State combine(const State &acc, const State &e) const {
+        return {e.vb + e.c * acc.vb, e.vc + e.c * acc.vc, e.c * acc.c};
+    }
+    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
+        Pair<T> yb[ITEMS], xn[ITEMS];
+        const Pair<T> e{T(0), T(1)};
+        load_chunk(ybar, c0, n, yb, Pair<T>{T(0), T(0)});
+        load_next(x, c0, n, xn, e);
+        load_prev(y, c0, n, aux.yprev, e);
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k].b, yb[k].c, xn[k].c} : identity();
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        Pair<T> out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, Pair<T>{T(0), T(0)});
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const T gb = st[k].vb;
+            const T gc = gb * aux.yprev[k].b + st[k].vc * aux.yprev[k].c;
+            out[k] = accumulate ? Pair<T>{out[k].b + gb, out[k].c + gc} : Pair<T>{gb, gc};
+        }
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
+// 2x2 matrix-product scan: f_i(L) = Ybar_i + L * M_{i+1}^T;  Mbar_i = P_{i-1}^T * lambda_i, P_{-1} = I.
+template <typename T> struct AffM { Mat2<T> v, c; };
+
+template <typename T, int ITEMS> struct VjpMM2 {
+    using State = AffM<T>;
+    struct Aux { Mat2<T> yprev[ITEMS]; };
+    const Mat2<T> *x, *y, *ybar;
+    Mat2<T> *xbar;
+    int accumulate;
+    __device__ State identity() const { return {mat_zero<T>(), mat_eye<T>()}; }
+    __device__ State combine(const State &acc, const State &e) const {
+        return {mat_add(e.v, mat_mul(acc.v, e.c)), mat_mul(acc.c, e.c)};
+    }
+    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
+        Mat2<T> yb[ITEMS], xn[ITEMS];
+        load_chunk(ybar, c0, n, yb, mat_zero<T>());
+        load_next(x, c0, n, xn, mat_eye<T>());
+        load_prev(y, c0, n, aux.yprev, mat_eye<T>());
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k], mat_t(xn[k])} : identity();
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        Mat2<T> out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, mat_zero<T>());
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const Mat2<T> g = mat_mul(mat_t(aux.yprev[k]), st[k].v);
+            out[k] = accumulate ? mat_add(out[k], g) : g;
+        }
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
+// -------------------------------------------------------------- launching --
+// Items per thread: 64 bytes of each streamed array per thread.
+template <typename T> struct Items {
+    static constexpr int scalar = 64 / sizeof(T);       // add / mul
+    static constexpr int pair = 64 / (2 * sizeof(T));   // lin
+    static constexpr int mat = 64 / (4 * sizeof(T));    // mm2
+    static constexpr int vscalar = 32 / sizeof(T);      // vjp mul
+    static constexpr int vpair = 32 / (2 * sizeof(T));  // vjp lin
+    static constexpr int vmat = 2;                      // vjp mm2
+};
+
+template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
+    using I = Items<T>;
+    size_t a = 0, b = 0;
+    switch (op) {
+    case ADC_OP_ADD:
+        a = ScanShape<FwdAdd<T, I::scalar>, I::scalar>::region(n);
+        b = ScanShape<VjpAdd<T, I::scalar>, I::scalar>::region(n);
+        break;
+    case ADC_OP_MUL:
+        a = ScanShape<FwdMul<T, I::scalar>, I::scalar>::region(n);
+        b = ScanShape<VjpMul<T, I::vscalar>, I::vscalar>::region(n);
+        break;
+    case ADC_OP_LIN:
+        a = ScanShape<FwdLin<T, I::pair>, I::pair>::region(n);
+        b = ScanShape<VjpLin<T, I::vpair>, I::vpair>::region(n);
+        break;
+    case ADC_OP_MM2:
+        a = ScanShape<FwdMM2<T, I::mat>, I::mat>::region(n);
+        b = ScanShape<VjpMM2<T, I::vmat>, I::vmat>::region(n);
+        break;
+    default: return 0;
+    }
+    return kWsHeader + (a > b ? a : b);
+}
+
+size_t scan_ws_bytes(adc_op op, adc_dtype dt, int64_t n) {
+    return dt == ADC_F64 ? scan_ws_t<double>(op, n) : scan_ws_t<float>(op, n);
+}
+
+template <typename T>
+static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
+    using I = Items<T>;
+    switch (op) {
+    case ADC_OP_ADD: {
+        FwdAdd<T, I::scalar> o{static_cast<const T *>(x), static_cast<T *>(y)};
+        return run_scan<decltype(o), I::scalar, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_MUL: {
+        FwdMul<T, I::scalar> o{static_cast<const T *>(x), static_cast<T *>(y)};
+        return run_scan<decltype(o), I::scalar, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_LIN: {
+        FwdLin<T, I::pair> o{static_cast<const Pair<T> *>(x), static_cast<Pair<T> *>(y)};
+        return run_scan<decltype(o), I::pair, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_MM2: {
+        FwdMM2<T, I::mat> o{static_cast<const Mat2<T> *>(x), static_cast<Mat2<T> *>(y)};
+        return run_scan<decltype(o), I::mat, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+adc_status scan_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
+    return dt == ADC_F64 ? scan_fwd_t<double>(op, n, x, y, ws, s) : scan_fwd_t<float>(op, n, x, y, ws, s);
+}
+
+template <typename T>
+static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y, const void *ybar, void *xbar,
+                             int acc, void *ws, cudaStream_t s) {
+    using I = Items<T>;
+    switch (op) {
+    case ADC_OP_ADD: {
+        VjpAdd<T, I::scalar> o{static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return run_scan<decltype(o), I::scalar, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_MUL: {
+        VjpMul<T, I::vscalar> o{static_cast<const T *>(x), static_cast<const T *>(y), static_cast<const T *>(ybar),
+                                static_cast<T *>(xbar), acc};
+        return run_scan<decltype(o), I::vscalar, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_LIN: {
+        VjpLin<T, I::vpair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
+                              static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
+        return run_scan<decltype(o), I::vpair, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    case ADC_OP_MM2: {
+        VjpMM2<T, I::vmat> o{static_cast<const Mat2<T> *>(x), static_cast<const Mat2<T> *>(y),
+                             static_cast<const Mat2<T> *>(ybar), static_cast<Mat2<T> *>(xbar), acc};
+        return run_scan<decltype(o), I::vmat, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+adc_status scan_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *ybar, void *xbar,
+                    int accumulate, void *ws, cudaStream_t s) {
+    return dt == ADC_F64 ? scan_vjp_t<double>(op, n, x, y, ybar, xbar, accumulate, ws, s)
+                         : scan_vjp_t<float>(op, n, x, y, ybar, xbar, accumulate, ws, s);
+}
+
+}  // namespace adc

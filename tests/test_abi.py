@@ -1,0 +1,76 @@
+"""CPU-only checks of the C ABI: the library builds and loads, exports every
+symbol include/adcomb.h declares, and rejects bad arguments on the host
+before queueing any device work (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2310_03568_gb300 import adcomb
+from paper_2310_03568_gb300.build import build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "adcomb.h")
+
+
+@pytest.fixture(scope="module")
+def L():
+    build()
+    return adcomb.lib()
+
+
+def declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(adc_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 14
+    raw = ctypes.CDLL(adcomb.LIB_PATH)
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert not missing, missing
+
+
+def test_status_strings(L):
+    assert adcomb.status_string(0) == "ok"
+    assert "timeout" in adcomb.status_string(5) or "expired" in adcomb.status_string(5)
+    assert "sm_103a" in adcomb.version()
+
+
+def test_size_queries(L):
+    f32 = 0
+    assert L.adc_workspace_bytes(1, 0, f32, 1000, 0) >= 256          # scan +
+    assert L.adc_workspace_bytes(1, 2, f32, 1000, 0) == 0            # scan min: unsupported
+    assert L.adc_workspace_bytes(2, 5, f32, 1000, 10) == 0           # hist mm2: unsupported
+    assert L.adc_workspace_bytes(2, 0, f32, 1000, 0) == 0            # hist with m = 0
+    assert L.adc_saved_bytes(2, 2, f32, 1000, 77) >= 77 * 4          # hist min: is[m]
+    assert L.adc_saved_bytes(2, 1, f32, 1000, 77) >= 77 * 8          # hist *: n0[m], p[m]
+    assert L.adc_saved_bytes(2, 4, f32, 1000, 77) >= 1000 * 16       # hist lin: perm, keys, values
+    assert L.adc_saved_bytes(0, 5, f32, 10 ** 6, 0) > 0              # reduce mm2: tile prefixes
+
+
+def test_host_validation_rejects_before_any_device_work(L):
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation first
+    ws_small = 8
+    # bad enums, negative sizes
+    assert L.adc_scan_fwd(9, 0, 10, fake, fake, fake, 1 << 20, None) == 1
+    assert L.adc_scan_fwd(0, 7, 10, fake, fake, fake, 1 << 20, None) == 1
+    assert L.adc_scan_fwd(0, 0, -1, fake, fake, fake, 1 << 20, None) == 1
+    # unsupported operator / combinator pairs
+    assert L.adc_scan_fwd(2, 0, 10, fake, fake, fake, 1 << 20, None) == 2
+    assert L.adc_hist_fwd(5, 0, 10, 4, fake, fake, None, fake, fake, fake, 1 << 20, None) == 2
+    # null / misaligned arrays
+    assert L.adc_scan_fwd(0, 0, 10, None, fake, fake, 1 << 20, None) == 1
+    assert L.adc_scan_fwd(0, 0, 10, ctypes.c_void_p((1 << 20) + 4), fake, fake, 1 << 20, None) == 1
+    assert L.adc_reduce_fwd(2, 0, 10, fake, fake, None, fake, 1 << 20, None) == 1   # min needs `saved`
+    # histogram bounds
+    assert L.adc_hist_fwd(0, 0, 10, 0, fake, fake, None, fake, None, fake, 1 << 20, None) == 1
+    assert L.adc_hist_fwd(0, 0, 1 << 31, 5, fake, fake, None, fake, None, fake, 1 << 40, None) == 1
+    # workspace too small is reported, not overrun
+    assert L.adc_scan_fwd(0, 0, 10 ** 6, fake, fake, fake, ws_small, None) == 3
+    assert L.adc_hist_fwd(2, 0, 1000, 100, fake, fake, None, fake, fake, fake, ws_small, None) == 3
+    # workspace must be 256-byte aligned
+    assert L.adc_scan_fwd(0, 0, 10, fake, fake, ctypes.c_void_p((1 << 20) + 16), 1 << 20, None) == 1
