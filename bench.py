@@ -45,7 +45,7 @@ LAUNCHES = {("fwd", "mul"): 3, ("vjp", "mul"): 1, ("fwd", "min"): 3, ("vjp", "mi
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=100)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=N, help="elements per instance (default: the full 50M)")
