@@ -136,6 +136,31 @@ adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, co
                         const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes,
                         void *stream);
 
+/*
+ * adc_scan_fwd, for callers that cannot allocate device memory -- for example
+ * code running inside an allocator or memory-pool callback (where cudaMalloc
+ * would re-enter the allocator), or a plugin handed only fixed input and
+ * output buffers.  The paper has no counterpart: this is a packaging of the
+ * same scan kernel whose look-back scratch lives in a file-scope device array
+ * of 4 MiB held by every GPU that loads the library until the process exits.
+ * Same operators, layouts and results as adc_scan_fwd; nothing is allocated
+ * or freed.
+ *   Limit : n must satisfy adc_workspace_bytes(ADC_SCAN, op, dtype, n, 0) <= 4 MiB
+ *           (about 1.4e9 fp32 + elements, 4.2e8 fp32 *, 1.5e8 fp32 lin,
+ *           3.1e7 fp32 mm2, 1.6e7 fp64 mm2); larger n returns
+ *           ADC_ERR_WORKSPACE before any work is queued.
+ *   Set-up: the first call on a device, with that device current, looks up the
+ *           array's device address; make that first call before capturing a
+ *           stream.
+ *   Sharing: all calls on a device use the same array, which keeps the last
+ *           call's contents; each call clears what must start at zero.  Calls
+ *           that may overlap on the GPU race and must not be issued.
+ *   A bounded device wait that expires leaves y incomplete; this entry point
+ *   cannot report it (it does not synchronise).
+ */
+adc_status adc_scan_fwd_noalloc(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
+                                void *stream);
+
 /* ------------------------------------------------------- reduce_by_index --
  * hist = reduce_by_index hist0 (.) e keys vals                    (Sec. 4)
  *   keys : [n] int32, vals : [n] elements, hist0 : [m] elements or NULL for the

@@ -55,6 +55,7 @@ def lib():
                 "adc_reduce_vjp": ([i32, i32, i64, p, p, p, p, p, i32, p, sz, p], i32),
                 "adc_scan_fwd": ([i32, i32, i64, p, p, p, sz, p], i32),
                 "adc_scan_vjp": ([i32, i32, i64, p, p, p, p, i32, p, sz, p], i32),
+                "adc_scan_fwd_noalloc": ([i32, i32, i64, p, p, p], i32),
                 "adc_hist_fwd": ([i32, i32, i64, i64, p, p, p, p, p, p, sz, p], i32),
                 "adc_hist_vjp": ([i32, i32, i64, i64, p, p, p, p, p, p, p, p, i32, p, sz, p], i32),
                 "adc_check_device_error": ([p, sz, p], i32),
@@ -167,6 +168,16 @@ def scan_fwd(op, x, y=None, ws=None, stream=None):
         y = torch.empty_like(x)
     w, wb = _ws("scan", op, x, n, 0, ws)
     _check("adc_scan_fwd", lib().adc_scan_fwd(OPS[op], _dt(x), n, _ptr(x), _ptr(y), _ptr(w), wb, _stream(stream)))
+    return y
+
+
+def scan_fwd_noalloc(op, x, y=None, stream=None):
+    """scan_fwd without caller scratch: for callers that cannot allocate (the
+    library keeps the scratch in a fixed 4 MiB device array; see the header)."""
+    n = x.shape[0]
+    if y is None:
+        y = torch.empty_like(x)
+    _check("adc_scan_fwd_noalloc", lib().adc_scan_fwd_noalloc(OPS[op], _dt(x), n, _ptr(x), _ptr(y), _stream(stream)))
     return y
 
 
