@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--n", type=int, default=N, help="elements per instance (default: the full 50M)")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--kernels", action="store_true",
+                   help="instead of the bench line: per-kernel achieved bandwidth at full sizes (markdown)")
     return p.parse_args()
 
 
@@ -251,6 +254,12 @@ def run_ours(args, world, rank, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(n, keys_h, vals_h, hbar_h)
 
+    del keys, vals, vbar
+    torch.cuda.empty_cache()
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(dev)
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
@@ -267,6 +276,7 @@ def run_ours(args, world, rank, local):
             "per_call_ms": {f"{op}/{m}/{ph}": round(v, 4) for (op, m, ph), v in call_ms.items()},
             "primal_ms": {f"{op}/{m}": round(statistics.mean(v), 4) for (op, m, _), v in prim_ms.items()},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "batched": batched,
         }
         print(json.dumps(line))
     if world > 1:
@@ -319,6 +329,121 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
     ms = a.elapsed_time(b) / steps
     return {"value": world * len(BINS) * len(OPS) * n / (ms * 1e-3), "unit": "elements/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+
+
+def run_batched(dev, seed=4):
+    """4096 hist -> +-scan -> sum instances (n_i, m_i log-uniform): forward + vjp
+    as two replayed CUDA graphs of the batched entry points, against the same
+    work through the single-instance entry points (several launches per
+    instance).  Reported beside the bench line; not part of its step."""
+    import torch
+
+    from paper_2310_03568_gb300 import batched as B
+    from paper_2310_03568_gb300 import synth
+    w = synth.batched(seed=seed)
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals, device=dev)
+    for _ in range(3):
+        p.replay_forward()
+        p.replay_backward()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record()
+    for _ in range(reps):
+        p.replay_forward()
+        p.replay_backward()
+    b.record()
+    torch.cuda.synchronize()
+    ms_batched = a.elapsed_time(b) / reps
+    vb = p.valsbar.clone()
+    B.per_instance_loss(desc, p.keys, p.vals)  # warm-up
+    torch.cuda.synchronize()
+    a.record()
+    loss_pi, vb_pi = B.per_instance_loss(desc, p.keys, p.vals)
+    b.record()
+    torch.cuda.synchronize()
+    ms_pi = a.elapsed_time(b)
+    same = bool(torch.equal(vb, vb_pi))
+    total = int(desc["n"].sum())
+    return {"instances": int(len(desc)), "values": total, "bins": int(desc["m"].sum()),
+            "batched_graph_ms": ms_batched, "per_instance_ms": ms_pi, "speedup": ms_pi / ms_batched,
+            "batched_values_per_s": total / (ms_batched * 1e-3), "gradients_bit_identical": same,
+            "loss_batched": float(p.loss.item()), "loss_per_instance": float(loss_pi.item())}
+
+
+# --------------------------------------------------------- kernel rooflines ----
+def run_kernels(args):
+    """Achieved bandwidth of every kernel family at full size (CUDA events, inputs
+    larger than L2, 3 warm-ups, mean of 10).  Prints a markdown table."""
+    import torch
+
+    from paper_2310_03568_gb300 import adcomb, synth
+    from paper_2310_03568_gb300.build import build
+    build()
+    peak, kind = read_peaks()
+    dev = torch.device("cuda", 0)
+    g = np.random.default_rng(0)
+    rows = []
+
+    def timeit(fn, reps=10):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def row(name, n, nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        rows.append((name, n, nbytes, ms, gbs, gbs / peak))
+
+    ws = adcomb.Workspace()
+    for op, dt, n in [("add", np.float32, 100_000_000), ("mul", np.float32, 100_000_000),
+                      ("lin", np.float32, 100_000_000), ("mm2", np.float32, 10_000_000),
+                      ("add", np.float64, 10_000_000), ("mul", np.float64, 10_000_000),
+                      ("lin", np.float64, 10_000_000)]:
+        x = torch.from_numpy(synth.scan_values(g, op, n, dt)).to(dev)
+        es = x.element_size() * (x.numel() // n)
+        y = adcomb.scan_fwd(op, x, ws=ws)
+        yb = torch.randn_like(x)
+        xb = torch.empty_like(x)
+        row(f"scan {op} fwd {np.dtype(dt).name}", n, 2 * n * es, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
+        vb_bytes = (2 if op == "add" else 4) * n * es
+        row(f"scan {op} vjp {np.dtype(dt).name}", n, vb_bytes,
+            timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        del x, y, yb, xb
+    for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000)]:
+        x = torch.from_numpy(synth.scan_values(g, "mm2_orth" if op == "mm2" else "add", n)).to(dev)
+        if op == "mul":
+            x = x * 0.05 + 1.0
+        es = x.element_size() * (x.numel() // n)
+        y, saved = adcomb.reduce_fwd(op, x, ws=ws)
+        yb = torch.ones_like(y)
+        xb = torch.empty_like(x)
+        row(f"reduce {op} fwd", n, n * es, timeit(lambda: adcomb.reduce_fwd(op, x, y, saved, ws=ws)))
+        vjp_bytes = {"add": n * es, "min": n * es, "mul": 2 * n * es, "mm2": 2 * n * es}[op]
+        row(f"reduce {op} vjp", n, vjp_bytes, timeit(lambda: adcomb.reduce_vjp(op, x, y, saved, yb, xbar=xb, ws=ws)))
+        del x, xb
+    for op, n, m in [("add", 100_000_000, 1000), ("add", 50_000_000, 10_000_000), ("lin", 10_000_000, 1000)]:
+        k = torch.randint(0, m, (n,), dtype=torch.int32, device=dev)
+        v = torch.from_numpy(synth.scan_values(g, op, n)).to(dev)
+        es = v.element_size() * (v.numel() // n)
+        h, saved = adcomb.hist_fwd(op, m, k, v, ws=ws)
+        hb = torch.randn_like(h)
+        vb = torch.empty_like(v)
+        row(f"hist {op} fwd m={m}", n, n * (4 + es), timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
+        row(f"hist {op} vjp m={m}", n, n * (4 + es),
+            timeit(lambda: adcomb.hist_vjp(op, m, k, v, None, h, saved, hb, valsbar=vb, ws=ws)))
+        del k, v, vb
+    print(f"| kernel | n | algorithmic bytes | ms | GB/s | frac of {kind} {peak:.0f} GB/s |")
+    print("|---|---|---|---|---|---|")
+    for name, n, nb, ms, gbs, fr in rows:
+        print(f"| {name} | {n:.3g} | {nb / 1e6:.0f} MB | {ms:.4f} | {gbs:.0f} | {fr:.2f} |")
 
 
 # ------------------------------------------------------------ cpu oracle ----
@@ -375,6 +500,8 @@ def main():
     world, rank, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.kernels:
+        run_kernels(args)
     else:
         run_ours(args, world, rank, local)
 

@@ -200,6 +200,75 @@ adc_status adc_hist_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t m, const 
                         const void *histbar, void *valsbar, void *hist0bar, int accumulate,
                         void *ws, size_t ws_bytes, void *stream);
 
+/* --------------------------------------------------------------- batched --
+ * Many independent instances of  loss = sum_j scan(+)(hist)_j  with
+ * hist = reduce_by_index (replicate m 0) (op) keys vals, op in {ADD, MAX}
+ * (Sec. 4's definition with an all-zero initial histogram, Sec. 5.1's scan and a
+ * +-reduce), evaluated for all instances together in a few persistent launches
+ * instead of several launches per instance.  The vjp chains the specialised
+ * rules: the adjoint of the sum is a broadcast (Sec. 3.2.1), of the +-scan a
+ * reverse +-scan (Sec. 5.3.1), then the gather (Sec. 4.2.1) or the argmax
+ * scatter (Fig. 5).
+ *
+ * Instances are described by adc_instance records.  Keys and values of all
+ * instances are concatenated (instance i owns [val_off, val_off + n)); bins
+ * likewise ([bin_off, bin_off + m) of hist / scan / is / histbar).  Work is cut
+ * into adc_work items (an instance's element range) by adc_batched_plan on the
+ * host; the device copy of both tables is passed to the kernels.
+ */
+typedef struct {
+    int64_t n;        /* values of the instance (< 2^31)                        */
+    int64_t m;        /* bins (1 <= m < 2^31)                                   */
+    int64_t val_off;  /* offset of its first key / value                        */
+    int64_t bin_off;  /* offset of its first bin                                */
+    int32_t op;       /* ADC_OP_ADD or ADC_OP_MAX                                */
+    int32_t pad;
+} adc_instance;
+
+typedef struct {
+    int32_t inst;     /* instance index                                         */
+    int32_t pad;
+    int64_t start;    /* first element, relative to the instance                */
+    int64_t len;      /* number of elements                                     */
+} adc_work;
+
+/*
+ * Host-only planning: cuts every instance into items of at most `chunk`
+ * elements (largest instances first).  Writes up to `capacity` items to
+ * `items` (host memory, may be NULL to count) and returns the number of items,
+ * or -1 on invalid arguments.
+ */
+int64_t adc_batched_plan(const adc_instance *desc, int32_t count, int64_t chunk, adc_work *items,
+                         int64_t capacity);
+
+/* Workspace bytes for the batched calls (total_bins = sum of m). */
+size_t adc_batched_workspace_bytes(int32_t count, int64_t total_bins);
+
+/*
+ * Forward: hist (fp32, [total_bins]), scan (fp32, [total_bins], the inclusive
+ * +-scan of each instance's histogram), is (int32, [total_bins]: for MAX
+ * instances the selected element's index within the instance, n when the zero
+ * initial value won or the bin is empty; unused for ADD), loss_parts (fp32,
+ * [count]) and loss (fp32, one value).  desc and items are DEVICE copies.
+ * smem_bins: shared-memory table size per block in bins (the instances with
+ * more bins use global atomics); 0 picks the default.
+ */
+adc_status adc_batched_hist_scan_fwd(const adc_instance *desc, int32_t count, const adc_work *items,
+                                     int64_t n_items, int64_t total_bins, const int32_t *keys,
+                                     const float *vals, float *hist, float *scan, int32_t *is,
+                                     float *loss_parts, float *loss, int32_t smem_bins, void *ws,
+                                     size_t ws_bytes, void *stream);
+
+/*
+ * vjp w.r.t. the values given the loss adjoint (one fp32 value in device
+ * memory): valsbar (fp32, [total values]); histbar (fp32, [total_bins]) receives
+ * the histogram adjoints on the way.  is comes from the forward call.
+ */
+adc_status adc_batched_hist_scan_vjp(const adc_instance *desc, int32_t count, const adc_work *items,
+                                     int64_t n_items, int64_t total_bins, const int32_t *keys,
+                                     const int32_t *is, const float *loss_bar, float *histbar,
+                                     float *valsbar, void *ws, size_t ws_bytes, void *stream);
+
 /* ----------------------------------------------------------- diagnostics --
  * Waits for `stream`, reads the workspace's device error word and returns
  * ADC_OK or the recorded error (ADC_ERR_TIMEOUT).  This call synchronises.

@@ -29,7 +29,7 @@
 
 namespace adc {
 
-enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2 };
+enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3 };
 
 // ------------------------------------------------------------ element loop --
 // Calls f(key, value, index) for every element, grid-stride over 4-element
@@ -70,6 +70,98 @@ __device__ __forceinline__ void for_each_elem(const int32_t *__restrict__ keys, 
 }
 
 __device__ __forceinline__ bool in_range(int32_t k, int64_t m) { return (uint32_t)k < (uint64_t)m; }
+
+// Same traversal, but hands the callback groups of up to 8 elements so that
+// it can keep 8 independent global atomics in flight.
+template <typename T, class F8>
+__device__ __forceinline__ void for_each_batch(const int32_t *__restrict__ keys, const T *__restrict__ vals,
+                                               const int64_t n, F8 &&f) {
+    const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t nv = n / 4;
+    int64_t v = gtid;
+    int32_t kk[8];
+    T vv[8];
+    int64_t ii[8];
+    for (; v + stride < nv; v += 2 * stride) {
+        const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        const int4 k1 = __ldcs(reinterpret_cast<const int4 *>(keys) + v + stride);
+        T a[4], b[4];
+        load_chunk(vals, v * 4, n, a, T(0));
+        load_chunk(vals, (v + stride) * 4, n, b, T(0));
+        kk[0] = k0.x; kk[1] = k0.y; kk[2] = k0.z; kk[3] = k0.w;
+        kk[4] = k1.x; kk[5] = k1.y; kk[6] = k1.z; kk[7] = k1.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vv[j] = a[j];
+            vv[4 + j] = b[j];
+            ii[j] = 4 * v + j;
+            ii[4 + j] = 4 * (v + stride) + j;
+        }
+        f(kk, vv, ii, 8);
+    }
+    if (v < nv) {
+        const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        T a[4];
+        load_chunk(vals, v * 4, n, a, T(0));
+        kk[0] = k0.x; kk[1] = k0.y; kk[2] = k0.z; kk[3] = k0.w;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            vv[j] = a[j];
+            ii[j] = 4 * v + j;
+        }
+        f(kk, vv, ii, 4);
+    }
+    for (int64_t i = nv * 4 + gtid; i < n; i += stride) {
+        kk[0] = keys[i];
+        vv[0] = vals[i];
+        ii[0] = i;
+        f(kk, vv, ii, 1);
+    }
+}
+
+// Compare-and-swap on the bit pattern of a float / double; returns the old value.
+__device__ __forceinline__ float cas_val(float *a, float expect, float val) {
+    return __uint_as_float(atomicCAS(reinterpret_cast<unsigned *>(a), __float_as_uint(expect), __float_as_uint(val)));
+}
+__device__ __forceinline__ double cas_val(double *a, double expect, double val) {
+    return __longlong_as_double((long long)atomicCAS(reinterpret_cast<unsigned long long *>(a),
+                                                     (unsigned long long)__double_as_longlong(expect),
+                                                     (unsigned long long)__double_as_longlong(val)));
+}
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+
+// Multiplies up to 8 values into global bins with all compare-and-swaps of a
+// round in flight together (bounded rounds; the error word records a give-up).
+template <typename T>
+__device__ __forceinline__ void batched_mul(T *__restrict__ p, const int32_t (&kk)[8], const T (&vv)[8],
+                                            const bool (&use)[8], unsigned *err) {
+    T cur[8];
+    bool todo[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        todo[j] = use[j];
+        if (todo[j]) cur[j] = __ldcg(p + kk[j]);
+    }
+    for (int round = 0; round < (1 << 20); ++round) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (todo[j]) {
+                const T old = cas_val(p + kk[j], cur[j], cur[j] * vv[j]);
+                if (same_bits(old, cur[j])) {
+                    todo[j] = false;
+                } else {
+                    cur[j] = old;
+                    any = true;
+                }
+            }
+        }
+        if (!any) return;
+    }
+    set_error(err, kErrCasLimit);
+}
 
 // ----------------------------------------------------------------- packing --
 template <bool MAX> struct Pack {
@@ -167,8 +259,22 @@ k_hist_sel_smem(const int32_t *__restrict__ keys, const float *__restrict__ vals
 template <bool MAX>
 __global__ void k_hist_sel_global(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n,
                                   const int64_t m, unsigned long long *__restrict__ tab) {
-    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
-        if (in_range(k, m)) Pack<MAX>::update(tab + k, Pack<MAX>::key(v, i));
+    // 8 reads of the current keys in flight, then the atomics that can still win
+    for_each_batch(keys, vals, n, [&](const int32_t (&kk)[8], const float (&vv)[8], const int64_t (&ii)[8], int cnt) {
+        unsigned long long key[8], cur[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = j < cnt && in_range(kk[j], m);
+            key[j] = ok ? Pack<MAX>::key(vv[j], ii[j]) : Pack<MAX>::kEmpty;
+            cur[j] = ok ? __ldcg(tab + kk[j]) : Pack<MAX>::kEmpty;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (Pack<MAX>::better(key[j], cur[j])) {
+                if (MAX) atomicMax(tab + kk[j], key[j]);
+                else atomicMin(tab + kk[j], key[j]);
+            }
+        }
     });
 }
 
@@ -299,11 +405,137 @@ template <typename T>
 __global__ void k_hist_mul_global(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n,
                                   const int64_t m, int32_t *__restrict__ n0, T *__restrict__ p,
                                   unsigned *__restrict__ err) {
+    for_each_batch(keys, vals, n, [&](const int32_t (&kk)[8], const T (&vv)[8], const int64_t (&)[8], int cnt) {
+        bool use[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = j < cnt && in_range(kk[j], m);
+            if (ok && vv[j] == T(0)) atomicAdd(n0 + kk[j], 1);
+            use[j] = ok && vv[j] != T(0);
+        }
+        batched_mul(p, kk, vv, use, err);
+    });
+}
+
+// One block-wide shared table of products (up to ~200 KB); the rare zeros go
+// straight to the global zero counts.
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_hist_mul_smem_prod(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                     int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) sp[j] = T(1);
+    __syncthreads();
     for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
         if (!in_range(k, m)) return;
         if (v == T(0)) atomicAdd(n0 + k, 1);
-        else atomic_mul(p + k, v, err);
+        else atomic_mul(sp + k, v, err);
     });
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
+        if (sp[j] != T(1)) atomic_mul(p + j, sp[j], err);
+}
+
+// ------------------------------------------------- per-thread private tables --
+// For tiny m: every thread owns a column of a [bin][thread] shared table, so
+// updates need no atomics and a warp's accesses hit 32 distinct banks whatever
+// the keys.  The block then reduces each bin across its threads.
+constexpr int kThrThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kThrThreads)
+k_hist_mul_thread(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                  int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sp = reinterpret_cast<T *>(smem_raw);
+    int32_t *sz = reinterpret_cast<int32_t *>(sp + m * kThrThreads);
+    for (int64_t j = threadIdx.x; j < m * kThrThreads; j += kThrThreads) {
+        sp[j] = T(1);
+        sz[j] = 0;
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (!in_range(k, m)) return;
+        const int64_t o = (int64_t)k * kThrThreads + t;
+        if (v == T(0)) sz[o] += 1;
+        else sp[o] *= v;
+    });
+    __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
+    for (int64_t j = warp; j < m; j += kThrThreads / kWarp) {
+        T prod = T(1);
+        int32_t z = 0;
+        for (int u = lane; u < kThrThreads; u += kWarp) {
+            prod *= sp[j * kThrThreads + u];
+            z += sz[j * kThrThreads + u];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            prod *= __shfl_xor_sync(0xffffffffu, prod, o);
+            z += __shfl_xor_sync(0xffffffffu, z, o);
+        }
+        if (lane == 0) {
+            if (z) atomicAdd(n0 + j, z);
+            if (prod != T(1)) atomic_mul(p + j, prod, err);
+        }
+    }
+}
+
+template <bool MAX>
+__global__ void __launch_bounds__(kThrThreads)
+k_hist_sel_thread(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                  unsigned long long *__restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *sh = reinterpret_cast<unsigned long long *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * kThrThreads; j += kThrThreads) sh[j] = Pack<MAX>::kEmpty;
+    __syncthreads();
+    const int t = threadIdx.x;
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
+        if (!in_range(k, m)) return;
+        const int64_t o = (int64_t)k * kThrThreads + t;
+        const unsigned long long key = Pack<MAX>::key(v, i);
+        if (Pack<MAX>::better(key, sh[o])) sh[o] = key;
+    });
+    __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
+    for (int64_t j = warp; j < m; j += kThrThreads / kWarp) {
+        unsigned long long b = Pack<MAX>::kEmpty;
+        for (int u = lane; u < kThrThreads; u += kWarp) {
+            const unsigned long long c = sh[j * kThrThreads + u];
+            if (Pack<MAX>::better(c, b)) b = c;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long c = __shfl_xor_sync(0xffffffffu, b, o);
+            if (Pack<MAX>::better(c, b)) b = c;
+        }
+        if (lane == 0 && b != Pack<MAX>::kEmpty) Pack<MAX>::update(tab + j, b);
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThrThreads)
+k_hist_add_thread(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+                  T *__restrict__ hist) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *sh = reinterpret_cast<T *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m * kThrThreads; j += kThrThreads) sh[j] = T(0);
+    __syncthreads();
+    const int t = threadIdx.x;
+    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
+        if (in_range(k, m)) sh[(int64_t)k * kThrThreads + t] += v;
+    });
+    __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
+    for (int64_t j = warp; j < m; j += kThrThreads / kWarp) {
+        T s = T(0);
+        for (int u = lane; u < kThrThreads; u += kWarp) s += sh[j * kThrThreads + u];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0 && s != T(0)) atomicAdd(hist + j, s);
+    }
 }
 
 template <typename T>
@@ -342,8 +574,11 @@ k_prim_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, co
 template <typename T>
 __global__ void k_prim_mul_global(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n,
                                   const int64_t m, T *__restrict__ hist, unsigned *__restrict__ err) {
-    for_each_elem(keys, vals, n, [&](int32_t k, T v, int64_t) {
-        if (in_range(k, m)) atomic_mul(hist + k, v, err);
+    for_each_batch(keys, vals, n, [&](const int32_t (&kk)[8], const T (&vv)[8], const int64_t (&)[8], int cnt) {
+        bool use[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) use[j] = j < cnt && in_range(kk[j], m);
+        batched_mul(hist, kk, vv, use, err);
     });
 }
 
@@ -399,8 +634,21 @@ k_prim_sel_smem(const int32_t *__restrict__ keys, const float *__restrict__ vals
 template <bool MAX>
 __global__ void k_prim_sel_global(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n,
                                   const int64_t m, uint32_t *__restrict__ tab) {
-    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t) {
-        if (in_range(k, m)) Ord32<MAX>::update(tab + k, ordered_key(v), false);
+    for_each_batch(keys, vals, n, [&](const int32_t (&kk)[8], const float (&vv)[8], const int64_t (&)[8], int cnt) {
+        uint32_t key[8], cur[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const bool ok = j < cnt && in_range(kk[j], m);
+            key[j] = ok ? ordered_key(vv[j]) : Ord32<MAX>::kEmpty;
+            cur[j] = ok ? __ldcg(tab + kk[j]) : Ord32<MAX>::kEmpty;
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (Ord32<MAX>::better(key[j], cur[j])) {
+                if (MAX) atomicMax(tab + kk[j], key[j]);
+                else atomicMin(tab + kk[j], key[j]);
+            }
+        }
     });
 }
 
@@ -473,24 +721,36 @@ __global__ void k_hist_sel_vjp(const int32_t *__restrict__ is, const T *__restri
     }
 }
 
-// Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.
+// Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.  A
+// per-bin record {a = hist0[k] * p[k] * histbar[k], z = n0[k]} is built first
+// so that the element pass gathers one word per element:
+//   z == 0          : vbar = (p / v) * hist0 * histbar = a / v
+//   z == 1 && v == 0: vbar = p * hist0 * histbar      = a
+//   otherwise       : 0
+template <typename T> struct MulRec { T a; int32_t z; int32_t pad; };
+
+template <typename T>
+__global__ void k_mul_vjp_prep(const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ h0,
+                               const T *__restrict__ hb, MulRec<T> *__restrict__ rec, const int64_t m) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t z = n0[j];
+        const T scale = h0 ? h0[j] * hb[j] : hb[j];
+        rec[j] = {z > 1 ? T(0) : p[j] * scale, z, 0};
+    }
+}
+
 template <typename T>
 __global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__restrict__ vals,
-                               const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ h0,
-                               const T *__restrict__ hb, T *__restrict__ vb, const int64_t n, const int64_t m,
-                               const int accumulate) {
+                               const MulRec<T> *__restrict__ rec, T *__restrict__ vb, const int64_t n,
+                               const int64_t m, const int accumulate) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     auto grad = [&](int32_t k, T v) -> T {
         if (!in_range(k, m)) return T(0);
-        const int32_t z = __ldg(n0 + k);
-        const T pk = __ldg(p + k);
-        T d;
-        if (z == 0) d = pk / v;
-        else if (z == 1 && v == T(0)) d = pk;
-        else return T(0);
-        const T scale = h0 ? __ldg(h0 + k) * __ldg(hb + k) : __ldg(hb + k);
-        return d * scale;
+        const MulRec<T> r = rec[k];
+        if (r.z == 0) return r.a / v;
+        if (r.z == 1 && v == T(0)) return r.a;
+        return T(0);
     };
     const int64_t nv = n / 4;
     for (int64_t v = g; v < nv; v += stride) {
@@ -529,41 +789,68 @@ static unsigned grid_for(int64_t work, int per_sm) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
-// Shared-memory bytes per bin entry of the forward strategy.
-static size_t entry_bytes(adc_op op, adc_dtype dt) {
-    const size_t s = dt == ADC_F64 ? 8 : 4;
+static int g_force_strategy = -1;  // tests: force a strategy (-1: automatic)
+
+constexpr size_t kThrBudget = 64 * 1024;    // per-thread tables: 3 blocks of 256 threads per SM
+constexpr size_t kWarpBudget = 24 * 1024;   // 8 per-warp copies
+constexpr size_t kBlockBudget = 200 * 1024; // one copy per 1024-thread block
+
+// Shared-memory bytes per bin and strategy.  MUL keeps its zero counts next to
+// the products except in the block-wide table (zeros then go to global memory).
+static size_t entry_bytes(adc_op op, size_t s, HistStrategy st) {
     switch (op) {
     case ADC_OP_ADD: return s;
-    case ADC_OP_MUL: return s + 4;
+    case ADC_OP_MUL: return st == kSmemBlock ? s : s + 4;
     case ADC_OP_MIN:
     case ADC_OP_MAX: return 8;
     default: return 0;
     }
 }
 
-static int g_force_strategy = -1;  // tests: force a strategy (-1: automatic)
-
-static HistStrategy pick(adc_op op, adc_dtype dt, int64_t m, int *R) {
-    const size_t e = entry_bytes(op, dt);
-    const bool sel64 = (op == ADC_OP_MIN || op == ADC_OP_MAX) && dt == ADC_F64;
-    HistStrategy s;
-    if (sel64) s = kGlobal;
-    else if ((size_t)m * e * 8 <= 24 * 1024) s = kSmemWarp;
-    else if ((size_t)m * e <= 200 * 1024) s = kSmemBlock;
-    else s = kGlobal;
-    if (g_force_strategy >= 0 && !sel64) {
-        const HistStrategy f = (HistStrategy)g_force_strategy;
-        if (f == kGlobal || (f == kSmemBlock && (size_t)m * e <= 200 * 1024) || (size_t)m * e * 8 <= 24 * 1024) s = f;
+static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
+    const size_t e = entry_bytes(op, s, st);
+    switch (st) {
+    case kSmemThread: return (size_t)m * e * kThrThreads <= kThrBudget;
+    case kSmemWarp: return (size_t)m * e * 8 <= kWarpBudget;
+    case kSmemBlock: return (size_t)m * e <= kBlockBudget;
+    default: return true;
     }
-    *R = (s == kSmemWarp) ? 8 : 1;
-    return s;
+}
+
+// Strategy for the lifted forward of op on a table of m bins.  fp64 min/max
+// always uses the two global phases.
+static HistStrategy pick(adc_op op, size_t s, int64_t m) {
+    if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
+    if (g_force_strategy >= 0 && g_force_strategy <= 3 && fits(op, s, (HistStrategy)g_force_strategy, m))
+        return (HistStrategy)g_force_strategy;
+    for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
+        if (fits(op, s, st, m)) return st;
+    return kGlobal;
+}
+
+struct Launch {
+    unsigned grid, block;
+    size_t smem;
+};
+
+static Launch shape(adc_op op, size_t s, HistStrategy st, int64_t m, int64_t n) {
+    const size_t e = entry_bytes(op, s, st);
+    switch (st) {
+    case kSmemThread: return {(unsigned)num_sms() * 3, (unsigned)kThrThreads, (size_t)m * e * kThrThreads};
+    case kSmemWarp: return {(unsigned)num_sms() * 4, 256u, (size_t)m * e * 8};
+    case kSmemBlock: return {(unsigned)num_sms(), 1024u, (size_t)m * e};
+    default: return {grid_for(n / 4 + 1, 8), 256u, 0};
+    }
+}
+
+template <typename K> static bool set_smem(K kernel, size_t smem) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
 }
 
 size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
-    (void)n;
     switch (op) {
-    case ADC_OP_ADD:
-    case ADC_OP_MUL: return kWsHeader;
+    case ADC_OP_ADD: return kWsHeader;
+    case ADC_OP_MUL: return kWsHeader + (size_t)m * 16;
     case ADC_OP_MIN:
     case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
     case ADC_OP_LIN: return histgen_ws_bytes(dt, n, m);
@@ -583,11 +870,11 @@ size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     }
 }
 
-// Strategy for a table of `e`-byte entries (same thresholds as pick()).
+// Strategy for the un-lifted primal's table of `e`-byte entries.
 static HistStrategy pick_entry(size_t e, int64_t m, int *R) {
     HistStrategy s;
-    if ((size_t)m * e * 8 <= 24 * 1024) s = kSmemWarp;
-    else if ((size_t)m * e <= 200 * 1024) s = kSmemBlock;
+    if ((size_t)m * e * 8 <= kWarpBudget) s = kSmemWarp;
+    else if ((size_t)m * e <= kBlockBudget) s = kSmemBlock;
     else s = kGlobal;
     *R = (s == kSmemWarp) ? 8 : 1;
     return s;
@@ -657,28 +944,24 @@ static adc_status hist_primal_t(adc_op op, int64_t n, int64_t m, const int32_t *
 template <typename T>
 static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0,
                              T *hist, void *saved, void *ws, cudaStream_t s) {
+    if (saved == nullptr && op != ADC_OP_ADD) return hist_primal_t<T>(op, n, m, keys, vals, h0, hist, ws, s);
     char *w = static_cast<char *>(ws);
     unsigned *err = reinterpret_cast<unsigned *>(w);
-    int R;
-    const HistStrategy st = pick(op, dt_of<T>(), m, &R);
-    const size_t e = entry_bytes(op, dt_of<T>());
-    const size_t smem = (size_t)m * e * R;
+    const HistStrategy st = pick(op, sizeof(T), m);
+    const Launch L = shape(op, sizeof(T), st, m, n);
     const unsigned gm = grid_for(m, 4);
-    const unsigned gsmem = (st == kSmemWarp) ? (unsigned)num_sms() * 4 : (unsigned)num_sms();
-    const unsigned tsmem = (st == kSmemWarp) ? 256 : 1024;
-    const unsigned gglob = grid_for(n / 4 + 1, 8);
-    if (saved == nullptr && op != ADC_OP_ADD) return hist_primal_t<T>(op, n, m, keys, vals, h0, hist, ws, s);
     switch (op) {
     case ADC_OP_ADD: {
         k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(0));
         if (n == 0) return check_launch();
         if (st == kGlobal) {
-            k_hist_add_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, hist);
+            k_hist_add_global<T><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, hist);
+        } else if (st == kSmemThread) {
+            if (!set_smem(k_hist_add_thread<T>, L.smem)) return ADC_ERR_CUDA;
+            k_hist_add_thread<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, hist);
         } else {
-            if (cudaFuncSetAttribute(k_hist_add_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                cudaSuccess)
-                return ADC_ERR_CUDA;
-            k_hist_add_smem<T><<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, hist);
+            if (!set_smem(k_hist_add_smem<T>, L.smem)) return ADC_ERR_CUDA;
+            k_hist_add_smem<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, st == kSmemWarp ? 8 : 1, hist);
         }
         return check_launch();
     }
@@ -688,12 +971,16 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
         if (n > 0) {
             if (st == kGlobal) {
-                k_hist_mul_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, n0, p, err);
+                k_hist_mul_global<T><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, n0, p, err);
+            } else if (st == kSmemThread) {
+                if (!set_smem(k_hist_mul_thread<T>, L.smem)) return ADC_ERR_CUDA;
+                k_hist_mul_thread<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, n0, p, err);
+            } else if (st == kSmemBlock) {
+                if (!set_smem(k_hist_mul_smem_prod<T>, L.smem)) return ADC_ERR_CUDA;
+                k_hist_mul_smem_prod<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, n0, p, err);
             } else {
-                if (cudaFuncSetAttribute(k_hist_mul_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                    cudaSuccess)
-                    return ADC_ERR_CUDA;
-                k_hist_mul_smem<T><<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, n0, p, err);
+                if (!set_smem(k_hist_mul_smem<T>, L.smem)) return ADC_ERR_CUDA;
+                k_hist_mul_smem<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, 8, n0, p, err);
             }
         }
         k_hist_mul_final<T><<<gm, 256, 0, s>>>(n0, p, h0, m, hist);
@@ -709,28 +996,31 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
             else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
             if (n > 0) {
                 if (st == kGlobal) {
-                    if (mx) k_hist_sel_global<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
-                    else k_hist_sel_global<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
+                    if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab);
+                    else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab);
+                } else if (st == kSmemThread) {
+                    auto kern = mx ? k_hist_sel_thread<true> : k_hist_sel_thread<false>;
+                    if (!set_smem(kern, L.smem)) return ADC_ERR_CUDA;
+                    kern<<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, tab);
                 } else {
                     auto kern = mx ? k_hist_sel_smem<true> : k_hist_sel_smem<false>;
-                    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                        cudaSuccess)
-                        return ADC_ERR_CUDA;
-                    kern<<<gsmem, tsmem, smem, s>>>(keys, vals, n, m, R, tab);
+                    if (!set_smem(kern, L.smem)) return ADC_ERR_CUDA;
+                    kern<<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, st == kSmemWarp ? 8 : 1, tab);
                 }
             }
             if (mx) k_hist_sel_final<true><<<gm, 256, 0, s>>>(tab, vals, h0, m, n, hist, is);
             else k_hist_sel_final<false><<<gm, 256, 0, s>>>(tab, vals, h0, m, n, hist, is);
         } else {
+            const unsigned gg = grid_for(n / 4 + 1, 8);
             unsigned *ti = reinterpret_cast<unsigned *>(w + kWsHeader + align_up((size_t)m * 8, 256));
             k_sel64_init<<<gm, 256, 0, s>>>(tab, ti, m, mx ? 0ull : ~0ull);
             if (n > 0) {
                 if (mx) {
-                    k_hist_sel64_value<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
-                    k_hist_sel64_index<true><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab, ti);
+                    k_hist_sel64_value<true><<<gg, 256, 0, s>>>(keys, vals, n, m, tab);
+                    k_hist_sel64_index<true><<<gg, 256, 0, s>>>(keys, vals, n, m, tab, ti);
                 } else {
-                    k_hist_sel64_value<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab);
-                    k_hist_sel64_index<false><<<gglob, 256, 0, s>>>(keys, vals, n, m, tab, ti);
+                    k_hist_sel64_value<false><<<gg, 256, 0, s>>>(keys, vals, n, m, tab);
+                    k_hist_sel64_index<false><<<gg, 256, 0, s>>>(keys, vals, n, m, tab, ti);
                 }
             }
             if (mx) k_hist_sel64_final<true><<<gm, 256, 0, s>>>(ti, vals, h0, m, n, hist, is);
@@ -754,7 +1044,7 @@ adc_status hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t
 
 template <typename T>
 static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0,
-                             const void *saved, const T *hb, T *vb, T *h0b, int acc, cudaStream_t s) {
+                             const void *saved, const T *hb, T *vb, T *h0b, int acc, void *ws, cudaStream_t s) {
     const unsigned gm = grid_for(m, 4);
     const unsigned gn = grid_for(n / 4 + 1, 8);
     switch (op) {
@@ -770,7 +1060,11 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
     case ADC_OP_MUL: {
         const int32_t *n0 = static_cast<const int32_t *>(saved);
         const T *p = reinterpret_cast<const T *>(static_cast<const char *>(saved) + align_up((size_t)m * 4, 16));
-        if (n > 0) k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, n0, p, h0, hb, vb, n, m, acc);
+        MulRec<T> *rec = reinterpret_cast<MulRec<T> *>(static_cast<char *>(ws) + kWsHeader);
+        if (n > 0) {
+            k_mul_vjp_prep<T><<<gm, 256, 0, s>>>(n0, p, h0, hb, rec, m);
+            k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, rec, vb, n, m, acc);
+        }
         if (h0b) k_h0bar_mul<T><<<gm, 256, 0, s>>>(n0, p, hb, h0b, m, acc);
         return check_launch();
     }
@@ -784,14 +1078,13 @@ adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t
     if (op == ADC_OP_LIN)
         return histgen_vjp(dt, n, m, keys, vals, hist0, hist, saved, histbar, valsbar, hist0bar, accumulate, ws, s);
     (void)hist;
-    (void)ws;
     if (dt == ADC_F64)
         return hist_vjp_t<double>(op, n, m, keys, static_cast<const double *>(vals),
                                   static_cast<const double *>(hist0), saved, static_cast<const double *>(histbar),
-                                  static_cast<double *>(valsbar), static_cast<double *>(hist0bar), accumulate, s);
+                                  static_cast<double *>(valsbar), static_cast<double *>(hist0bar), accumulate, ws, s);
     return hist_vjp_t<float>(op, n, m, keys, static_cast<const float *>(vals), static_cast<const float *>(hist0), saved,
                              static_cast<const float *>(histbar), static_cast<float *>(valsbar),
-                             static_cast<float *>(hist0bar), accumulate, s);
+                             static_cast<float *>(hist0bar), accumulate, ws, s);
 }
 
 }  // namespace adc

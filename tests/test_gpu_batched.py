@@ -1,0 +1,155 @@
+"""GPU: batched hist -> +-scan -> sum over many instances, against the oracle,
+the closed-form gradient, the per-instance launches and CUDA-graph replay."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2310_03568_gb300 import batched as B
+from paper_2310_03568_gb300 import synth
+from tests._gpu import ensure_lib
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    ensure_lib()
+
+
+def small_workload(seed=31, count=48):
+    """Log-uniform sizes like the full workload, scaled down; includes bins beyond
+    the shared-memory table and instances with fewer values than bins."""
+    w = synth.batched(seed=seed, count=count, n_lo=1e2, n_hi=2e5, m_lo=16, m_hi=65536)
+    return w
+
+
+def oracle_reference(desc, keys, vals):
+    """Per instance: hist (zero initial histogram), scan, loss, selected indices
+    and the value adjoint for a unit loss adjoint, all from the fp64 oracle."""
+    out = []
+    for d in desc:
+        n, m, o = int(d["n"]), int(d["m"]), int(d["val_off"])
+        op = "add" if d["op"] == B.OPCODE["add"] else "max"
+        k, v = keys[o:o + n], vals[o:o + n]
+        h0 = np.zeros(m)
+        if op == "max":
+            h, idx = oracle.hist_fwd("max", m, k, v, h0)
+        else:
+            h, idx = oracle.hist_fwd("add", m, k, v, h0), None
+        s = oracle.scan_fwd("add", h)
+        # loss_i = reduce (+) scan; the adjoint chain uses the oracle's own vjps
+        sbar = oracle.reduce_vjp("add", s, [1.0])
+        hbar = oracle.scan_vjp("add", h, sbar)
+        vbar, _ = oracle.hist_vjp(op, m, k, v, hbar, h0)
+        out.append(dict(h=h, idx=idx, s=s, loss=oracle.reduce_fwd("add", s), vbar=vbar, op=op))
+    return out
+
+
+def check_problem(p, desc, keys, vals, ref):
+    hist, scan, is_ = p.hist.cpu().numpy(), p.scan.cpu().numpy(), p.is_.cpu().numpy()
+    vb = p.valsbar.cpu().numpy()
+    total_abs = 0.0
+    for d, r in zip(desc, ref):
+        n, m, o, b = int(d["n"]), int(d["m"]), int(d["val_off"]), int(d["bin_off"])
+        if r["op"] == "max":
+            assert np.array_equal(hist[b:b + m], r["h"].astype(np.float32))
+            assert np.array_equal(is_[b:b + m], r["idx"].astype(np.int32))
+        else:
+            pop = np.bincount(keys[o:o + n], minlength=m)
+            tol = 1e-5 * np.maximum(np.abs(r["h"]), np.sqrt(pop + 1) * 1.0)
+            assert np.all(np.abs(hist[b:b + m] - r["h"]) <= tol)
+        # gradients are exact integers (m - j), so the comparison is bit-exact
+        assert np.array_equal(vb[o:o + n], r["vbar"].astype(np.float32))
+        total_abs += np.abs(r["s"]).sum()
+    loss_ref = sum(r["loss"] for r in ref)
+    # a sum of fp32 scan values: bounded by rtol times the sum of magnitudes
+    assert abs(float(p.loss.item()) - loss_ref) <= 1e-5 * total_abs
+
+
+def test_batched_matches_oracle_and_closed_form():
+    w = small_workload()
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals, chunk=1 << 14)
+    p.forward()
+    p.backward()
+    torch.cuda.synchronize()
+    check_problem(p, desc, keys, vals, oracle_reference(desc, keys, vals))
+
+
+@pytest.mark.parametrize("chunk,smem_bins", [(1 << 10, 2048), (1 << 16, 8192), (1 << 20, 0), (333, 24000)])
+def test_batched_tunings_agree(chunk, smem_bins):
+    w = small_workload(seed=32, count=24)
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals, chunk=chunk, smem_bins=smem_bins)
+    p.forward()
+    p.backward()
+    torch.cuda.synchronize()
+    check_problem(p, desc, keys, vals, oracle_reference(desc, keys, vals))
+
+
+def test_graph_replay_is_idempotent_and_equals_per_instance():
+    w = small_workload(seed=33, count=40)
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals, chunk=1 << 15)
+    runs = []
+    for _ in range(3):
+        p.replay_forward()
+        p.replay_backward()
+        torch.cuda.synchronize()
+        runs.append((p.loss.item(), p.valsbar.cpu().numpy().copy(), p.is_.cpu().numpy().copy()))
+    for r in runs[1:]:
+        assert np.array_equal(r[1], runs[0][1]) and np.array_equal(r[2], runs[0][2])
+        assert abs(r[0] - runs[0][0]) <= 1e-6 * abs(runs[0][0]) + 1e-3
+    loss_pi, vb_pi = B.per_instance_loss(desc, p.keys, p.vals)
+    torch.cuda.synchronize()
+    vb = runs[0][1]
+    vbp = vb_pi.cpu().numpy()
+    for d in desc:
+        o, n = int(d["val_off"]), int(d["n"])
+        assert np.array_equal(vb[o:o + n], vbp[o:o + n])
+    ref = oracle_reference(desc, keys, vals)
+    total_abs = sum(np.abs(r["s"]).sum() for r in ref)
+    assert abs(loss_pi.item() - runs[0][0]) <= 2e-5 * total_abs
+
+
+def test_batched_autograd():
+    w = small_workload(seed=34, count=16)
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals, chunk=1 << 14)
+    v = torch.tensor(vals, device="cuda", requires_grad=True)
+    loss = B.batched_loss(v, p, use_graph=True)
+    (2.0 * loss).backward()
+    ref = oracle_reference(desc, keys, vals)
+    g = v.grad.cpu().numpy()
+    for d, r in zip(desc, ref):
+        o, n = int(d["val_off"]), int(d["n"])
+        assert np.array_equal(g[o:o + n], (2.0 * r["vbar"]).astype(np.float32))
+
+
+@pytest.mark.slow
+def test_batched_full_workload_gradient_closed_form():
+    """The full workload (4096 instances, ~5.9e8 values): the value adjoint of a
+    +-instance is m - k exactly, of a max-instance m - j at the selected index."""
+    w = synth.batched()
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals)
+    p.forward()
+    p.backward()
+    torch.cuda.synchronize()
+    vb = p.valsbar.cpu().numpy()
+    is_ = p.is_.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for i in rng.choice(len(desc), 64, replace=False):  # oracle on a sample of instances
+        d = desc[i]
+        n, m, o, b = int(d["n"]), int(d["m"]), int(d["val_off"]), int(d["bin_off"])
+        k, v = keys[o:o + n], vals[o:o + n]
+        if d["op"] == B.OPCODE["add"]:
+            assert np.array_equal(vb[o:o + n], (m - k).astype(np.float32))
+        else:
+            _, idx = oracle.hist_fwd("max", m, k, v, np.zeros(m))
+            assert np.array_equal(is_[b:b + m], idx.astype(np.int32))
+            expect = np.zeros(n, np.float32)
+            sel = idx < n
+            expect[idx[sel]] = (m - np.arange(m))[sel]
+            assert np.array_equal(vb[o:o + n], expect)

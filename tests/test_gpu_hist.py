@@ -56,14 +56,23 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2]
+STRATS = [-1, 0, 1, 2, 3]  # auto, per-warp, per-block, global, per-thread
 
 
 def fits(op, dt, m, s):
-    e = {"add": dt().itemsize, "mul": dt().itemsize + 4, "min": 8, "max": 8}[op]
+    """Mirror of the library's shared-memory budgets: strategies that cannot hold
+    the table are skipped (the library would fall back to its own choice)."""
+    sz = np.dtype(dt).itemsize
     if op in ("min", "max") and dt == np.float64:
         return s in (-1, 2)
-    return s in (-1, 2) or (s == 1 and m * e <= 200 * 1024) or (s == 0 and m * e * 8 <= 24 * 1024)
+    e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
+    if s == 3:
+        return m * e * 256 <= 64 * 1024
+    if s == 0:
+        return m * e * 8 <= 24 * 1024
+    if s == 1:
+        return m * (sz if op == "mul" else e) <= 200 * 1024
+    return True
 
 
 CASES = [(0, 7), (1, 1), (33, 5), (4097, 31), (100_003, 401), (100_003, 5000), (300_001, 50_000)]
