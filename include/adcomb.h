@@ -146,8 +146,8 @@ adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, co
  * Same operators, layouts and results as adc_scan_fwd; nothing is allocated
  * or freed.
  *   Limit : n must satisfy adc_workspace_bytes(ADC_SCAN, op, dtype, n, 0) <= 4 MiB
- *           (about 1.4e9 fp32 + elements, 4.2e8 fp32 *, 1.5e8 fp32 lin,
- *           3.1e7 fp32 mm2, 1.6e7 fp64 mm2); larger n returns
+ *           (about 1.0e9 fp32 + elements, 2.6e8 fp32 *, 8.9e7 fp32 lin,
+ *           1.6e7 fp32 mm2, 8.3e6 fp64 mm2); larger n returns
  *           ADC_ERR_WORKSPACE before any work is queued.
  *   Set-up: the first call on a device, with that device current, looks up the
  *           array's device address; make that first call before capturing a

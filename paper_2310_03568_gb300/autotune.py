@@ -1,0 +1,137 @@
+"""Autotuner for the launch parameters libadcomb exposes.
+
+* batched hist -> scan -> sum: work-item size (``chunk``) and shared-memory
+  table size (``smem_bins``) of the persistent histogram launch;
+* reduce_by_index (single call): the forward strategy -- per-thread tables,
+  per-warp copies, one block-wide table, or global atomics
+  (``adc_debug_force_hist_strategy``; the library validates that the table fits).
+
+Each candidate is timed with CUDA events on the real inputs (warm-up, then the
+mean of a few runs); the winner is cached in a JSON file keyed by the shape
+bucket, so later calls with a similar shape reuse it without measuring.
+Cache file: ``$ADC_AUTOTUNE_CACHE`` or ``~/.cache/adcomb_autotune.json``.
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+import torch
+
+from . import adcomb
+
+_lock = threading.Lock()
+_cache = None
+
+BATCHED_CHUNKS = (1 << 14, 1 << 16, 1 << 18)
+BATCHED_SMEM_BINS = (4096, 8192, 16384)
+HIST_STRATEGIES = (3, 0, 1, 2)  # per-thread, per-warp, per-block, global
+
+
+def cache_path():
+    return os.environ.get("ADC_AUTOTUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache",
+                                                             "adcomb_autotune.json"))
+
+
+def _load():
+    global _cache
+    if _cache is None:
+        try:
+            with open(cache_path()) as f:
+                _cache = json.load(f)
+        except (OSError, ValueError):
+            _cache = {}
+    return _cache
+
+
+def _store():
+    p = cache_path()
+    try:
+        os.makedirs(os.path.dirname(p), exist_ok=True)
+        tmp = p + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(_cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, p)
+    except OSError:
+        pass  # a read-only home: the in-memory cache still serves this process
+
+
+def _bucket(x):
+    return int(round(math.log2(max(int(x), 1))))
+
+
+def _time(fn, reps=3):
+    fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def batched_key(desc):
+    dev = torch.cuda.get_device_name()
+    return (f"batched|{dev}|count={_bucket(len(desc))}|n={_bucket(desc['n'].sum())}|"
+            f"mmean={_bucket(desc['m'].mean())}")
+
+
+def tune_batched(problem, force=False):
+    """Chooses (chunk, smem_bins) for a BatchedHistScan and applies them."""
+    key = batched_key(problem.desc_h)
+    with _lock:
+        hit = _load().get(key)
+    if hit is not None and not force:
+        problem.smem_bins = hit["smem_bins"]
+        if hit["chunk"] != problem.chunk:
+            problem.set_plan(hit["chunk"])
+        return hit
+    best = None
+    results = []
+    for chunk in BATCHED_CHUNKS:
+        problem.set_plan(chunk)
+        for sb in BATCHED_SMEM_BINS:
+            problem.smem_bins = sb
+            ms = _time(lambda: (problem.forward(), problem.backward()))
+            results.append({"chunk": chunk, "smem_bins": sb, "ms": ms})
+            if best is None or ms < best["ms"]:
+                best = results[-1]
+    problem.set_plan(best["chunk"])
+    problem.smem_bins = best["smem_bins"]
+    entry = dict(best, candidates=results)
+    with _lock:
+        _load()[key] = entry
+        _store()
+    return entry
+
+
+def hist_key(op, dtype, n, m):
+    return f"hist|{torch.cuda.get_device_name()}|{op}|{dtype}|n={_bucket(n)}|m={_bucket(m)}"
+
+
+def tune_hist(op, m, keys, vals, force=False):
+    """Chooses the forward strategy for reduce_by_index(op) at this shape; returns it
+    and leaves it selected in the library (-1 restores the built-in choice)."""
+    key = hist_key(op, vals.dtype, keys.shape[0], m)
+    with _lock:
+        hit = _load().get(key)
+    if hit is not None and not force:
+        adcomb.debug_force_hist_strategy(hit["strategy"])
+        return hit
+    hist, saved = adcomb.hist_fwd(op, m, keys, vals)
+    results = []
+    for s in HIST_STRATEGIES:
+        adcomb.debug_force_hist_strategy(s)
+        ms = _time(lambda: adcomb.hist_fwd(op, m, keys, vals, None, hist, saved))
+        results.append({"strategy": s, "ms": ms})
+    best = min(results, key=lambda r: r["ms"])
+    adcomb.debug_force_hist_strategy(best["strategy"])
+    entry = dict(best, candidates=results)
+    with _lock:
+        _load()[key] = entry
+        _store()
+    return entry

@@ -721,36 +721,32 @@ __global__ void k_hist_sel_vjp(const int32_t *__restrict__ is, const T *__restri
     }
 }
 
-// Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.  A
-// per-bin record {a = hist0[k] * p[k] * histbar[k], z = n0[k]} is built first
-// so that the element pass gathers one word per element:
-//   z == 0          : vbar = (p / v) * hist0 * histbar = a / v
-//   z == 1 && v == 0: vbar = p * hist0 * histbar      = a
-//   otherwise       : 0
-template <typename T> struct MulRec { T a; int32_t z; int32_t pad; };
-
+// Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.  Two
+// per-bin coefficients are built first, with a = hist0[k] * p[k] * histbar[k]:
+//   anz[k] = a if n0[k] == 0 else 0   -> vbar = anz[k] / v   for v != 0
+//   az[k]  = a if n0[k] == 1 else 0   -> vbar = az[k]        for v == 0
+// so the element pass gathers ONE word per non-zero value (and one from the
+// second table for the rare zeros).
 template <typename T>
 __global__ void k_mul_vjp_prep(const int32_t *__restrict__ n0, const T *__restrict__ p, const T *__restrict__ h0,
-                               const T *__restrict__ hb, MulRec<T> *__restrict__ rec, const int64_t m) {
+                               const T *__restrict__ hb, T *__restrict__ anz, T *__restrict__ az, const int64_t m) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
         const int32_t z = n0[j];
-        const T scale = h0 ? h0[j] * hb[j] : hb[j];
-        rec[j] = {z > 1 ? T(0) : p[j] * scale, z, 0};
+        const T a = p[j] * (h0 ? h0[j] * hb[j] : hb[j]);
+        anz[j] = z == 0 ? a : T(0);
+        az[j] = z == 1 ? a : T(0);
     }
 }
 
 template <typename T>
 __global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__restrict__ vals,
-                               const MulRec<T> *__restrict__ rec, T *__restrict__ vb, const int64_t n,
-                               const int64_t m, const int accumulate) {
+                               const T *__restrict__ anz, const T *__restrict__ az, T *__restrict__ vb,
+                               const int64_t n, const int64_t m, const int accumulate) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     auto grad = [&](int32_t k, T v) -> T {
         if (!in_range(k, m)) return T(0);
-        const MulRec<T> r = rec[k];
-        if (r.z == 0) return r.a / v;
-        if (r.z == 1 && v == T(0)) return r.a;
-        return T(0);
+        return v != T(0) ? __ldg(anz + k) / v : __ldg(az + k);
     };
     const int64_t nv = n / 4;
     for (int64_t v = g; v < nv; v += stride) {
@@ -792,7 +788,7 @@ static unsigned grid_for(int64_t work, int per_sm) {
 static int g_force_strategy = -1;  // tests: force a strategy (-1: automatic)
 
 constexpr size_t kThrBudget = 64 * 1024;    // per-thread tables: 3 blocks of 256 threads per SM
-constexpr size_t kWarpBudget = 24 * 1024;   // 8 per-warp copies
+constexpr size_t kWarpBudget = 48 * 1024;   // 8 per-warp copies, 4 blocks per SM
 constexpr size_t kBlockBudget = 200 * 1024; // one copy per 1024-thread block
 
 // Shared-memory bytes per bin and strategy.  MUL keeps its zero counts next to
@@ -823,8 +819,12 @@ static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
     if (g_force_strategy >= 0 && g_force_strategy <= 3 && fits(op, s, (HistStrategy)g_force_strategy, m))
         return (HistStrategy)g_force_strategy;
+    // min/max updates are rare after the first few values of a bin (a read
+    // filters them), so per-warp copies beat per-thread tables there: the
+    // latter's larger footprint costs occupancy.
+    const bool select = op == ADC_OP_MIN || op == ADC_OP_MAX;
     for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
-        if (fits(op, s, st, m)) return st;
+        if (!(select && st == kSmemThread) && fits(op, s, st, m)) return st;
     return kGlobal;
 }
 
@@ -850,7 +850,7 @@ template <typename K> static bool set_smem(K kernel, size_t smem) {
 size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     switch (op) {
     case ADC_OP_ADD: return kWsHeader;
-    case ADC_OP_MUL: return kWsHeader + (size_t)m * 16;
+    case ADC_OP_MUL: return kWsHeader + 2 * align_up((size_t)m * 8, 256);
     case ADC_OP_MIN:
     case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
     case ADC_OP_LIN: return histgen_ws_bytes(dt, n, m);
@@ -1060,10 +1060,11 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
     case ADC_OP_MUL: {
         const int32_t *n0 = static_cast<const int32_t *>(saved);
         const T *p = reinterpret_cast<const T *>(static_cast<const char *>(saved) + align_up((size_t)m * 4, 16));
-        MulRec<T> *rec = reinterpret_cast<MulRec<T> *>(static_cast<char *>(ws) + kWsHeader);
+        T *anz = reinterpret_cast<T *>(static_cast<char *>(ws) + kWsHeader);
+        T *az = reinterpret_cast<T *>(static_cast<char *>(ws) + kWsHeader + align_up((size_t)m * sizeof(T), 256));
         if (n > 0) {
-            k_mul_vjp_prep<T><<<gm, 256, 0, s>>>(n0, p, h0, hb, rec, m);
-            k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, rec, vb, n, m, acc);
+            k_mul_vjp_prep<T><<<gm, 256, 0, s>>>(n0, p, h0, hb, anz, az, m);
+            k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, anz, az, vb, n, m, acc);
         }
         if (h0b) k_h0bar_mul<T><<<gm, 256, 0, s>>>(n0, p, hb, h0b, m, acc);
         return check_launch();

@@ -18,6 +18,7 @@
 #include "block_scan.cuh"
 #include "common.cuh"
 #include "internal.h"
+#include "scan_engine.cuh"
 #include "tile_io.cuh"
 
 namespace adc {
@@ -127,16 +128,14 @@ template <typename T> __global__ void k_fin_mul(const MulS<T> *r, T *y, int32_t 
 }
 
 // ------------------------------------------------------ general reduction --
+// Pass 1: the aggregate of every tile, in order.
 template <class Op, typename T, int ITEMS>
 __global__ void __launch_bounds__(kRedThreads)
-k_reduce_general(const Op op, const typename Op::State *__restrict__ x, const int64_t n, const int64_t T_,
-                 typename Op::State *__restrict__ tpart, unsigned *__restrict__ ticket,
-                 typename Op::State *__restrict__ Lex, typename Op::State *__restrict__ Rex,
-                 typename Op::State *__restrict__ y) {
+k_reduce_tiles(const Op op, const typename Op::State *__restrict__ x, const int64_t n,
+               typename Op::State *__restrict__ tpart) {
     using S = typename Op::State;
     constexpr int TILE = kRedThreads * ITEMS;
     __shared__ S tmp[kRedThreads / kWarp];
-    __shared__ bool last;
     const int64_t c0 = (int64_t)blockIdx.x * TILE + (int64_t)threadIdx.x * ITEMS;
     S v[ITEMS];
     load_chunk(x, c0, n, v, op.identity());
@@ -145,35 +144,72 @@ k_reduce_general(const Op op, const typename Op::State *__restrict__ x, const in
     for (int k = 0; k < ITEMS; ++k) acc = op.combine(acc, v[k]);
     S total;
     block_exclusive_fwd<Op, kRedThreads>(op, acc, tmp, &total);
-    if (threadIdx.x == 0) {
-        tpart[blockIdx.x] = total;
-        __threadfence();
-        last = (atomicAdd(ticket, 1u) == gridDim.x - 1);
-    }
-    __syncthreads();
-    if (!last) return;
-    __threadfence();
-    // last block: exclusive prefix and suffix of the tile aggregates
-    const int64_t per = (T_ + kRedThreads - 1) / kRedThreads;
-    const int64_t b0 = (int64_t)threadIdx.x * per;
-    S a = op.identity();
-    for (int64_t j = 0; j < per; ++j)
-        if (b0 + j < T_) a = op.combine(a, load_cg(&tpart[b0 + j]));
-    S all;
-    S pre = block_exclusive_fwd<Op, kRedThreads>(op, a, tmp, &all);
-    S suf = block_exclusive_rev<Op, kRedThreads>(op, a, tmp);
-    for (int64_t j = 0; j < per; ++j) {
-        if (b0 + j >= T_) break;
-        Lex[b0 + j] = pre;
-        pre = op.combine(pre, load_cg(&tpart[b0 + j]));
-    }
-    for (int64_t j = per - 1; j >= 0; --j) {
-        if (b0 + j >= T_) continue;
-        Rex[b0 + j] = suf;
-        suf = op.combine(load_cg(&tpart[b0 + j]), suf);
-    }
-    if (threadIdx.x == 0) *y = all;
+    if (threadIdx.x == 0) tpart[blockIdx.x] = total;
 }
+
+// Pass 2 (look-back scans over the T tile aggregates): element t carries the
+// aggregate of tile t-1, so the inclusive scan at t is the EXCLUSIVE prefix
+// L_t; the store of the last element also writes y = L_{T-1} . P_{T-1}.
+template <class G, int ITEMS> struct TilePrefix {
+    using State = typename G::State;
+    using Aux = NoAux;
+    struct Raw { State v[ITEMS]; };
+    G g;
+    const State *tpart;
+    State *Lex;
+    State *y;
+    __device__ State identity() const { return g.identity(); }
+    __device__ State combine(const State &a, const State &b) const { return g.combine(a, b); }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = c0 + k;
+            r.v[k] = (i > 0 && i <= n) ? tpart[i - 1] : g.identity();
+        }
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? r.v[k] : g.identity();
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            if (c0 + k < n) Lex[c0 + k] = st[k];
+            if (c0 + k == n - 1) *y = g.combine(st[k], tpart[n - 1]);
+        }
+    }
+};
+
+// Reverse look-back scan: element t carries the aggregate of tile t+1, so the
+// inclusive value at t is the EXCLUSIVE suffix R_t.
+template <class G, int ITEMS> struct TileSuffix {
+    using State = typename G::State;
+    using Aux = NoAux;
+    struct Raw { State v[ITEMS]; };
+    G g;
+    const State *tpart;
+    State *Rex;
+    __device__ State identity() const { return g.identity(); }
+    // logical order: `e` lies physically before everything already combined
+    __device__ State combine(const State &acc, const State &e) const { return g.combine(e, acc); }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = c0 + k;
+            r.v[k] = (i + 1 < n) ? tpart[i + 1] : g.identity();
+        }
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? r.v[k] : g.identity();
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k)
+            if (c0 + k < n) Rex[c0 + k] = st[k];
+    }
+};
+constexpr int kTileScanItems = 4;
 
 // vjp of the general rule: xbar_i = d(l_i . x_i . r_i)/dx_i ^T ybar.
 template <typename T> __device__ __forceinline__ Pair<T> general_adj(const Pair<T> &l, const Pair<T> &r, const Pair<T> &yb) {
@@ -288,27 +324,36 @@ __global__ void k_vjp_mul(T *__restrict__ xbar, const T *__restrict__ x, const T
     constexpr int V = 16 / sizeof(T);
     const int64_t nv = (n + V - 1) / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += stride) {
-        T a[V], o[V];
+    auto grad = [&](T a) -> T {
+        if (n0 == 0) return (p / a) * yb;
+        if (n0 == 1 && a == T(0)) return p * yb;
+        return T(0);
+    };
+    // two vectors per thread in flight before any result is needed
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < nv; i += 2 * stride) {
+        const int64_t j = i + stride;
+        T a[V], b[V], o[V], q[V];
         load_chunk(x, i * V, n, a, T(1));
-        if (accumulate) load_chunk(xbar, i * V, n, o, T(0));
+        if (j < nv) load_chunk(x, j * V, n, b, T(1));
+        if (accumulate) {
+            load_chunk(xbar, i * V, n, o, T(0));
+            if (j < nv) load_chunk(xbar, j * V, n, q, T(0));
+        }
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            T g;
-            if (n0 == 0) g = (p / a[k]) * yb;
-            else if (n0 == 1 && a[k] == T(0)) g = p * yb;
-            else g = T(0);
-            o[k] = accumulate ? o[k] + g : g;
+            o[k] = accumulate ? o[k] + grad(a[k]) : grad(a[k]);
+            if (j < nv) q[k] = accumulate ? q[k] + grad(b[k]) : grad(b[k]);
         }
         store_chunk(xbar, i * V, n, o);
+        if (j < nv) store_chunk(xbar, j * V, n, q);
     }
 }
 
 // --------------------------------------------------------------- planning --
 template <typename T> struct RedItems {
     static constexpr int scalar = 64 / sizeof(T);
-    static constexpr int pair = 32 / (2 * sizeof(T)) > 0 ? 32 / (2 * sizeof(T)) : 1;
-    static constexpr int mat = 2;
+    static constexpr int pair = 64 / (2 * sizeof(T));  // 16 KB tiles of (b, c) pairs
+    static constexpr int mat = 64 / (4 * sizeof(T));   // 16 KB tiles of 2x2 matrices
 };
 
 static int64_t simple_grid(int64_t tiles) {
@@ -323,9 +368,39 @@ template <typename T> static int64_t general_tiles(adc_op op, int64_t n) {
     return (n + tile - 1) / tile;
 }
 
+// Workspace of the general reduce: [header][tile aggregates][two look-back regions].
+template <class G> static size_t general_ws(int64_t tiles) {
+    using P = TilePrefix<G, kTileScanItems>;
+    using Q = TileSuffix<G, kTileScanItems>;
+    const size_t sb = sizeof(typename G::State);
+    return kWsHeader + align_up((size_t)(tiles + 1) * sb, 256) + ScanShape<P, kTileScanItems>::region(tiles) +
+           ScanShape<Q, kTileScanItems>::region(tiles);
+}
+
+template <class G, typename T, int ITEMS>
+static adc_status general_fwd(int64_t n, const void *xv, void *yv, void *saved, void *ws, cudaStream_t s) {
+    using S = typename G::State;
+    constexpr int TILE = kRedThreads * ITEMS;
+    const int64_t tiles = n > 0 ? (n + TILE - 1) / TILE : 1;  // n == 0: one tile of identities
+    char *w = static_cast<char *>(ws);
+    S *tpart = reinterpret_cast<S *>(w + kWsHeader);
+    char *reg1 = w + kWsHeader + align_up((size_t)(tiles + 1) * sizeof(S), 256);
+    char *reg2 = reg1 + ScanShape<TilePrefix<G, kTileScanItems>, kTileScanItems>::region(tiles);
+    S *Lex = static_cast<S *>(saved);
+    S *Rex = Lex + tiles;
+    k_reduce_tiles<G, T, ITEMS><<<(unsigned)tiles, kRedThreads, 0, s>>>(G{}, static_cast<const S *>(xv), n, tpart);
+    adc_status st = check_launch();
+    if (st != ADC_OK) return st;
+    TilePrefix<G, kTileScanItems> pre{G{}, tpart, Lex, static_cast<S *>(yv)};
+    if ((st = run_scan<decltype(pre), kTileScanItems, false>(pre, tiles, ws, 2, reg1, s)) != ADC_OK) return st;
+    TileSuffix<G, kTileScanItems> suf{G{}, tpart, Rex};
+    return run_scan<decltype(suf), kTileScanItems, true>(suf, tiles, ws, 3, reg2, s);
+}
+
 template <typename T> static size_t red_ws_t(adc_op op, int64_t n) {
     if (op == ADC_OP_LIN || op == ADC_OP_MM2) {
-        return kWsHeader + (size_t)(general_tiles<T>(op, n) + 1) * general_state_bytes<T>(op) + 256;
+        const int64_t tiles = general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1;
+        return op == ADC_OP_LIN ? general_ws<GLin<T>>(tiles) : general_ws<GMM2<T>>(tiles);
     }
     const int64_t tiles = (n + kRedThreads * RedItems<T>::scalar - 1) / (kRedThreads * RedItems<T>::scalar);
     return kWsHeader + (size_t)(simple_grid(tiles) + 1) * 32 + 256;
@@ -403,27 +478,9 @@ static adc_status red_fwd_t(adc_op op, int64_t n, const void *xv, void *yv, void
         return check_launch();
     }
     case ADC_OP_LIN:
-    case ADC_OP_MM2: {
-        const int64_t Tn = general_tiles<T>(op, n);
-        char *w = static_cast<char *>(ws);
-        const size_t sb = general_state_bytes<T>(op);
-        char *sv = static_cast<char *>(saved);
-        const int64_t G = Tn > 0 ? Tn : 1;  // n == 0: one block writes the identity
-        if (op == ADC_OP_LIN) {
-            using S = Pair<T>;
-            k_reduce_general<GLin<T>, T, RedItems<T>::pair><<<(unsigned)G, kRedThreads, 0, s>>>(
-                GLin<T>{}, static_cast<const S *>(xv), n, G, reinterpret_cast<S *>(w + kWsHeader),
-                counter_slot(ws, 1), reinterpret_cast<S *>(sv), reinterpret_cast<S *>(sv + G * sb),
-                reinterpret_cast<S *>(yv));
-        } else {
-            using S = Mat2<T>;
-            k_reduce_general<GMM2<T>, T, RedItems<T>::mat><<<(unsigned)G, kRedThreads, 0, s>>>(
-                GMM2<T>{}, static_cast<const S *>(xv), n, G, reinterpret_cast<S *>(w + kWsHeader),
-                counter_slot(ws, 1), reinterpret_cast<S *>(sv), reinterpret_cast<S *>(sv + G * sb),
-                reinterpret_cast<S *>(yv));
-        }
-        return check_launch();
-    }
+        return general_fwd<GLin<T>, T, RedItems<T>::pair>(n, xv, yv, saved, ws, s);
+    case ADC_OP_MM2:
+        return general_fwd<GMM2<T>, T, RedItems<T>::mat>(n, xv, yv, saved, ws, s);
     default: return ADC_ERR_UNSUPPORTED;
     }
 }

@@ -15,52 +15,73 @@
 
 namespace adc {
 
-struct NoAux {};
+// One streamed array: the thread's chunk, loaded in fetch() and read in build().
+template <typename E, int ITEMS> struct Chunk { E v[ITEMS]; };
 
-// ------------------------------------------------------------ forward ops --
-template <typename T, int ITEMS> struct FwdAdd {
-    using State = T;
-    using Aux = NoAux;
-    const T *x;
-    T *y;
-    __device__ T identity() const { return T(0); }
-    __device__ T combine(T a, T b) const { return a + b; }
-    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, T(0)); }
-    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+// A streamed array plus its neighbour on one side (x_{i+1} beyond the chunk,
+// or y_{i-1} before it).
+template <typename E, int ITEMS> struct HaloChunk {
+    E v[ITEMS];
+    E halo;
 };
 
-template <typename T, int ITEMS> struct FwdMul {
-    using State = T;
+template <typename E, int ITEMS>
+__device__ __forceinline__ void fetch_next(const E *x, int64_t c0, int64_t n, HaloChunk<E, ITEMS> &r, E fill) {
+    load_chunk(x, c0, n, r.v, fill);
+    r.halo = (c0 + ITEMS < n) ? x[c0 + ITEMS] : fill;
+}
+template <typename E, int ITEMS>
+__device__ __forceinline__ void fetch_prev(const E *y, int64_t c0, int64_t n, HaloChunk<E, ITEMS> &r, E e) {
+    load_chunk(y, c0, n, r.v, e);
+    r.halo = (c0 > 0 && c0 - 1 < n) ? y[c0 - 1] : e;
+}
+// xs[k] = x[c0 + k + 1]  and  ys[k] = y[c0 + k - 1]
+template <typename E, int ITEMS> __device__ __forceinline__ E next_of(const HaloChunk<E, ITEMS> &r, int k) {
+    return (k + 1 < ITEMS) ? r.v[k + 1] : r.halo;
+}
+template <typename E, int ITEMS> __device__ __forceinline__ E prev_of(const HaloChunk<E, ITEMS> &r, int k) {
+    return k > 0 ? r.v[k - 1] : r.halo;
+}
+
+// ------------------------------------------------------------ forward ops --
+// One input array, scanned as is; the state is the element type.
+template <typename E, int ITEMS, class Derived> struct PlainScan {
+    using State = E;
     using Aux = NoAux;
-    const T *x;
-    T *y;
+    using Raw = Chunk<E, ITEMS>;
+    const E *x;
+    E *y;
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(x, c0, n, r.v, static_cast<const Derived *>(this)->identity());
+    }
+    __device__ void build(int64_t, int64_t, const Raw &r, State (&st)[ITEMS], Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = r.v[k];
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const {
+        store_chunk(y, c0, n, st);
+    }
+};
+
+template <typename T, int ITEMS> struct FwdAdd : PlainScan<T, ITEMS, FwdAdd<T, ITEMS>> {
+    __device__ T identity() const { return T(0); }
+    __device__ T combine(T a, T b) const { return a + b; }
+};
+
+template <typename T, int ITEMS> struct FwdMul : PlainScan<T, ITEMS, FwdMul<T, ITEMS>> {
     __device__ T identity() const { return T(1); }
     __device__ T combine(T a, T b) const { return a * b; }
-    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, T(1)); }
-    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
 };
 
 // linFnComp (Fig. 8): (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)
-template <typename T, int ITEMS> struct FwdLin {
-    using State = Pair<T>;
-    using Aux = NoAux;
-    const Pair<T> *x;
-    Pair<T> *y;
-    __device__ State identity() const { return {T(0), T(1)}; }
-    __device__ State combine(const State &a, const State &b) const { return {b.b + b.c * a.b, b.c * a.c}; }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, identity()); }
-    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+template <typename T, int ITEMS> struct FwdLin : PlainScan<Pair<T>, ITEMS, FwdLin<T, ITEMS>> {
+    __device__ Pair<T> identity() const { return {T(0), T(1)}; }
+    __device__ Pair<T> combine(const Pair<T> &a, const Pair<T> &b) const { return {b.b + b.c * a.b, b.c * a.c}; }
 };
 
-template <typename T, int ITEMS> struct FwdMM2 {
-    using State = Mat2<T>;
-    using Aux = NoAux;
-    const Mat2<T> *x;
-    Mat2<T> *y;
-    __device__ State identity() const { return mat_eye<T>(); }
-    __device__ State combine(const State &a, const State &b) const { return mat_mul(a, b); }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &) const { load_chunk(x, c0, n, st, identity()); }
-    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &) const { store_chunk(y, c0, n, st); }
+template <typename T, int ITEMS> struct FwdMM2 : PlainScan<Mat2<T>, ITEMS, FwdMM2<T, ITEMS>> {
+    __device__ Mat2<T> identity() const { return mat_eye<T>(); }
+    __device__ Mat2<T> combine(const Mat2<T> &a, const Mat2<T> &b) const { return mat_mul(a, b); }
 };
 
 // ---------------------------------------------------------------- vjp ops --
@@ -68,12 +89,17 @@ template <typename T, int ITEMS> struct FwdMM2 {
 template <typename T, int ITEMS> struct VjpAdd {
     using State = T;
     using Aux = NoAux;
+    using Raw = Chunk<T, ITEMS>;
     const T *ybar;
     T *xbar;
     int accumulate;
     __device__ T identity() const { return T(0); }
     __device__ T combine(T a, T b) const { return a + b; }
-    __device__ void load(int64_t c0, int64_t n, T (&st)[ITEMS], Aux &) const { load_chunk(ybar, c0, n, st, T(0)); }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const { load_chunk(ybar, c0, n, r.v, T(0)); }
+    __device__ void build(int64_t, int64_t, const Raw &r, T (&st)[ITEMS], Aux &) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) st[k] = r.v[k];
+    }
     __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const Aux &) const {
         if (accumulate) {
             T old[ITEMS], out[ITEMS];
@@ -91,43 +117,34 @@ template <typename T, int ITEMS> struct VjpAdd {
 template <typename T> struct AffS { T v, c; };
 template <typename T> struct AffP { T vb, vc, c; };  // 2-vector value (lin)
 
-// Fetch the coefficient source x_{i+1} for every element of the chunk:
-// xs[k] = x[c0 + k + 1] (identity beyond n).
-template <typename E, int ITEMS>
-__device__ __forceinline__ void load_next(const E *x, int64_t c0, int64_t n, E (&xs)[ITEMS], E fill) {
-    E raw[ITEMS];
-    load_chunk(x, c0, n, raw, fill);
-#pragma unroll
-    for (int k = 0; k + 1 < ITEMS; ++k) xs[k] = raw[k + 1];
-    xs[ITEMS - 1] = (c0 + ITEMS < n) ? x[c0 + ITEMS] : fill;
-}
-
-// Fetch y_{i-1} for every element: ys[k] = y[c0 + k - 1], y_{-1} = e.
-template <typename E, int ITEMS>
-__device__ __forceinline__ void load_prev(const E *y, int64_t c0, int64_t n, E (&ys)[ITEMS], E e) {
-    E raw[ITEMS];
-    load_chunk(y, c0, n, raw, e);
-#pragma unroll
-    for (int k = ITEMS - 1; k > 0; --k) ys[k] = raw[k - 1];
-    ys[0] = (c0 > 0 && c0 - 1 < n) ? y[c0 - 1] : e;
-}
+// Inputs of the recurrence vjps: ybar_i, x_{i+1} (coefficient) and y_{i-1} (map).
+template <typename E, int ITEMS> struct VjpRaw {
+    Chunk<E, ITEMS> yb;
+    HaloChunk<E, ITEMS> x;  // halo = x[c0 + ITEMS]
+    HaloChunk<E, ITEMS> y;  // halo = y[c0 - 1]
+};
 
 // Product scan: J_{i+1} = x_{i+1}; xbar_i = y_{i-1} * lambda_i.
 template <typename T, int ITEMS> struct VjpMul {
     using State = AffS<T>;
+    using Raw = VjpRaw<T, ITEMS>;
     struct Aux { T yprev[ITEMS]; };
     const T *x, *y, *ybar;
     T *xbar;
     int accumulate;
     __device__ State identity() const { return {T(0), T(1)}; }
     __device__ State combine(const State &acc, const State &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
-        T yb[ITEMS], xn[ITEMS];
-        load_chunk(ybar, c0, n, yb, T(0));
-        load_next(x, c0, n, xn, T(1));
-        load_prev(y, c0, n, aux.yprev, T(1));
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(ybar, c0, n, r.yb.v, T(0));
+        fetch_next(x, c0, n, r.x, T(1));
+        fetch_prev(y, c0, n, r.y, T(1));
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k], xn[k]} : identity();
+        for (int k = 0; k < ITEMS; ++k) {
+            aux.yprev[k] = prev_of(r.y, k);
+            st[k] = (c0 + k < n) ? State{r.yb.v[k], next_of(r.x, k)} : identity();
+        }
     }
     __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
         T out[ITEMS];
@@ -142,6 +159,7 @@ template <typename T, int ITEMS> struct VjpMul {
 // bbar_i = lambda.b, cbar_i = lambda.b * B_{i-1} + lambda.c * C_{i-1}, (B,C)_{-1} = (0,1).
 template <typename T, int ITEMS> struct VjpLin {
     using State = AffP<T>;
+    using Raw = VjpRaw<Pair<T>, ITEMS>;
     struct Aux { Pair<T> yprev[ITEMS]; };
     const Pair<T> *x, *y, *ybar;
     Pair<T> *xbar;
@@ -150,14 +168,18 @@ template <typename T, int ITEMS> struct VjpLin {
     __device__ State combine(const State &acc, const State &e) const {
         return {e.vb + e.c * acc.vb, e.vc + e.c * acc.vc, e.c * acc.c};
     }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
-        Pair<T> yb[ITEMS], xn[ITEMS];
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
         const Pair<T> e{T(0), T(1)};
-        load_chunk(ybar, c0, n, yb, Pair<T>{T(0), T(0)});
-        load_next(x, c0, n, xn, e);
-        load_prev(y, c0, n, aux.yprev, e);
+        load_chunk(ybar, c0, n, r.yb.v, Pair<T>{T(0), T(0)});
+        fetch_next(x, c0, n, r.x, e);
+        fetch_prev(y, c0, n, r.y, e);
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k].b, yb[k].c, xn[k].c} : identity();
+        for (int k = 0; k < ITEMS; ++k) {
+            aux.yprev[k] = prev_of(r.y, k);
+            st[k] = (c0 + k < n) ? State{r.yb.v[k].b, r.yb.v[k].c, next_of(r.x, k).c} : identity();
+        }
     }
     __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
         Pair<T> out[ITEMS];
@@ -177,6 +199,7 @@ template <typename T> struct AffM { Mat2<T> v, c; };
 
 template <typename T, int ITEMS> struct VjpMM2 {
     using State = AffM<T>;
+    using Raw = VjpRaw<Mat2<T>, ITEMS>;
     struct Aux { Mat2<T> yprev[ITEMS]; };
     const Mat2<T> *x, *y, *ybar;
     Mat2<T> *xbar;
@@ -185,13 +208,17 @@ template <typename T, int ITEMS> struct VjpMM2 {
     __device__ State combine(const State &acc, const State &e) const {
         return {mat_add(e.v, mat_mul(acc.v, e.c)), mat_mul(acc.c, e.c)};
     }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
-        Mat2<T> yb[ITEMS], xn[ITEMS];
-        load_chunk(ybar, c0, n, yb, mat_zero<T>());
-        load_next(x, c0, n, xn, mat_eye<T>());
-        load_prev(y, c0, n, aux.yprev, mat_eye<T>());
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(ybar, c0, n, r.yb.v, mat_zero<T>());
+        fetch_next(x, c0, n, r.x, mat_eye<T>());
+        fetch_prev(y, c0, n, r.y, mat_eye<T>());
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) st[k] = (c0 + k < n) ? State{yb[k], mat_t(xn[k])} : identity();
+        for (int k = 0; k < ITEMS; ++k) {
+            aux.yprev[k] = prev_of(r.y, k);
+            st[k] = (c0 + k < n) ? State{r.yb.v[k], mat_t(next_of(r.x, k))} : identity();
+        }
     }
     __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
         Mat2<T> out[ITEMS];
@@ -206,7 +233,8 @@ template <typename T, int ITEMS> struct VjpMM2 {
 };
 
 // -------------------------------------------------------------- launching --
-// Items per thread: 64 bytes of each streamed array per thread.
+// Items per thread: 64 bytes of each streamed array per thread (32 for the
+// three-array vjps), so a tile is 16 KB (8 KB) per array.
 template <typename T> struct Items {
     static constexpr int scalar = 64 / sizeof(T);       // add / mul
     static constexpr int pair = 64 / (2 * sizeof(T));   // lin
@@ -245,25 +273,38 @@ size_t scan_ws_bytes(adc_op op, adc_dtype dt, int64_t n) {
     return dt == ADC_F64 ? scan_ws_t<double>(op, n) : scan_ws_t<float>(op, n);
 }
 
+template <class Op, int ITEMS, bool REVERSE>
+static adc_status launch(const Op &o, int64_t n, void *ws, cudaStream_t s) {
+    return run_scan<Op, ITEMS, REVERSE>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+}
+
 template <typename T>
 static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
     using I = Items<T>;
     switch (op) {
     case ADC_OP_ADD: {
-        FwdAdd<T, I::scalar> o{static_cast<const T *>(x), static_cast<T *>(y)};
-        return run_scan<decltype(o), I::scalar, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        FwdAdd<T, I::scalar> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::scalar, false>(o, n, ws, s);
     }
     case ADC_OP_MUL: {
-        FwdMul<T, I::scalar> o{static_cast<const T *>(x), static_cast<T *>(y)};
-        return run_scan<decltype(o), I::scalar, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        FwdMul<T, I::scalar> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::scalar, false>(o, n, ws, s);
     }
     case ADC_OP_LIN: {
-        FwdLin<T, I::pair> o{static_cast<const Pair<T> *>(x), static_cast<Pair<T> *>(y)};
-        return run_scan<decltype(o), I::pair, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        FwdLin<T, I::pair> o;
+        o.x = static_cast<const Pair<T> *>(x);
+        o.y = static_cast<Pair<T> *>(y);
+        return launch<decltype(o), I::pair, false>(o, n, ws, s);
     }
     case ADC_OP_MM2: {
-        FwdMM2<T, I::mat> o{static_cast<const Mat2<T> *>(x), static_cast<Mat2<T> *>(y)};
-        return run_scan<decltype(o), I::mat, false>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        FwdMM2<T, I::mat> o;
+        o.x = static_cast<const Mat2<T> *>(x);
+        o.y = static_cast<Mat2<T> *>(y);
+        return launch<decltype(o), I::mat, false>(o, n, ws, s);
     }
     default: return ADC_ERR_UNSUPPORTED;
     }
@@ -280,22 +321,22 @@ static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y,
     switch (op) {
     case ADC_OP_ADD: {
         VjpAdd<T, I::scalar> o{static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
-        return run_scan<decltype(o), I::scalar, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        return launch<decltype(o), I::scalar, true>(o, n, ws, s);
     }
     case ADC_OP_MUL: {
         VjpMul<T, I::vscalar> o{static_cast<const T *>(x), static_cast<const T *>(y), static_cast<const T *>(ybar),
                                 static_cast<T *>(xbar), acc};
-        return run_scan<decltype(o), I::vscalar, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        return launch<decltype(o), I::vscalar, true>(o, n, ws, s);
     }
     case ADC_OP_LIN: {
         VjpLin<T, I::vpair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
                               static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
-        return run_scan<decltype(o), I::vpair, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        return launch<decltype(o), I::vpair, true>(o, n, ws, s);
     }
     case ADC_OP_MM2: {
         VjpMM2<T, I::vmat> o{static_cast<const Mat2<T> *>(x), static_cast<const Mat2<T> *>(y),
                              static_cast<const Mat2<T> *>(ybar), static_cast<Mat2<T> *>(xbar), acc};
-        return run_scan<decltype(o), I::vmat, true>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
+        return launch<decltype(o), I::vmat, true>(o, n, ws, s);
     }
     default: return ADC_ERR_UNSUPPORTED;
     }

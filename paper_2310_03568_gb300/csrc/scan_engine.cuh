@@ -1,14 +1,18 @@
 // Single-pass scan with decoupled look-back (Merrill & Garland), forward or
-// reverse, for any associative operator given as an Op class.
+// reverse, for any associative operator given as an Op class.  One tile per
+// block; the tile index comes from an atomic counter, so every tile a block
+// waits on belongs to a block that is already running.
 //
 // An Op provides
 //   using State;                         the scanned value
-//   struct Aux;                          per-thread data carried from load to store
+//   struct Raw;                          this thread's loaded data for one tile
+//   struct Aux;                          per-thread data carried from build to store
 //   State identity() const;
 //   State combine(const State& earlier, const State& later) const;   (logical order)
-//   void  load (int64_t c0, int64_t n, State (&st)[ITEMS], Aux&) const;
-//         fills st with the elements [c0, c0+ITEMS) in PHYSICAL order,
-//         identity() beyond n
+//   void  fetch(int64_t c0, int64_t n, Raw&) const;
+//         issues the loads of elements [c0, c0+ITEMS) (and any halo)
+//   void  build(int64_t c0, int64_t n, const Raw&, State (&st)[ITEMS], Aux&) const;
+//         the elements' states in PHYSICAL order, identity() beyond n
 //   void  store(int64_t c0, int64_t n, const State (&inc)[ITEMS], const Aux&) const;
 //         receives the inclusive scan values of those elements.
 //
@@ -16,13 +20,16 @@
 // tile T-1-t and the scan is inclusive from the right, i.e. a forward scan of
 // the reversed array (the reversals of Figs 2, 4 and 7 are index maps here).
 //
-// Protocol per tile: claim a tile index from an atomic counter (so every tile
-// a block waits on is already resident or finished), reduce the tile, publish
-// its aggregate (flag AGG), look back over predecessors with one warp, 32
-// tiles per step, until a tile with an inclusive prefix (flag INC) is found,
-// publish the inclusive prefix, then rescan the tile from registers.  Every
-// wait is bounded: on expiry the tile publishes ERROR, the error word gets
-// kErrTimeout and the block leaves without storing.
+// Protocol per tile: reduce the tile, publish its aggregate (tag AGG), look
+// back over predecessors with the whole block -- each of the 8 warps polls 32
+// tiles, so 256 predecessors per step -- until a tile with an inclusive
+// prefix (tag INC) is found, publish the inclusive prefix, then rescan the
+// tile from registers.  With many tiles in flight the inclusive-prefix
+// frontier advances by one look-back window per memory round trip, so the
+// window is made wide (256 tiles) and a poll is one round trip (tagged words
+// below).  Every wait is bounded: on expiry the
+// tile publishes ERROR, the error word gets kErrTimeout and the tile is not
+// stored; later tiles see ERROR and stop waiting at once.
 #pragma once
 
 #include "common.cuh"
@@ -30,128 +37,221 @@
 
 namespace adc {
 
+struct NoAux {};
+
+// ---------------------------------------------------- tagged tile status --
+// A published tile state S is stored as K = sizeof(S)/4 64-bit words, each
+// (tag << 32 | one 32-bit word of S), in two arrays: aggregates (tag AGG) and
+// inclusive prefixes (tag INC; ERROR marks a failed tile).  Every word is
+// written and read with single-copy-atomic 64-bit accesses, so a reader that
+// sees the same non-zero tag in all K words holds a consistent state -- one
+// round trip per poll, no separate flag and no acquire/release pair.  Mixed
+// tags mean a write in progress: poll again.
+template <typename S> struct Tagged {
+    static constexpr int K = sizeof(S) / 4;
+    static_assert(sizeof(S) % 4 == 0, "state must be made of 32-bit words");
+};
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+template <typename S> __device__ __forceinline__ void publish(unsigned long long *slot, const S &v, unsigned tag) {
+    const unsigned *w = reinterpret_cast<const unsigned *>(&v);
+#pragma unroll
+    for (int k = 0; k < Tagged<S>::K; ++k) st_relaxed_u64(slot + k, ((unsigned long long)tag << 32) | w[k]);
+}
+__device__ __forceinline__ void publish_tag(unsigned long long *slot, int K, unsigned tag) {
+    for (int k = 0; k < K; ++k) st_relaxed_u64(slot + k, (unsigned long long)tag << 32);
+}
+
+// One poll of tile j: returns kFlagInc / kFlagAgg with the state in *out,
+// kFlagError if the tile failed, or kFlagNone if nothing complete is visible.
+template <typename S>
+__device__ __forceinline__ unsigned poll_tile(const unsigned long long *agg, const unsigned long long *inc, S *out) {
+    constexpr int K = Tagged<S>::K;
+    unsigned long long a[K], b[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        b[k] = ld_relaxed_u64(inc + k);
+        a[k] = ld_relaxed_u64(agg + k);
+    }
+    unsigned *w = reinterpret_cast<unsigned *>(out);
+    bool inc_ok = true, agg_ok = true, err = false;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        inc_ok &= (unsigned)(b[k] >> 32) == kFlagInc;
+        agg_ok &= (unsigned)(a[k] >> 32) == kFlagAgg;
+        err |= (unsigned)(b[k] >> 32) == kFlagError;
+    }
+    if (err) return kFlagError;
+    if (inc_ok) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = (unsigned)b[k];
+        return kFlagInc;
+    }
+    if (agg_ok) {
+#pragma unroll
+        for (int k = 0; k < K; ++k) w[k] = (unsigned)a[k];
+        return kFlagAgg;
+    }
+    return kFlagNone;
+}
+
+// Bounded spin until tile j shows a complete state.
+template <typename S>
+__device__ __forceinline__ unsigned wait_tile(const unsigned long long *agg, const unsigned long long *inc, S *out,
+                                              long long limit) {
+    long long it = 0;
+    unsigned f = poll_tile(agg, inc, out);
+    while (f == kFlagNone) {
+        if (++it > limit) return kFlagError;
+        __nanosleep(32);
+        f = poll_tile(agg, inc, out);
+    }
+    return f;
+}
+
 template <class Op, int THREADS, int ITEMS, bool REVERSE>
 __global__ void __launch_bounds__(THREADS)
-k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned *__restrict__ flags,
-       typename Op::State *__restrict__ agg, typename Op::State *__restrict__ inc, const DevCtl ctl) {
+k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long *__restrict__ aggw,
+       unsigned long long *__restrict__ incw, const DevCtl ctl) {
     using S = typename Op::State;
     constexpr int TILE = THREADS * ITEMS;
     constexpr int NW = THREADS / kWarp;
+    constexpr int K = Tagged<S>::K;
     static_assert(NW <= kWarp, "block too large");
     __shared__ unsigned s_tile;
-    __shared__ int s_abort;
-    __shared__ S s_warp[NW];
+    __shared__ S s_warp[NW];   // per-warp totals, then per-warp exclusive prefixes
+    __shared__ S s_lbv[NW];    // look-back: each warp's combined window
+    __shared__ int s_lbinc[NW], s_lberr[NW];
+    __shared__ S s_total;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid == 0) {
-        s_tile = atomicAdd(ctl.counter, 1u);
-        s_abort = 0;
-    }
+    const int jc = REVERSE ? (THREADS - 1 - tid) : tid;
+
+    // One tile per block, claimed when the block starts: its aggregate is
+    // published one load latency after the claim, so no tile a successor
+    // waits on is ever held back behind other work.
+    if (tid == 0) s_tile = atomicAdd(ctl.counter, 1u);
     __syncthreads();
     const long long t = s_tile;
-    if (t == ctl.stall_tile) return;  // fault injection: this tile never publishes
+    {
+        const int64_t p = REVERSE ? (num_tiles - 1 - t) : t;
+        const int64_t c0 = p * (int64_t)TILE + (int64_t)jc * ITEMS;
+        typename Op::Raw raw;
+        op.fetch(c0, n, raw);
+        S st[ITEMS];
+        typename Op::Aux aux;
+        op.build(c0, n, raw, st, aux);
 
-    const int64_t p = REVERSE ? (num_tiles - 1 - t) : t;
-    const int jc = REVERSE ? (THREADS - 1 - tid) : tid;
-    const int64_t c0 = p * (int64_t)TILE + (int64_t)jc * ITEMS;
-
-    S st[ITEMS];
-    typename Op::Aux aux;
-    op.load(c0, n, st, aux);
-
-    S a = op.identity();
+        if (t != ctl.stall_tile) {  // fault injection: this tile never publishes
+            // ---- tile reduction and its publication as an aggregate
+            S a = op.identity();
 #pragma unroll
-    for (int k = 0; k < ITEMS; ++k) a = op.combine(a, st[REVERSE ? ITEMS - 1 - k : k]);
-    const S winc = warp_inclusive_scan(op, a);
-    if (lane == kWarp - 1) s_warp[warp] = winc;
-    __syncthreads();
-    S wexc = shfl_up(winc, 1);
-    if (lane == 0) wexc = op.identity();
-
-    if (warp == 0) {
-        const S w = (lane < NW) ? s_warp[lane] : op.identity();
-        const S wi = warp_inclusive_scan(op, w);
-        const S total = shfl_idx(wi, NW - 1);
-        S wex = shfl_up(wi, 1);
-        if (lane == 0) wex = op.identity();
-        S prefix = op.identity();
-        bool abort = false;
-        if (t == 0) {
-            if (lane == 0) {
-                inc[0] = total;
-                st_release_u32(&flags[0], kFlagInc);
-            }
-        } else {
-            if (lane == 0) {
-                agg[t] = total;
-                st_release_u32(&flags[t], kFlagAgg);
-            }
-            long long base = t - 1;
-            S run = op.identity();
-            while (true) {
-                const long long tj = base - lane;  // lane 0: nearest predecessor
-                unsigned f = kFlagInc;
-                if (tj >= 0) f = spin_flag(&flags[tj], ctl.spin_limit);
-                if (__any_sync(0xffffffffu, f == kFlagError)) {
-                    abort = true;
-                    break;
-                }
-                S v = op.identity();
-                if (tj >= 0) v = (f == kFlagInc) ? load_cg(&inc[tj]) : load_cg(&agg[tj]);
-                const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
-                const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
-                if (lane > stop) v = op.identity();
-                // ordered reduction: farthest (highest lane) first
-#pragma unroll
-                for (int o = 1; o < kWarp; o <<= 1) {
-                    const S other = shfl_down(v, o);
-                    if (lane + o < kWarp) v = op.combine(other, v);
-                }
-                v = shfl_idx(v, 0);
-                run = op.combine(v, run);
-                if (incmask) break;
-                base -= kWarp;
-            }
-            if (abort) {
+            for (int k = 0; k < ITEMS; ++k) a = op.combine(a, st[REVERSE ? ITEMS - 1 - k : k]);
+            const S winc = warp_inclusive_scan(op, a);
+            if (lane == kWarp - 1) s_warp[warp] = winc;
+            __syncthreads();
+            S wexc = shfl_up(winc, 1);
+            if (lane == 0) wexc = op.identity();
+            if (warp == 0) {
+                const S w = (lane < NW) ? s_warp[lane] : op.identity();
+                const S wi = warp_inclusive_scan(op, w);
+                S wex = shfl_up(wi, 1);
+                if (lane == 0) wex = op.identity();
+                const S total = shfl_idx(wi, NW - 1);
                 if (lane == 0) {
-                    st_release_u32(&flags[t], kFlagError);
-                    set_error(ctl.err, kErrTimeout);
-                    s_abort = 1;
+                    s_total = total;
+                    publish(aggw + t * K, total, kFlagAgg);
+                    if (t == 0) publish(incw, total, kFlagInc);
+                }
+                if (lane < NW) s_warp[lane] = wex;
+            }
+            // ---- block-wide look-back: 32 x NW predecessors per step
+            S prefix = op.identity();
+            bool abort = false;
+            if (t > 0) {
+                long long base = t - 1;
+                while (true) {
+                    const long long tj = base - (long long)kWarp * warp - lane;  // warp 0 lane 0: nearest
+                    S v = op.identity();
+                    unsigned f = kFlagInc;
+                    if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
+                    const bool err = __any_sync(0xffffffffu, f == kFlagError);
+                    const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
+                    const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
+                    if (lane > stop) v = op.identity();
+#pragma unroll
+                    for (int o = 1; o < kWarp; o <<= 1) {  // ordered: farthest (highest lane) first
+                        const S other = shfl_down(v, o);
+                        if (lane + o < kWarp) v = op.combine(other, v);
+                    }
+                    if (lane == 0) {
+                        s_lbv[warp] = v;
+                        s_lbinc[warp] = incmask != 0;
+                        s_lberr[warp] = err;
+                    }
+                    __syncthreads();
+                    bool found = false;
+                    for (int w = 0; w < NW; ++w) {
+                        if (s_lberr[w]) {
+                            abort = true;
+                            break;
+                        }
+                        prefix = op.combine(s_lbv[w], prefix);
+                        if (s_lbinc[w]) {
+                            found = true;
+                            break;
+                        }
+                    }
+                    __syncthreads();
+                    if (abort || found) break;
+                    base -= (long long)kWarp * NW;
+                }
+                if (tid == 0) {
+                    if (abort) {
+                        publish_tag(incw + t * K, K, kFlagError);
+                        set_error(ctl.err, kErrTimeout);
+                    } else {
+                        publish(incw + t * K, op.combine(prefix, s_total), kFlagInc);
+                    }
                 }
             } else {
-                prefix = run;
-                if (lane == 0) {
-                    inc[t] = op.combine(prefix, total);
-                    st_release_u32(&flags[t], kFlagInc);
+                __syncthreads();  // s_warp prefixes written by warp 0 are visible
+            }
+            if (!abort) {
+                S run = op.combine(op.combine(prefix, s_warp[warp]), wexc);
+#pragma unroll
+                for (int k = 0; k < ITEMS; ++k) {
+                    const int kk = REVERSE ? ITEMS - 1 - k : k;
+                    run = op.combine(run, st[kk]);
+                    st[kk] = run;
                 }
+                op.store(c0, n, st, aux);
             }
         }
-        if (lane < NW) s_warp[lane] = op.combine(prefix, wex);
     }
-    __syncthreads();
-    if (s_abort) return;
-
-    S run = op.combine(s_warp[warp], wexc);
-#pragma unroll
-    for (int k = 0; k < ITEMS; ++k) {
-        const int kk = REVERSE ? ITEMS - 1 - k : k;
-        run = op.combine(run, st[kk]);
-        st[kk] = run;
-    }
-    op.store(c0, n, st, aux);
 }
 
-// Layout of one scan launch's region of the workspace: [flags][agg][inc].
+// Layout of one scan launch's region of the workspace: tagged aggregates and
+// tagged inclusive prefixes, 8 bytes per 32-bit state word, both zeroed before
+// the launch (tag 0 = nothing published).
 struct ScanWs {
-    size_t flags_off, agg_off, inc_off, bytes;
+    size_t agg_off, inc_off, bytes;
 };
 
 inline ScanWs scan_ws_layout(int64_t num_tiles, size_t state_bytes) {
     ScanWs w;
-    w.flags_off = 0;
-    w.agg_off = align_up(w.flags_off + (size_t)num_tiles * 4, 256);
-    w.inc_off = align_up(w.agg_off + (size_t)num_tiles * state_bytes, 256);
-    w.bytes = align_up(w.inc_off + (size_t)num_tiles * state_bytes, 256);
+    const size_t words = (size_t)num_tiles * (state_bytes / 4) * 8;
+    w.agg_off = 0;
+    w.inc_off = align_up(words, 256);
+    w.bytes = align_up(w.inc_off + words, 256);
     return w;
 }
 
@@ -172,12 +272,11 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     const int64_t T = Sh::tiles(n);
     const ScanWs L = scan_ws_layout(T, sizeof(typename Op::State));
     char *w = static_cast<char *>(region);
-    if (cudaMemsetAsync(w, 0, L.agg_off, s) != cudaSuccess) return ADC_ERR_CUDA;
+    if (cudaMemsetAsync(w, 0, L.bytes, s) != cudaSuccess) return ADC_ERR_CUDA;
     const DevCtl ctl = make_ctl(ws, slot);
     k_scan<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)T, kScanThreads, 0, s>>>(
-        op, n, T, reinterpret_cast<unsigned *>(w + L.flags_off),
-        reinterpret_cast<typename Op::State *>(w + L.agg_off), reinterpret_cast<typename Op::State *>(w + L.inc_off),
-        ctl);
+        op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
+        reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
     return check_launch();
 }
 

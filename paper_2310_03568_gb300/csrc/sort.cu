@@ -73,14 +73,18 @@ k_sort_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m,
 template <int ITEMS> struct ExclAddI32 {
     using State = int32_t;
     struct Aux { int32_t own[ITEMS]; };
+    struct Raw { int32_t v[ITEMS]; };
     const int32_t *in;
     int32_t *out;
     __device__ int32_t identity() const { return 0; }
     __device__ int32_t combine(int32_t a, int32_t b) const { return a + b; }
-    __device__ void load(int64_t c0, int64_t n, int32_t (&st)[ITEMS], Aux &aux) const {
-        load_chunk(in, c0, n, st, 0);
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const { load_chunk(in, c0, n, r.v, 0); }
+    __device__ void build(int64_t, int64_t, const Raw &r, int32_t (&st)[ITEMS], Aux &aux) const {
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) aux.own[k] = st[k];
+        for (int k = 0; k < ITEMS; ++k) {
+            st[k] = r.v[k];
+            aux.own[k] = r.v[k];
+        }
     }
     __device__ void store(int64_t c0, int64_t n, const int32_t (&st)[ITEMS], const Aux &aux) const {
         int32_t o[ITEMS];
@@ -189,16 +193,27 @@ template <typename T, int ITEMS> struct SegFwd {
     __device__ State combine(const State &a, const State &b) const {
         return {b.f ? b.v : lin(a.v, b.v), a.f | b.f, 0u};
     }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
-        load_chunk(sk, c0, n, aux.k, (int32_t)0);
-        load_chunk(sv, c0, n, aux.v, lin_id<T>());
-        const int32_t kprev = (c0 > 0 && c0 <= n) ? sk[c0 - 1] : -1;
-        const Pair<T> vprev = (c0 > 0 && c0 <= n) ? sv[c0 - 1] : lin_id<T>();
-        aux.knext = (c0 + ITEMS < n) ? sk[c0 + ITEMS] : -1;
+    struct Raw {
+        int32_t k[ITEMS];
+        int32_t kprev, knext;
+        Pair<T> v[ITEMS];
+        Pair<T> vprev;
+    };
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(sk, c0, n, r.k, (int32_t)0);
+        load_chunk(sv, c0, n, r.v, lin_id<T>());
+        r.kprev = (c0 > 0 && c0 <= n) ? sk[c0 - 1] : -1;
+        r.vprev = (c0 > 0 && c0 <= n) ? sv[c0 - 1] : lin_id<T>();
+        r.knext = (c0 + ITEMS < n) ? sk[c0 + ITEMS] : -1;
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
+        aux.knext = r.knext;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const bool start = (c0 + j == 0) || ((j == 0 ? kprev : aux.k[j - 1]) != aux.k[j]);
-            const Pair<T> prev = (j == 0) ? vprev : aux.v[j - 1];
+            aux.k[j] = r.k[j];
+            aux.v[j] = r.v[j];
+            const bool start = (c0 + j == 0) || ((j == 0 ? r.kprev : r.k[j - 1]) != r.k[j]);
+            const Pair<T> prev = (j == 0) ? r.vprev : r.v[j - 1];
             st[j] = (c0 + j < n) ? State{start ? lin_id<T>() : prev, start ? 1u : 0u, 0u} : identity();
         }
     }
@@ -248,16 +263,27 @@ template <typename T, int ITEMS> struct SegRev {
     __device__ State combine(const State &acc, const State &e) const {
         return {e.f ? e.v : lin(e.v, acc.v), acc.f | e.f, 0u};
     }
-    __device__ void load(int64_t c0, int64_t n, State (&st)[ITEMS], Aux &aux) const {
-        load_chunk(sk, c0, n, aux.k, (int32_t)0);
-        load_chunk(sv, c0, n, aux.v, lin_id<T>());
-        aux.knext = (c0 + ITEMS < n) ? sk[c0 + ITEMS] : -1;
-        const Pair<T> vnext = (c0 + ITEMS < n) ? sv[c0 + ITEMS] : lin_id<T>();
+    struct Raw {
+        int32_t k[ITEMS];
+        int32_t knext;
+        Pair<T> v[ITEMS];
+        Pair<T> vnext;
+    };
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(sk, c0, n, r.k, (int32_t)0);
+        load_chunk(sv, c0, n, r.v, lin_id<T>());
+        r.knext = (c0 + ITEMS < n) ? sk[c0 + ITEMS] : -1;
+        r.vnext = (c0 + ITEMS < n) ? sv[c0 + ITEMS] : lin_id<T>();
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
+        aux.knext = r.knext;
 #pragma unroll
         for (int j = 0; j < ITEMS; ++j) {
-            const int32_t kn = (j + 1 < ITEMS) ? aux.k[j + 1] : aux.knext;
-            const bool end = (c0 + j == n - 1) || (kn != aux.k[j]);
-            const Pair<T> nxt = (j + 1 < ITEMS) ? aux.v[j + 1] : vnext;
+            aux.k[j] = r.k[j];
+            aux.v[j] = r.v[j];
+            const int32_t kn = (j + 1 < ITEMS) ? r.k[j + 1] : r.knext;
+            const bool end = (c0 + j == n - 1) || (kn != r.k[j]);
+            const Pair<T> nxt = (j + 1 < ITEMS) ? r.v[j + 1] : r.vnext;
             st[j] = (c0 + j < n) ? State{end ? lin_id<T>() : nxt, end ? 1u : 0u, 0u} : identity();
         }
     }
