@@ -285,50 +285,87 @@ def run_ours(args, world, rank, local):
 
 
 def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
-    """Same metric through the C-ABI calls with host buffers: H2D of every
-    instance's inputs and D2H of its results inside the timed region."""
+    """Same metric through the C-ABI calls with host buffers: every step copies
+    its inputs (4 key arrays, 3 value arrays, 4 histogram adjoints) from pinned
+    host memory and reads every instance's results (histogram and value
+    adjoint) back, inside the timed region.  Copies run on their own streams and
+    overlap the compute of other instances (events order each buffer's use)."""
     import torch
 
     from paper_2310_03568_gb300 import adcomb
     pin_k = {m: torch.from_numpy(keys_h[m]).pin_memory() for m in BINS}
     pin_v = {op: torch.from_numpy(vals_h[op]).pin_memory() for op in OPS}
     pin_h = {m: torch.from_numpy(hbar_h[m]).pin_memory() for m in BINS}
-    out_h = {m: torch.empty(m, dtype=torch.float32).pin_memory() for m in BINS}
-    out_v = torch.empty(n, dtype=torch.float32).pin_memory()
-    k_d = torch.empty(n, dtype=torch.int32, device=dev)
-    v_d = torch.empty(n, dtype=torch.float32, device=dev)
+    inst = [(op, m) for m in BINS for op in OPS]
+    out_h = {i: torch.empty(i[1], dtype=torch.float32).pin_memory() for i in inst}
+    out_v = {i: torch.empty(n, dtype=torch.float32).pin_memory() for i in inst}
+    k_d = {m: torch.empty(n, dtype=torch.int32, device=dev) for m in BINS}
+    v_d = {op: torch.empty(n, dtype=torch.float32, device=dev) for op in OPS}
     hb_d = {m: torch.empty(m, dtype=torch.float32, device=dev) for m in BINS}
-    vbar = torch.empty(n, dtype=torch.float32, device=dev)
+    hist_d = {i: torch.empty(i[1], dtype=torch.float32, device=dev) for i in inst}
+    vb_d = {i: torch.empty(n, dtype=torch.float32, device=dev) for i in inst}
+    comp = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()  # noqa: E731
+    prev_done = None                      # compute of the previous step (inputs free)
+    prev_read = {i: None for i in inst}   # D2H of the previous step (outputs free)
     h2d = d2h = 0
 
     def step():
-        nonlocal h2d, d2h
+        nonlocal prev_done, h2d, d2h
         h2d = d2h = 0
-        for m in BINS:
-            k_d.copy_(pin_k[m], non_blocking=True)
-            hb_d[m].copy_(pin_h[m], non_blocking=True)
-            h2d += 4 * n + 4 * m
-            for op in OPS:
-                v_d.copy_(pin_v[op], non_blocking=True)
-                h2d += 4 * n
-                adcomb.hist_fwd(op, m, k_d, v_d, None, hist[m], saved[(op, m)], ws=ws)
-                adcomb.hist_vjp(op, m, k_d, v_d, None, hist[m], saved[(op, m)], hb_d[m], valsbar=vbar, ws=ws)
-                out_h[m].copy_(hist[m], non_blocking=True)
-                out_v.copy_(vbar, non_blocking=True)
-                d2h += 4 * m + 4 * n
+        ready_k, ready_v = {}, {}
+        with torch.cuda.stream(s_in):
+            if prev_done is not None:
+                s_in.wait_event(prev_done)
+            order = [("k", BINS[0])] + [("v", op) for op in OPS] + [("k", m) for m in BINS[1:]]
+            for kind, key in order:
+                if kind == "k":
+                    k_d[key].copy_(pin_k[key], non_blocking=True)
+                    hb_d[key].copy_(pin_h[key], non_blocking=True)
+                    h2d += 4 * n + 4 * key
+                    ready_k[key] = ev()
+                    ready_k[key].record(s_in)
+                else:
+                    v_d[key].copy_(pin_v[key], non_blocking=True)
+                    h2d += 4 * n
+                    ready_v[key] = ev()
+                    ready_v[key].record(s_in)
+        done = {}
+        for op, m in inst:
+            comp.wait_event(ready_k[m])
+            comp.wait_event(ready_v[op])
+            if prev_read[(op, m)] is not None:
+                comp.wait_event(prev_read[(op, m)])
+            adcomb.hist_fwd(op, m, k_d[m], v_d[op], None, hist_d[(op, m)], saved[(op, m)], ws=ws)
+            adcomb.hist_vjp(op, m, k_d[m], v_d[op], None, hist_d[(op, m)], saved[(op, m)], hb_d[m],
+                            valsbar=vb_d[(op, m)], ws=ws)
+            done[(op, m)] = ev()
+            done[(op, m)].record(comp)
+        prev_done = done[inst[-1]]
+        with torch.cuda.stream(s_out):
+            for i in inst:
+                s_out.wait_event(done[i])
+                out_h[i].copy_(hist_d[i], non_blocking=True)
+                out_v[i].copy_(vb_d[i], non_blocking=True)
+                d2h += 4 * i[1] + 4 * n
+                prev_read[i] = ev()
+                prev_read[i].record(s_out)
 
     step()
     torch.cuda.synchronize()
-    steps = max(1, min(args.steps, 3))
+    steps = max(1, min(args.steps, 5))
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
+    a.record(comp)
     for _ in range(steps):
         step()
-    b.record()
+    comp.wait_stream(s_out)
+    b.record(comp)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     return {"value": world * len(BINS) * len(OPS) * n / (ms * 1e-3), "unit": "elements/s",
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms}
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms,
+            "overlap": "H2D and D2H on their own streams, ordered by events against the compute stream"}
 
 
 def run_batched(dev, seed=4):
@@ -412,10 +449,14 @@ def run_kernels(args):
         y = adcomb.scan_fwd(op, x, ws=ws)
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
-        row(f"scan {op} fwd {np.dtype(dt).name}", n, 2 * n * es, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
         vb_bytes = (2 if op == "add" else 4) * n * es
-        row(f"scan {op} vjp {np.dtype(dt).name}", n, vb_bytes,
-            timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        for eng, label in ((2, "ranges"), (1, "per-tile")):
+            adcomb.debug_set_scan_engine(eng)
+            row(f"scan {op} fwd {np.dtype(dt).name} [{label}]", n, 2 * n * es,
+                timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
+            row(f"scan {op} vjp {np.dtype(dt).name} [{label}]", n, vb_bytes,
+                timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        adcomb.debug_set_scan_engine(0)
         del x, y, yb, xb
     for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000)]:
         x = torch.from_numpy(synth.scan_values(g, "mm2_orth" if op == "mm2" else "add", n)).to(dev)

@@ -289,6 +289,14 @@ void adc_set_spin_limit(int64_t iterations);
 void adc_debug_set_stall_tile(int64_t tile);
 
 /*
+ * Test hook: scan engine selection -- 0 automatic (range-partitioned for large
+ * n, per-tile look-back otherwise), 1 per-tile look-back only, 2 range-
+ * partitioned wherever it applies.  In the fault-injection hook above, the
+ * "tile" of the range-partitioned engine is a range.
+ */
+void adc_debug_set_scan_engine(int engine);
+
+/*
  * Test hook: force the forward histogram strategy of ADD/MUL/MIN/MAX
  * (0: per-warp shared-memory copies, 1: one shared-memory copy per block,
  * 2: global atomics) where the histogram fits it; -1 (default) chooses

@@ -62,6 +62,7 @@ def lib():
                 "adc_set_spin_limit": ([i64], None),
                 "adc_debug_set_stall_tile": ([i64], None),
                 "adc_debug_force_hist_strategy": ([i32], None),
+                "adc_debug_set_scan_engine": ([i32], None),
                 "adc_status_string": ([i32], ctypes.c_char_p),
                 "adc_version": ([], ctypes.c_char_p),
             }
@@ -250,6 +251,11 @@ def debug_set_stall_tile(tile):
 
 def debug_force_hist_strategy(strategy):
     lib().adc_debug_force_hist_strategy(int(strategy))
+
+
+def debug_set_scan_engine(engine):
+    """0 automatic, 1 per-tile look-back only, 2 range-partitioned wherever it applies."""
+    lib().adc_debug_set_scan_engine(int(engine))
 
 
 def status_string(code):

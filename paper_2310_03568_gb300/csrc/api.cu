@@ -10,6 +10,7 @@ namespace adc {
 
 static long long g_spin_limit = 1ll << 22;
 static long long g_stall_tile = -1;
+int g_scan_engine = 0;
 
 DevCtl make_ctl(void *ws, int slot) {
     DevCtl c;
@@ -176,7 +177,7 @@ adc_status adc_hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int
     if (op == ADC_OP_MM2) return ADC_ERR_UNSUPPORTED;
     if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(histbar, m) || !arr_ok(valsbar, n)) return ADC_ERR_INVALID_ARG;
-    if ((op == ADC_OP_ADD || op == ADC_OP_MUL) && !arr_ok(keys, n)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_LIN && !arr_ok(keys, n)) return ADC_ERR_INVALID_ARG;
     if (op == ADC_OP_MUL && !arr_ok(vals, n)) return ADC_ERR_INVALID_ARG;
     if ((hist0 != nullptr && !aligned(hist0, 16)) || (hist0bar != nullptr && !aligned(hist0bar, 16)))
         return ADC_ERR_INVALID_ARG;
@@ -199,5 +200,7 @@ adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream)
 void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1ll << 22) : iterations; }
 
 void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
+
+void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 2) ? engine : 0; }
 
 }  // extern "C"

@@ -258,15 +258,17 @@ k_hist_sel_smem(const int32_t *__restrict__ keys, const float *__restrict__ vals
 
 template <bool MAX>
 __global__ void k_hist_sel_global(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n,
-                                  const int64_t m, unsigned long long *__restrict__ tab) {
-    // 8 reads of the current keys in flight, then the atomics that can still win
+                                  const int64_t m, unsigned long long *__restrict__ tab, const int filter) {
+    // With many values per bin: 8 reads of the current keys in flight, then
+    // only the atomics that can still win.  With few values per bin most
+    // updates win anyway: issue the (fire-and-forget) atomic directly.
     for_each_batch(keys, vals, n, [&](const int32_t (&kk)[8], const float (&vv)[8], const int64_t (&ii)[8], int cnt) {
         unsigned long long key[8], cur[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const bool ok = j < cnt && in_range(kk[j], m);
             key[j] = ok ? Pack<MAX>::key(vv[j], ii[j]) : Pack<MAX>::kEmpty;
-            cur[j] = ok ? __ldcg(tab + kk[j]) : Pack<MAX>::kEmpty;
+            cur[j] = (ok && filter) ? __ldcg(tab + kk[j]) : Pack<MAX>::kEmpty;
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -721,6 +723,45 @@ __global__ void k_hist_sel_vjp(const int32_t *__restrict__ is, const T *__restri
     }
 }
 
+// The same Fig. 5 return sweep as a gather, for large m (few values per bin):
+// element i is the selected one of its bin iff is[k_i] == i.  One streaming
+// pass over the keys replaces a zero-fill plus a scatter of partial sectors.
+template <typename T>
+__global__ void k_hist_sel_vjp_gather(const int32_t *__restrict__ keys, const int32_t *__restrict__ is,
+                                      const T *__restrict__ hb, T *__restrict__ vb, const int64_t n, const int64_t m,
+                                      const int accumulate) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nv = n / 4;
+    for (int64_t v = g; v < nv; v += stride) {
+        const int4 k = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
+        T o[4];
+        if (accumulate) load_chunk(vb, v * 4, n, o, T(0));
+        const int kk[4] = {k.x, k.y, k.z, k.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const bool sel = in_range(kk[c], m) && __ldg(is + kk[c]) == (int32_t)(4 * v + c);
+            const T gv = sel ? __ldg(hb + kk[c]) : T(0);
+            o[c] = accumulate ? o[c] + gv : gv;
+        }
+        store_chunk(vb, v * 4, n, o);
+    }
+    for (int64_t i = nv * 4 + g; i < n; i += stride) {
+        const int32_t k = keys[i];
+        const T gv = (in_range(k, m) && is[k] == (int32_t)i) ? hb[k] : T(0);
+        vb[i] = accumulate ? vb[i] + gv : gv;
+    }
+}
+
+template <typename T>
+__global__ void k_h0bar_sel(const int32_t *__restrict__ is, const T *__restrict__ hb, T *__restrict__ h0b,
+                            const int64_t m, const int64_t n, const int accumulate) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        const T g = (is[j] >= n) ? hb[j] : T(0);
+        h0b[j] = accumulate ? h0b[j] + g : g;
+    }
+}
+
 // Sec. 4.2.3 return sweep with the zero-count cases of Fig. 3, per bin.  Two
 // per-bin coefficients are built first, with a = hist0[k] * p[k] * histbar[k]:
 //   anz[k] = a if n0[k] == 0 else 0   -> vbar = anz[k] / v   for v != 0
@@ -996,8 +1037,8 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
             else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
             if (n > 0) {
                 if (st == kGlobal) {
-                    if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab);
-                    else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab);
+                    if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
+                    else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
                 } else if (st == kSmemThread) {
                     auto kern = mx ? k_hist_sel_thread<true> : k_hist_sel_thread<false>;
                     if (!set_smem(kern, L.smem)) return ADC_ERR_CUDA;
@@ -1053,10 +1094,17 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         if (h0b) k_h0bar_add<T><<<gm, 256, 0, s>>>(hb, h0b, m, acc);
         return check_launch();
     case ADC_OP_MIN:
-    case ADC_OP_MAX:
-        if (!acc && n > 0) k_fill<T><<<grid_for(n / 4 + 1, 8), 256, 0, s>>>(vb, n);
-        k_hist_sel_vjp<T><<<gm, 256, 0, s>>>(static_cast<const int32_t *>(saved), hb, vb, h0b, m, n, acc);
+    case ADC_OP_MAX: {
+        const int32_t *is = static_cast<const int32_t *>(saved);
+        if (m * 8 > n) {  // few values per bin: one gather pass
+            if (n > 0) k_hist_sel_vjp_gather<T><<<gn, 256, 0, s>>>(keys, is, hb, vb, n, m, acc);
+            if (h0b) k_h0bar_sel<T><<<gm, 256, 0, s>>>(is, hb, h0b, m, n, acc);
+        } else {          // many values per bin: zero-fill, then scatter m adjoints
+            if (!acc && n > 0) k_fill<T><<<grid_for(n / 4 + 1, 8), 256, 0, s>>>(vb, n);
+            k_hist_sel_vjp<T><<<gm, 256, 0, s>>>(is, hb, vb, h0b, m, n, acc);
+        }
         return check_launch();
+    }
     case ADC_OP_MUL: {
         const int32_t *n0 = static_cast<const int32_t *>(saved);
         const T *p = reinterpret_cast<const T *>(static_cast<const char *>(saved) + align_up((size_t)m * 4, 16));

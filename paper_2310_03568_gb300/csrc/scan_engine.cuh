@@ -239,6 +239,204 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
     }
 }
 
+// Block-wide exclusive scan of one state per thread in thread order; returns
+// this thread's exclusive value and (through *total) the block's aggregate.
+// Contains two __syncthreads().
+template <class Op, int THREADS, typename S>
+__device__ __forceinline__ S block_scan_excl(const Op &op, const S &a, S *s_warp, S *total) {
+    constexpr int NW = THREADS / kWarp;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const S winc = warp_inclusive_scan(op, a);
+    if (lane == kWarp - 1) s_warp[warp] = winc;
+    __syncthreads();
+    S wexc = shfl_up(winc, 1);
+    if (lane == 0) wexc = op.identity();
+    S before = op.identity(), all = op.identity();
+#pragma unroll
+    for (int w = 0; w < NW; ++w) {
+        if (w < warp) before = op.combine(before, s_warp[w]);
+        all = op.combine(all, s_warp[w]);
+    }
+    __syncthreads();
+    *total = all;
+    return op.combine(before, wexc);
+}
+
+// ------------------------------------------------- range-partitioned scan --
+// For large n.  Each block claims (atomic counter, so every block it waits on
+// is running) a contiguous range of tiles.  Phase A streams the range once;
+// every warp reduces its part of each tile in order and keeps the result in
+// shared memory (no block barrier per tile: the warps stream independently).
+// The block then folds these warp-tile aggregates into its range aggregate,
+// publishes it and looks back over the other ranges -- a few hundred, so the
+// look-back is short -- and turns the warp-tile aggregates into exclusive
+// prefixes.  Phase B streams the range again in REVERSE tile order, so the
+// tiles read last in phase A (still in L2) come first, and each warp rescans
+// its part of a tile from its prefix, again without block barriers.
+// Traffic: the input twice (less what L2 keeps), the output once.  Same Op
+// interface as k_scan.
+template <typename S> constexpr int range_max_tiles() {
+    return (int)((32 * 1024) / (8 * sizeof(S))) < 128 ? (int)((32 * 1024) / (8 * sizeof(S))) : 128;
+}
+
+template <class Op, int THREADS, int ITEMS, bool REVERSE>
+__global__ void __launch_bounds__(THREADS)
+k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long *__restrict__ aggw,
+              unsigned long long *__restrict__ incw, const DevCtl ctl) {
+    using S = typename Op::State;
+    constexpr int TILE = THREADS * ITEMS;
+    constexpr int NW = THREADS / kWarp;
+    constexpr int K = Tagged<S>::K;
+    constexpr int MT = range_max_tiles<S>();
+    __shared__ unsigned s_range;
+    __shared__ S s_wt[MT * NW];  // warp-tile aggregates, then their exclusive prefixes
+    __shared__ S s_lbv[NW];
+    __shared__ int s_lbinc[NW], s_lberr[NW];
+    __shared__ S s_range_agg;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int jc = REVERSE ? (THREADS - 1 - tid) : tid;
+    if (tid == 0) s_range = atomicAdd(ctl.counter, 1u);
+    __syncthreads();
+    const long long r = s_range;
+    const long long G = gridDim.x;
+    const int64_t per = num_tiles / G, extra = num_tiles % G;
+    const int64_t t0 = r * per + (r < extra ? r : extra);
+    const int cnt = (int)(per + (r < extra ? 1 : 0));
+    auto chunk0 = [&](int64_t t) -> int64_t {
+        const int64_t p = REVERSE ? (num_tiles - 1 - t) : t;
+        return p * (int64_t)TILE + (int64_t)jc * ITEMS;
+    };
+    auto thread_agg = [&](const S (&st)[ITEMS]) -> S {
+        S a = op.identity();
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) a = op.combine(a, st[REVERSE ? ITEMS - 1 - k : k]);
+        return a;
+    };
+
+    // ---- phase A: warp-tile aggregates
+    typename Op::Raw raw;
+    if (cnt > 0) op.fetch(chunk0(t0), n, raw);
+    for (int i = 0; i < cnt; ++i) {
+        S st[ITEMS];
+        typename Op::Aux aux;
+        op.build(chunk0(t0 + i), n, raw, st, aux);
+        if (i + 1 < cnt) op.fetch(chunk0(t0 + i + 1), n, raw);
+        const S winc = warp_inclusive_scan(op, thread_agg(st));
+        if (lane == kWarp - 1) s_wt[i * NW + warp] = winc;
+    }
+    __syncthreads();
+
+    // ---- range aggregate: warp 0 folds the cnt*NW entries in order
+    const int E = cnt * NW;
+    const int per_lane = (E + kWarp - 1) / kWarp;
+    S lane_fold = op.identity();
+    if (warp == 0) {
+        for (int e = lane * per_lane; e < E && e < (lane + 1) * per_lane; ++e) lane_fold = op.combine(lane_fold, s_wt[e]);
+        S v = lane_fold;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {  // ordered reduction: lane 0 ends with lanes 0..31 in order
+            const S other = shfl_down(v, o);
+            if (lane + o < kWarp) v = op.combine(v, other);
+        }
+        if (lane == 0) s_range_agg = v;
+    }
+    __syncthreads();
+    const S range_agg = s_range_agg;
+
+    // ---- look-back over the ranges
+    bool abort = false;
+    S prefix = op.identity();
+    if (r == ctl.stall_tile) {  // fault injection: this range never publishes
+        abort = true;
+    } else {
+        if (tid == 0) publish(aggw + r * K, range_agg, kFlagAgg);
+        if (r == 0) {
+            if (tid == 0) publish(incw, range_agg, kFlagInc);
+        } else {
+            long long base = r - 1;
+            while (true) {
+                const long long tj = base - (long long)kWarp * warp - lane;
+                S v = op.identity();
+                unsigned f = kFlagInc;
+                if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
+                const bool err = __any_sync(0xffffffffu, f == kFlagError);
+                const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
+                const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
+                if (lane > stop) v = op.identity();
+#pragma unroll
+                for (int o = 1; o < kWarp; o <<= 1) {  // farthest (highest lane) first
+                    const S other = shfl_down(v, o);
+                    if (lane + o < kWarp) v = op.combine(other, v);
+                }
+                if (lane == 0) {
+                    s_lbv[warp] = v;
+                    s_lbinc[warp] = incmask != 0;
+                    s_lberr[warp] = err;
+                }
+                __syncthreads();
+                bool found = false;
+                for (int w = 0; w < NW; ++w) {
+                    if (s_lberr[w]) {
+                        abort = true;
+                        break;
+                    }
+                    prefix = op.combine(s_lbv[w], prefix);
+                    if (s_lbinc[w]) {
+                        found = true;
+                        break;
+                    }
+                }
+                __syncthreads();
+                if (abort || found) break;
+                base -= (long long)kWarp * NW;
+            }
+            if (tid == 0) {
+                if (abort) {
+                    publish_tag(incw + r * K, K, kFlagError);
+                    set_error(ctl.err, kErrTimeout);
+                } else {
+                    publish(incw + r * K, op.combine(prefix, range_agg), kFlagInc);
+                }
+            }
+        }
+    }
+    if (abort) return;  // block-uniform
+
+    // ---- exclusive prefix of every warp-tile entry (warp 0, in order)
+    if (warp == 0) {
+        S ex = shfl_up(warp_inclusive_scan(op, lane_fold), 1);
+        if (lane == 0) ex = op.identity();
+        S run = op.combine(prefix, ex);
+        for (int e = lane * per_lane; e < E && e < (lane + 1) * per_lane; ++e) {
+            const S agg = s_wt[e];
+            s_wt[e] = run;
+            run = op.combine(run, agg);
+        }
+    }
+    __syncthreads();
+
+    // ---- phase B: rescan, last tile of phase A first; warps independent
+    if (cnt > 0) op.fetch(chunk0(t0 + cnt - 1), n, raw);
+    for (int i = cnt - 1; i >= 0; --i) {
+        S st[ITEMS];
+        typename Op::Aux aux;
+        const int64_t c0 = chunk0(t0 + i);
+        op.build(c0, n, raw, st, aux);
+        if (i > 0) op.fetch(chunk0(t0 + i - 1), n, raw);
+        S ex = shfl_up(warp_inclusive_scan(op, thread_agg(st)), 1);
+        if (lane == 0) ex = op.identity();
+        S run = op.combine(s_wt[i * NW + warp], ex);
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int kk = REVERSE ? ITEMS - 1 - k : k;
+            run = op.combine(run, st[kk]);
+            st[kk] = run;
+        }
+        op.store(c0, n, st, aux);
+    }
+}
+
 // Layout of one scan launch's region of the workspace: tagged aggregates and
 // tagged inclusive prefixes, 8 bytes per 32-bit state word, both zeroed before
 // the launch (tag 0 = nothing published).
@@ -263,6 +461,26 @@ template <class Op, int ITEMS> struct ScanShape {
     static size_t region(int64_t n) { return scan_ws_layout(tiles(n), sizeof(typename Op::State)).bytes; }
 };
 
+// Resident blocks per SM of one range-scan instantiation (cached per device).
+template <class Op, int ITEMS, bool REVERSE> int ranges_blocks_per_sm() {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE>,
+                                                          kScanThreads, 0) != cudaSuccess ||
+            b < 1)
+            b = 1;
+        cache[dev] = b;
+    }
+    return cache[dev];
+}
+
+// Engine selection for tests and measurements: 0 automatic, 1 per-tile
+// look-back only, 2 range-partitioned where it applies.
+extern int g_scan_engine;
+
 // Queue one scan.  `ws` is the call's workspace (error word and counter slot
 // `slot` in its header); `region` holds this launch's tile flags and states.
 template <class Op, int ITEMS, bool REVERSE>
@@ -274,6 +492,15 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     char *w = static_cast<char *>(region);
     if (cudaMemsetAsync(w, 0, L.bytes, s) != cudaSuccess) return ADC_ERR_CUDA;
     const DevCtl ctl = make_ctl(ws, slot);
+    const int64_t G = (int64_t)num_sms() * ranges_blocks_per_sm<Op, ITEMS, REVERSE>();
+    const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * G &&
+                        (g_scan_engine == 2 || (g_scan_engine == 0 && T >= 4 * G));
+    if (ranges) {
+        k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)G, kScanThreads, 0, s>>>(
+            op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
+            reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
+        return check_launch();
+    }
     k_scan<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)T, kScanThreads, 0, s>>>(
         op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
         reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);

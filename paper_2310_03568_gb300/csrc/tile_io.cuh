@@ -16,7 +16,7 @@ __device__ __forceinline__ void load_chunk(const E *__restrict__ p, int64_t c0, 
             const uint4 *src = reinterpret_cast<const uint4 *>(p + c0);
 #pragma unroll
             for (int w = 0; w < BYTES / 16; ++w) {
-                uint4 v = __ldcs(src + w);
+                uint4 v = __ldg(src + w);  // default L2 policy: a second pass may hit L2
                 memcpy(reinterpret_cast<char *>(st) + 16 * w, &v, 16);
             }
             return;

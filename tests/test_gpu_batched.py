@@ -153,3 +153,37 @@ def test_batched_full_workload_gradient_closed_form():
             sel = idx < n
             expect[idx[sel]] = (m - np.arange(m))[sel]
             assert np.array_equal(vb[o:o + n], expect)
+
+
+def test_autotuner_picks_a_configuration_and_caches_it(tmp_path, monkeypatch):
+    from paper_2310_03568_gb300 import adcomb, autotune
+    monkeypatch.setenv("ADC_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    autotune._cache = None
+    w = small_workload(seed=35, count=20)
+    desc, keys, vals = B.layout(w)
+    p = B.BatchedHistScan(desc, keys, vals)
+    entry = autotune.tune_batched(p)
+    assert entry["chunk"] in autotune.BATCHED_CHUNKS and entry["smem_bins"] in autotune.BATCHED_SMEM_BINS
+    assert len(entry["candidates"]) == len(autotune.BATCHED_CHUNKS) * len(autotune.BATCHED_SMEM_BINS)
+    p.forward()
+    p.backward()
+    torch.cuda.synchronize()
+    check_problem(p, desc, keys, vals, oracle_reference(desc, keys, vals))
+    autotune._cache = None  # reload from the file: a cache hit, no re-measurement
+    again = autotune.tune_batched(B.BatchedHistScan(desc, keys, vals))
+    assert again["chunk"] == entry["chunk"] and again["smem_bins"] == entry["smem_bins"]
+    # single-call histogram strategy
+    n, m = 400_000, 401
+    g = np.random.default_rng(36)
+    k = g.integers(0, m, n).astype(np.int32)
+    v = synth.hist_spec_values(g, "max", n, m)
+    kd, vd = torch.tensor(k, device="cuda"), torch.tensor(v, device="cuda")
+    try:
+        e = autotune.tune_hist("max", m, kd, vd)
+        assert e["strategy"] in autotune.HIST_STRATEGIES
+        h, saved = adcomb.hist_fwd("max", m, kd, vd)
+        ref, idx = oracle.hist_fwd("max", m, k, v)
+        assert np.array_equal(h.cpu().numpy(), ref.astype(np.float32))
+        assert np.array_equal(saved.view(torch.int32).cpu().numpy()[:m], idx.astype(np.int32))
+    finally:
+        adcomb.debug_force_hist_strategy(-1)

@@ -27,21 +27,24 @@ def lib():
     adcomb.set_spin_limit(0)
 
 
+@pytest.mark.parametrize("engine", [1, 2], ids=["per-tile", "ranges"])
 @pytest.mark.parametrize("op,stall", [("add", 3), ("lin", 0), ("mm2", 17)])
-def test_stalled_tile_times_out_and_context_survives(op, stall):
+def test_stalled_tile_times_out_and_context_survives(op, stall, engine):
     g = np.random.default_rng(8)
     n = 200_000
     x = synth.scan_values(g, op, n) if op != "add" else synth.uniform(g, n, -1, 1)
     xd = dev(x)
     ws = adcomb.Workspace()
     try:
+        adcomb.debug_set_scan_engine(engine)
         adcomb.set_spin_limit(2000)          # ~0.1-1 ms per wait
-        adcomb.debug_set_stall_tile(stall)
+        adcomb.debug_set_stall_tile(stall)   # a tile (per-tile engine) or a range (range engine)
         adcomb.scan_fwd(op, xd, ws=ws)       # queues fine: the failure is on the device
         assert adcomb.check_device_error(ws) == 5  # ADC_ERR_TIMEOUT
     finally:
         adcomb.debug_set_stall_tile(-1)
         adcomb.set_spin_limit(0)
+        adcomb.debug_set_scan_engine(0)
     # the context is intact and the same workspace works again
     y = adcomb.scan_fwd(op, xd, ws=ws)
     assert adcomb.check_device_error(ws) == 0

@@ -69,7 +69,7 @@ def fits(op, dt, m, s):
     if s == 3:
         return m * e * 256 <= 64 * 1024
     if s == 0:
-        return m * e * 8 <= 24 * 1024
+        return m * e * 8 <= 48 * 1024
     if s == 1:
         return m * (sz if op == "mul" else e) <= 200 * 1024
     return True

@@ -65,11 +65,22 @@ def check_scan(op, x, ybar, dt, accumulate=False):
 @pytest.fixture(scope="module", autouse=True)
 def lib():
     ensure_lib()
+    yield
+    adcomb.debug_set_scan_engine(0)
+
+
+@pytest.fixture(params=[1, 2], ids=["per-tile", "ranges"])
+def engine(request):
+    """Both scan engines: per-tile look-back, and range-partitioned (forced even
+    for small n, where several ranges are empty)."""
+    adcomb.debug_set_scan_engine(request.param)
+    yield request.param
+    adcomb.debug_set_scan_engine(0)
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2"])
-def test_scan_sizes(op, dt):
+def test_scan_sizes(op, dt, engine):
     g = np.random.default_rng(1000 + len(op))
     for n in sizes(op, dt):
         x = make_x(g, op, n, dt)
@@ -78,10 +89,20 @@ def test_scan_sizes(op, dt):
 
 
 @pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2"])
-def test_scan_accumulate(op):
+def test_scan_accumulate(op, engine):
     g = np.random.default_rng(7)
     x = make_x(g, op, 9001, np.float32)
     check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)
+
+
+@pytest.mark.parametrize("op", ["add", "lin", "mm2"])
+def test_scan_ranges_engine_many_tiles(op):
+    """Large enough that the automatic choice is the range-partitioned engine
+    (several tiles per range), checked against the per-tile engine's inputs."""
+    g = np.random.default_rng(17)
+    n = {"add": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001}[op]
+    x = make_x(g, op, n, np.float32)
+    check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
 
 
 def test_mul_scan_zero_paths_exact():
