@@ -54,6 +54,11 @@ def parse():
     p.add_argument("--no-batched", action="store_true")
     p.add_argument("--kernels", action="store_true",
                    help="instead of the bench line: per-kernel achieved bandwidth at full sizes (markdown)")
+    p.add_argument("--only", default=None,
+                   help="with --kernels: run only the families whose label contains this text, "
+                        "e.g. 'scan add float32', 'reduce mul', 'hist add m=1000'")
+    p.add_argument("--range-tiles", default="0",
+                   help="with --kernels: comma list of tiles per range for the range-partitioned scan (0 = default)")
     return p.parse_args()
 
 
@@ -439,26 +444,38 @@ def run_kernels(args):
         gbs = nbytes / (ms * 1e-3) / 1e9
         rows.append((name, n, nbytes, ms, gbs, gbs / peak))
 
+    def want(label):
+        return args.only is None or args.only in label
+
+    rts = [int(t) for t in args.range_tiles.split(",")]
+
     ws = adcomb.Workspace()
     for op, dt, n in [("add", np.float32, 100_000_000), ("mul", np.float32, 100_000_000),
                       ("lin", np.float32, 100_000_000), ("mm2", np.float32, 10_000_000),
                       ("add", np.float64, 10_000_000), ("mul", np.float64, 10_000_000),
                       ("lin", np.float64, 10_000_000)]:
+        if not want(f"scan {op} {np.dtype(dt).name}"):
+            continue
         x = torch.from_numpy(synth.scan_values(g, op, n, dt)).to(dev)
         es = x.element_size() * (x.numel() // n)
         y = adcomb.scan_fwd(op, x, ws=ws)
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
         vb_bytes = (2 if op == "add" else 4) * n * es
-        for eng, label in ((2, "ranges"), (1, "per-tile")):
+        variants = [(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] + [(1, 0, "per-tile")]
+        for eng, rt, label in variants:
             adcomb.debug_set_scan_engine(eng)
+            adcomb.debug_set_scan_range_tiles(rt)
             row(f"scan {op} fwd {np.dtype(dt).name} [{label}]", n, 2 * n * es,
                 timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
             row(f"scan {op} vjp {np.dtype(dt).name} [{label}]", n, vb_bytes,
                 timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
         adcomb.debug_set_scan_engine(0)
+        adcomb.debug_set_scan_range_tiles(0)
         del x, y, yb, xb
     for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000)]:
+        if not want(f"reduce {op}"):
+            continue
         x = torch.from_numpy(synth.scan_values(g, "mm2_orth" if op == "mm2" else "add", n)).to(dev)
         if op == "mul":
             x = x * 0.05 + 1.0
@@ -471,6 +488,8 @@ def run_kernels(args):
         row(f"reduce {op} vjp", n, vjp_bytes, timeit(lambda: adcomb.reduce_vjp(op, x, y, saved, yb, xbar=xb, ws=ws)))
         del x, xb
     for op, n, m in [("add", 100_000_000, 1000), ("add", 50_000_000, 10_000_000), ("lin", 10_000_000, 1000)]:
+        if not want(f"hist {op} m={m}"):
+            continue
         k = torch.randint(0, m, (n,), dtype=torch.int32, device=dev)
         v = torch.from_numpy(synth.scan_values(g, op, n)).to(dev)
         es = v.element_size() * (v.numel() // n)

@@ -297,6 +297,14 @@ void adc_debug_set_stall_tile(int64_t tile);
 void adc_debug_set_scan_engine(int engine);
 
 /*
+ * Tuning hook: tiles per range of the range-partitioned scan engine.  0 (the
+ * default) lets the library choose; a positive value launches
+ * ceil(tiles / value) ranges (as long as no range would exceed the engine's
+ * per-block limit).  Results do not depend on it beyond rounding order.
+ */
+void adc_debug_set_scan_range_tiles(int tiles);
+
+/*
  * Test hook: force the forward histogram strategy of ADD/MUL/MIN/MAX
  * (0: per-warp shared-memory copies, 1: one shared-memory copy per block,
  * 2: global atomics) where the histogram fits it; -1 (default) chooses

@@ -63,6 +63,7 @@ def lib():
                 "adc_debug_set_stall_tile": ([i64], None),
                 "adc_debug_force_hist_strategy": ([i32], None),
                 "adc_debug_set_scan_engine": ([i32], None),
+                "adc_debug_set_scan_range_tiles": ([i32], None),
                 "adc_status_string": ([i32], ctypes.c_char_p),
                 "adc_version": ([], ctypes.c_char_p),
             }
@@ -256,6 +257,11 @@ def debug_force_hist_strategy(strategy):
 def debug_set_scan_engine(engine):
     """0 automatic, 1 per-tile look-back only, 2 range-partitioned wherever it applies."""
     lib().adc_debug_set_scan_engine(int(engine))
+
+
+def debug_set_scan_range_tiles(tiles):
+    """Tiles per range of the range-partitioned scan engine; 0 lets the library choose."""
+    lib().adc_debug_set_scan_range_tiles(int(tiles))
 
 
 def status_string(code):

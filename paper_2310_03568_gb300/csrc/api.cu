@@ -11,6 +11,7 @@ namespace adc {
 static long long g_spin_limit = 1ll << 22;
 static long long g_stall_tile = -1;
 int g_scan_engine = 0;
+int g_scan_range_tiles = 0;
 
 DevCtl make_ctl(void *ws, int slot) {
     DevCtl c;
@@ -202,5 +203,6 @@ void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1
 void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
 
 void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 2) ? engine : 0; }
+void adc_debug_set_scan_range_tiles(int tiles) { g_scan_range_tiles = tiles > 0 ? tiles : 0; }
 
 }  // extern "C"

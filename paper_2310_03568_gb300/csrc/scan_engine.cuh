@@ -480,6 +480,7 @@ template <class Op, int ITEMS, bool REVERSE> int ranges_blocks_per_sm() {
 // Engine selection for tests and measurements: 0 automatic, 1 per-tile
 // look-back only, 2 range-partitioned where it applies.
 extern int g_scan_engine;
+extern int g_scan_range_tiles;
 
 // Queue one scan.  `ws` is the call's workspace (error word and counter slot
 // `slot` in its header); `region` holds this launch's tile flags and states.
@@ -493,10 +494,16 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     if (cudaMemsetAsync(w, 0, L.bytes, s) != cudaSuccess) return ADC_ERR_CUDA;
     const DevCtl ctl = make_ctl(ws, slot);
     const int64_t G = (int64_t)num_sms() * ranges_blocks_per_sm<Op, ITEMS, REVERSE>();
-    const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * G &&
+    // Ranges: one per resident block by default; a tuned count launches more,
+    // smaller ranges (blocks claim them in start order, so the look-back only
+    // ever waits on running blocks).
+    int64_t R = G;
+    if (g_scan_range_tiles > 0) R = (T + g_scan_range_tiles - 1) / g_scan_range_tiles;
+    if (R > T) R = T;
+    const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * R &&
                         (g_scan_engine == 2 || (g_scan_engine == 0 && T >= 4 * G));
     if (ranges) {
-        k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)G, kScanThreads, 0, s>>>(
+        k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)R, kScanThreads, 0, s>>>(
             op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
             reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
         return check_launch();
