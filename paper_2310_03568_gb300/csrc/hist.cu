@@ -6,8 +6,11 @@
 //               the global result -- for histograms of up to a few KB.
 //   SMEM_BLOCK: one sub-histogram per 1024-thread block filling most of the
 //               SM's shared memory -- for histograms up to ~200 KB.
-//   GLOBAL    : atomics directly on the global table (L2-resident for
-//               m up to ~1e7 fp32).
+//   PART      : for tables beyond shared memory: the elements are first
+//               partitioned by bin range so that every range's bins fit one
+//               block's shared memory (hist_part.cu) -- no global atomics.
+//   GLOBAL    : atomics directly on the global table (L2-resident); for
+//               fp64 min/max and tables too large for PART.
 // Operators and their atomics:
 //   ADD     : native float/double atomic add.
 //   MIN/MAX : fp32 value and int32 index packed into one 64-bit key
@@ -24,12 +27,13 @@
 // histogram of the values from the neutral element and a finalising map folds
 // hist0 in (hist0 wins min/max ties, acting as index -1).
 #include "common.cuh"
+#include "hist_common.cuh"
 #include "internal.h"
 #include "tile_io.cuh"
 
 namespace adc {
 
-enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3 };
+enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4 };
 
 // ------------------------------------------------------------ element loop --
 // Calls f(key, value, index) for every element, grid-stride over 4-element
@@ -69,7 +73,6 @@ __device__ __forceinline__ void for_each_elem(const int32_t *__restrict__ keys, 
     for (int64_t i = nv * 4 + gtid; i < n; i += stride) f(keys[i], vals[i], i);
 }
 
-__device__ __forceinline__ bool in_range(int32_t k, int64_t m) { return (uint32_t)k < (uint64_t)m; }
 
 // Same traversal, but hands the callback groups of up to 8 elements so that
 // it can keep 8 independent global atomics in flight.
@@ -162,34 +165,6 @@ __device__ __forceinline__ void batched_mul(T *__restrict__ p, const int32_t (&k
     }
     set_error(err, kErrCasLimit);
 }
-
-// ----------------------------------------------------------------- packing --
-template <bool MAX> struct Pack {
-    static constexpr unsigned long long kEmpty = MAX ? 0ull : ~0ull;
-    static __device__ __forceinline__ unsigned long long key(float v, int64_t i) {
-        const uint32_t idx = MAX ? (0xffffffffu - (uint32_t)i) : (uint32_t)i;
-        return ((unsigned long long)ordered_key(v) << 32) | idx;
-    }
-    static __device__ __forceinline__ int64_t index(unsigned long long k) {
-        const uint32_t lo = (uint32_t)k;
-        return MAX ? (int64_t)(0xffffffffu - lo) : (int64_t)lo;
-    }
-    static __device__ __forceinline__ bool better(unsigned long long a, unsigned long long b) {
-        return MAX ? a > b : a < b;
-    }
-    static __device__ __forceinline__ void update(unsigned long long *p, unsigned long long k) {
-        if (better(k, __ldcg(p))) {
-            if (MAX) atomicMax(p, k);
-            else atomicMin(p, k);
-        }
-    }
-    static __device__ __forceinline__ void update_smem(unsigned long long *p, unsigned long long k) {
-        if (better(k, *reinterpret_cast<volatile unsigned long long *>(p))) {
-            if (MAX) atomicMax(p, k);
-            else atomicMin(p, k);
-        }
-    }
-};
 
 // ===================================================================== ADD ==
 template <typename T>
@@ -292,7 +267,10 @@ __global__ void k_hist_sel_final(const unsigned long long *__restrict__ tab, con
         int64_t idx = n;
         if (key != Pack<MAX>::kEmpty) {
             idx = Pack<MAX>::index(key);
-            v = vals[idx];
+            // the key holds the value itself; only a zero needs the stored
+            // element (the key folds -0.0 onto +0.0)
+            v = from_ordered((uint32_t)(key >> 32));
+            if (v == 0.0f) v = vals[idx];
         }
         if (h0) {
             const float a = h0[j];
@@ -584,26 +562,6 @@ __global__ void k_prim_mul_global(const int32_t *__restrict__ keys, const T *__r
     });
 }
 
-template <bool MAX> struct Ord32 {
-    static constexpr uint32_t kEmpty = MAX ? 0u : 0xffffffffu;
-    static __device__ __forceinline__ bool better(uint32_t a, uint32_t b) { return MAX ? a > b : a < b; }
-    static __device__ __forceinline__ void update(uint32_t *p, uint32_t k, bool shared) {
-        const uint32_t cur = shared ? *reinterpret_cast<volatile uint32_t *>(p) : __ldcg(p);
-        if (better(k, cur)) {
-            if (MAX) atomicMax(p, k);
-            else atomicMin(p, k);
-        }
-    }
-};
-
-__device__ __forceinline__ float from_ordered(uint32_t u) {
-    return __uint_as_float((u & 0x80000000u) ? (u & 0x7fffffffu) : ~u);
-}
-__device__ __forceinline__ double from_ordered(unsigned long long u) {
-    return __longlong_as_double(
-        (long long)((u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u));
-}
-
 template <bool MAX>
 __global__ void k_ord32_init(uint32_t *__restrict__ tab, const int64_t m) {
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x)
@@ -844,9 +802,24 @@ static size_t entry_bytes(adc_op op, size_t s, HistStrategy st) {
     }
 }
 
+static int part_mode(adc_op op, bool primal) {
+    switch (op) {
+    case ADC_OP_ADD: return kPAdd;
+    case ADC_OP_MUL: return primal ? kPPrimMul : kPMul;
+    case ADC_OP_MIN: return primal ? kPPrimMin : kPMin;
+    case ADC_OP_MAX: return primal ? kPPrimMax : kPMax;
+    default: return -1;
+    }
+}
+
+// Below this many bins the bucketed tables get too small (heavy shared-memory
+// contention) and the single-pass strategies win.
+constexpr int64_t kPartMinBins = 1 << 18;
+
 static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
     const size_t e = entry_bytes(op, s, st);
     switch (st) {
+    case kPart: return part_applicable(part_mode(op, false), s, m);
     case kSmemThread: return (size_t)m * e * kThrThreads <= kThrBudget;
     case kSmemWarp: return (size_t)m * e * 8 <= kWarpBudget;
     case kSmemBlock: return (size_t)m * e <= kBlockBudget;
@@ -858,7 +831,7 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
 // always uses the two global phases.
 static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
-    if (g_force_strategy >= 0 && g_force_strategy <= 3 && fits(op, s, (HistStrategy)g_force_strategy, m))
+    if (g_force_strategy >= 0 && g_force_strategy <= 4 && fits(op, s, (HistStrategy)g_force_strategy, m))
         return (HistStrategy)g_force_strategy;
     // min/max updates are rare after the first few values of a bin (a read
     // filters them), so per-warp copies beat per-thread tables there: the
@@ -866,6 +839,7 @@ static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     const bool select = op == ADC_OP_MIN || op == ADC_OP_MAX;
     for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
         if (!(select && st == kSmemThread) && fits(op, s, st, m)) return st;
+    if (m >= kPartMinBins && fits(op, s, kPart, m)) return kPart;
     return kGlobal;
 }
 
@@ -888,15 +862,26 @@ template <typename K> static bool set_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
 }
 
-size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+// Workspace: the header, the operator's tables, then (where the partitioned
+// strategy can run) its scratch at part_off().
+static size_t base_ws(adc_op op, adc_dtype dt, int64_t m) {
     switch (op) {
     case ADC_OP_ADD: return kWsHeader;
     case ADC_OP_MUL: return kWsHeader + 2 * align_up((size_t)m * 8, 256);
     case ADC_OP_MIN:
     case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
-    case ADC_OP_LIN: return histgen_ws_bytes(dt, n, m);
     default: return 0;
     }
+}
+static size_t part_off(adc_op op, adc_dtype dt, int64_t m) { return align_up(base_ws(op, dt, m), 256); }
+
+size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
+    if (op == ADC_OP_LIN) return histgen_ws_bytes(dt, n, m);
+    if (op != ADC_OP_ADD && op != ADC_OP_MUL && op != ADC_OP_MIN && op != ADC_OP_MAX) return 0;
+    const size_t s = dt == ADC_F64 ? 8 : 4;
+    const size_t a = part_ws_bytes(part_mode(op, false), s, n, m);
+    const size_t b = part_ws_bytes(part_mode(op, true), s, n, m);
+    return part_off(op, dt, m) + (a > b ? a : b);
 }
 
 size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
@@ -911,14 +896,19 @@ size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     }
 }
 
-// Strategy for the un-lifted primal's table of `e`-byte entries.
-static HistStrategy pick_entry(size_t e, int64_t m, int *R) {
-    HistStrategy s;
-    if ((size_t)m * e * 8 <= kWarpBudget) s = kSmemWarp;
-    else if ((size_t)m * e <= kBlockBudget) s = kSmemBlock;
-    else s = kGlobal;
-    *R = (s == kSmemWarp) ? 8 : 1;
-    return s;
+// Strategy for the un-lifted primal's table of `e`-byte entries (the same
+// choices as the lifted forward's, so that the AD overhead compares like with
+// like).
+static HistStrategy pick_entry(adc_op op, size_t s, size_t e, int64_t m, int *R) {
+    HistStrategy st;
+    const bool part = part_applicable(part_mode(op, true), s, m);
+    if (g_force_strategy == kPart && part) st = kPart;
+    else if ((size_t)m * e * 8 <= kWarpBudget) st = kSmemWarp;
+    else if ((size_t)m * e <= kBlockBudget) st = kSmemBlock;
+    else if (m >= kPartMinBins && part) st = kPart;
+    else st = kGlobal;
+    *R = (st == kSmemWarp) ? 8 : 1;
+    return st;
 }
 
 template <typename T>
@@ -929,8 +919,12 @@ static adc_status hist_primal_t(adc_op op, int64_t n, int64_t m, const int32_t *
     const unsigned gm = grid_for(m, 4);
     const unsigned gglob = grid_for(n / 4 + 1, 8);
     int R;
+    const adc_dtype dt = dt_of<T>();
     if (op == ADC_OP_MUL) {
-        const HistStrategy st = pick_entry(sizeof(T), m, &R);
+        const HistStrategy st = pick_entry(op, sizeof(T), sizeof(T), m, &R);
+        if (st == kPart && n > 0)
+            return part_fwd(kPPrimMul, dt, n, m, keys, vals, h0, hist, nullptr, nullptr, nullptr, ws,
+                            part_off(op, dt, m), s);
         k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(1));
         if (n > 0) {
             if (st == kGlobal) {
@@ -947,9 +941,12 @@ static adc_status hist_primal_t(adc_op op, int64_t n, int64_t m, const int32_t *
         return check_launch();
     }
     const bool mx = op == ADC_OP_MAX;
+    if (n > 0 && pick_entry(op, sizeof(T), sizeof(T), m, &R) == kPart)
+        return part_fwd(mx ? kPPrimMax : kPPrimMin, dt, n, m, keys, vals, h0, hist, nullptr, nullptr, nullptr, ws,
+                        part_off(op, dt, m), s);
     if constexpr (sizeof(T) == 4) {
         uint32_t *tab = reinterpret_cast<uint32_t *>(w + kWsHeader);
-        const HistStrategy st = pick_entry(4, m, &R);
+        const HistStrategy st = pick_entry(op, 4, 4, m, &R);
         if (mx) k_ord32_init<true><<<gm, 256, 0, s>>>(tab, m);
         else k_ord32_init<false><<<gm, 256, 0, s>>>(tab, m);
         if (n > 0) {
@@ -993,6 +990,9 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
     const unsigned gm = grid_for(m, 4);
     switch (op) {
     case ADC_OP_ADD: {
+        if (st == kPart && n > 0)
+            return part_fwd(kPAdd, dt_of<T>(), n, m, keys, vals, h0, hist, nullptr, nullptr, nullptr, ws,
+                            part_off(op, dt_of<T>(), m), s);
         k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(0));
         if (n == 0) return check_launch();
         if (st == kGlobal) {
@@ -1009,8 +1009,14 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
     case ADC_OP_MUL: {
         int32_t *n0 = static_cast<int32_t *>(saved);
         T *p = reinterpret_cast<T *>(static_cast<char *>(saved) + align_up((size_t)m * 4, 16));
-        k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
-        if (n > 0) {
+        if (st == kPart && n > 0) {
+            const adc_status r = part_fwd(kPMul, dt_of<T>(), n, m, keys, vals, h0, nullptr, n0, p, nullptr, ws,
+                                          part_off(op, dt_of<T>(), m), s);
+            if (r != ADC_OK) return r;
+        } else {
+            k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
+        }
+        if (n > 0 && st != kPart) {
             if (st == kGlobal) {
                 k_hist_mul_global<T><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, n0, p, err);
             } else if (st == kSmemThread) {
@@ -1033,9 +1039,15 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         unsigned long long *tab = reinterpret_cast<unsigned long long *>(w + kWsHeader);
         int32_t *is = static_cast<int32_t *>(saved);
         if constexpr (sizeof(T) == 4) {
-            if (mx) k_pack_init<true><<<gm, 256, 0, s>>>(tab, m);
-            else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
-            if (n > 0) {
+            if (st == kPart && n > 0) {
+                const adc_status r = part_fwd(mx ? kPMax : kPMin, ADC_F32, n, m, keys, vals, h0, nullptr, nullptr,
+                                              nullptr, tab, ws, part_off(op, ADC_F32, m), s);
+                if (r != ADC_OK) return r;
+            } else {
+                if (mx) k_pack_init<true><<<gm, 256, 0, s>>>(tab, m);
+                else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
+            }
+            if (n > 0 && st != kPart) {
                 if (st == kGlobal) {
                     if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
                     else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);

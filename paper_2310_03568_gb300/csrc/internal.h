@@ -62,4 +62,19 @@ adc_status histgen_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, 
                        const void *hist0, const void *hist, const void *saved, const void *histbar,
                        void *valsbar, void *hist0bar, int accumulate, void *ws, cudaStream_t s);
 
+size_t excl_scan_i32_region(int64_t n);
+adc_status excl_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, int slot, void *region,
+                         cudaStream_t s);
+
+// hist_part.cu (reduce_by_index for tables beyond shared memory: partition by
+// bin range, then per-bucket shared-memory tables)
+enum PartMode { kPAdd = 0, kPMul = 1, kPMin = 2, kPMax = 3, kPPrimMul = 4, kPPrimMin = 5, kPPrimMax = 6 };
+bool part_applicable(int mode, size_t s, int64_t m);
+size_t part_ws_bytes(int mode, size_t s, int64_t n, int64_t m);
+// Outputs: ADD and the primals write hist (hist0 folded in); MUL writes the
+// residuals n0, p; MIN/MAX write the packed key table `tab`.  n > 0.
+adc_status part_fwd(int mode, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
+                    const void *hist0, void *hist, int32_t *n0, void *p, unsigned long long *tab, void *ws,
+                    size_t ws_off, cudaStream_t s);
+
 }  // namespace adc

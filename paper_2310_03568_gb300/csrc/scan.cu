@@ -126,6 +126,7 @@ template <typename E, int ITEMS> struct VjpRaw {
 
 // Product scan: J_{i+1} = x_{i+1}; xbar_i = y_{i-1} * lambda_i.
 template <typename T, int ITEMS> struct VjpMul {
+    static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
     using State = AffS<T>;
     using Raw = VjpRaw<T, ITEMS>;
     struct Aux { T yprev[ITEMS]; };
@@ -158,6 +159,7 @@ template <typename T, int ITEMS> struct VjpMul {
 // linFnComp scan: J = diag(c_{i+1}, c_{i+1}) (Sec. 5.3.4);
 // bbar_i = lambda.b, cbar_i = lambda.b * B_{i-1} + lambda.c * C_{i-1}, (B,C)_{-1} = (0,1).
 template <typename T, int ITEMS> struct VjpLin {
+    static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
     using State = AffP<T>;
     using Raw = VjpRaw<Pair<T>, ITEMS>;
     struct Aux { Pair<T> yprev[ITEMS]; };

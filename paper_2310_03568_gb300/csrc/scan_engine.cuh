@@ -477,6 +477,12 @@ template <class Op, int ITEMS, bool REVERSE> int ranges_blocks_per_sm() {
     return cache[dev];
 }
 
+// An Op may ask for ranges of a fixed number of tiles (static constexpr int
+// kRangeTiles) instead of one range per resident block: worth it when its
+// phase-B re-read from DRAM costs more than the extra look-backs (measured).
+template <class Op> constexpr int range_tiles_hint(long) { return 0; }
+template <class Op> constexpr auto range_tiles_hint(int) -> decltype(Op::kRangeTiles, int()) { return Op::kRangeTiles; }
+
 // Engine selection for tests and measurements: 0 automatic, 1 per-tile
 // look-back only, 2 range-partitioned where it applies.
 extern int g_scan_engine;
@@ -498,7 +504,8 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     // smaller ranges (blocks claim them in start order, so the look-back only
     // ever waits on running blocks).
     int64_t R = G;
-    if (g_scan_range_tiles > 0) R = (T + g_scan_range_tiles - 1) / g_scan_range_tiles;
+    const int rt = g_scan_range_tiles > 0 ? g_scan_range_tiles : range_tiles_hint<Op>(0);
+    if (rt > 0) R = (T + rt - 1) / rt;
     if (R > T) R = T;
     const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * R &&
                         (g_scan_engine == 2 || (g_scan_engine == 0 && T >= 4 * G));

@@ -481,6 +481,15 @@ static adc_status gen_vjp_t(int64_t n, int64_t m, const Pair<T> *h0, const void 
     return ADC_OK;
 }
 
+// Exclusive +-scan of an int32 array (count matrices of the partitioned passes).
+size_t excl_scan_i32_region(int64_t n) { return ScanShape<ExclAddI32<kCountItems>, kCountItems>::region(n); }
+
+adc_status excl_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, int slot, void *region,
+                         cudaStream_t s) {
+    ExclAddI32<kCountItems> ex{in, out};
+    return run_scan<ExclAddI32<kCountItems>, kCountItems, false>(ex, n, ws, slot, region, s);
+}
+
 adc_status histgen_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
                        void *hist, void *saved, void *ws, cudaStream_t s) {
     if (dt == ADC_F64)

@@ -56,7 +56,7 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2, 3]  # auto, per-warp, per-block, global, per-thread
+STRATS = [-1, 0, 1, 2, 3, 4]  # auto, per-warp, per-block, global, per-thread, partitioned by bin range
 
 
 def fits(op, dt, m, s):
@@ -65,6 +65,8 @@ def fits(op, dt, m, s):
     sz = np.dtype(dt).itemsize
     if op in ("min", "max") and dt == np.float64:
         return s in (-1, 2)
+    if s == 4:
+        return True
     e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
     if s == 3:
         return m * e * 256 <= 64 * 1024
@@ -75,7 +77,9 @@ def fits(op, dt, m, s):
     return True
 
 
-CASES = [(0, 7), (1, 1), (33, 5), (4097, 31), (100_003, 401), (100_003, 5000), (300_001, 50_000)]
+# the last case is large enough for the automatic choice to partition by bin range
+CASES = [(0, 7), (1, 1), (33, 5), (4097, 31), (100_003, 401), (100_003, 5000), (300_001, 50_000),
+         (3_000_001, 2_000_003)]
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
@@ -176,6 +180,41 @@ def test_hist_mul_zero_counting(dt, strategy):
             scale = pmax[kc] * np.abs(hb[kc]) / np.where(v != 0, np.minimum(np.abs(v.astype(np.float64)), 1), 1)
             assert_tol("hist * vjp", host(vb), vr, np.where(inr, pop[kc], 1), np.where(inr, scale, 0), rtol)
             assert_tol("hist * hist0bar", host(h0b), h0r, pop, bin_partial_products(k, v, m) * np.abs(hb), rtol)
+    adcomb.debug_force_hist_strategy(-1)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("op", ["mul", "min", "max"])
+def test_hist_original_primal(op, dt, strategy):
+    """The un-lifted primal (saved = NULL: the program being differentiated,
+    timed for the AD overhead) gives the same histogram as the lifted forward:
+    min/max bit-exact; * within the product tolerance, exactly 0 where a bin
+    holds a zero."""
+    g = np.random.default_rng(24)
+    rtol = rtol_for(dt)
+    for n, m in CASES:
+        if not fits(op, dt, m, strategy):
+            continue
+        adcomb.debug_force_hist_strategy(strategy)
+        k = keys_oor(g, n, m)
+        if op == "mul":
+            v = np.exp(g.uniform(-1, 1, n) * 3.0 / np.sqrt(max(n / m, 1))).astype(dt)
+            v[g.random(n) < 0.001] = 0
+            h0 = synth.uniform(g, m, 0.5, 1.5, dt)
+        else:
+            v = synth.hist_spec_values(g, op, n, m, dt)
+            h0 = ((g.integers(0, 1024, m) - 512) / 64.0).astype(dt)
+        for hist0 in (None, h0):
+            h = host(adcomb.hist_primal(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0)))
+            ref = oracle.hist_fwd(op, m, k, v, hist0)
+            if op == "mul":
+                pop, _ = bin_stats(k, v, m)
+                pmax = bin_partial_products(k, v, m) * (np.abs(hist0) if hist0 is not None else 1.0)
+                assert_tol("hist * primal", h, ref, pop + 1, pmax, rtol)
+                assert np.array_equal(h == 0, ref == 0)
+            else:
+                assert np.array_equal(h, ref[0].astype(dt))
     adcomb.debug_force_hist_strategy(-1)
 
 

@@ -67,6 +67,7 @@ def lib():
     ensure_lib()
     yield
     adcomb.debug_set_scan_engine(0)
+    adcomb.debug_set_scan_range_tiles(0)
 
 
 @pytest.fixture(params=[1, 2], ids=["per-tile", "ranges"])
@@ -95,14 +96,20 @@ def test_scan_accumulate(op, engine):
     check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)
 
 
+@pytest.mark.parametrize("range_tiles", [0, 3, 16])
 @pytest.mark.parametrize("op", ["add", "lin", "mm2"])
-def test_scan_ranges_engine_many_tiles(op):
+def test_scan_ranges_engine_many_tiles(op, range_tiles):
     """Large enough that the automatic choice is the range-partitioned engine
-    (several tiles per range), checked against the per-tile engine's inputs."""
+    (several tiles per range); also with more, smaller ranges than resident
+    blocks (3 tiles: a ragged last range)."""
     g = np.random.default_rng(17)
     n = {"add": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001}[op]
     x = make_x(g, op, n, np.float32)
-    check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
+    try:
+        adcomb.debug_set_scan_range_tiles(range_tiles)
+        check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
+    finally:
+        adcomb.debug_set_scan_range_tiles(0)
 
 
 def test_mul_scan_zero_paths_exact():
