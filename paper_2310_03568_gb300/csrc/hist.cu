@@ -123,49 +123,6 @@ __device__ __forceinline__ void for_each_batch(const int32_t *__restrict__ keys,
     }
 }
 
-// Compare-and-swap on the bit pattern of a float / double; returns the old value.
-__device__ __forceinline__ float cas_val(float *a, float expect, float val) {
-    return __uint_as_float(atomicCAS(reinterpret_cast<unsigned *>(a), __float_as_uint(expect), __float_as_uint(val)));
-}
-__device__ __forceinline__ double cas_val(double *a, double expect, double val) {
-    return __longlong_as_double((long long)atomicCAS(reinterpret_cast<unsigned long long *>(a),
-                                                     (unsigned long long)__double_as_longlong(expect),
-                                                     (unsigned long long)__double_as_longlong(val)));
-}
-__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
-__device__ __forceinline__ bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
-
-// Multiplies up to 8 values into global bins with all compare-and-swaps of a
-// round in flight together (bounded rounds; the error word records a give-up).
-template <typename T>
-__device__ __forceinline__ void batched_mul(T *__restrict__ p, const int32_t (&kk)[8], const T (&vv)[8],
-                                            const bool (&use)[8], unsigned *err) {
-    T cur[8];
-    bool todo[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        todo[j] = use[j];
-        if (todo[j]) cur[j] = __ldcg(p + kk[j]);
-    }
-    for (int round = 0; round < (1 << 20); ++round) {
-        bool any = false;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (todo[j]) {
-                const T old = cas_val(p + kk[j], cur[j], cur[j] * vv[j]);
-                if (same_bits(old, cur[j])) {
-                    todo[j] = false;
-                } else {
-                    cur[j] = old;
-                    any = true;
-                }
-            }
-        }
-        if (!any) return;
-    }
-    set_error(err, kErrCasLimit);
-}
-
 // ===================================================================== ADD ==
 template <typename T>
 __global__ void k_hist_init(T *__restrict__ h, const T *__restrict__ h0, const int64_t m, const T e) {
@@ -393,7 +350,7 @@ __global__ void k_hist_mul_global(const int32_t *__restrict__ keys, const T *__r
             if (ok && vv[j] == T(0)) atomicAdd(n0 + kk[j], 1);
             use[j] = ok && vv[j] != T(0);
         }
-        batched_mul(p, kk, vv, use, err);
+        mul_batch<T, 8>(p, kk, vv, use, err);
     });
 }
 
@@ -558,7 +515,7 @@ __global__ void k_prim_mul_global(const int32_t *__restrict__ keys, const T *__r
         bool use[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) use[j] = j < cnt && in_range(kk[j], m);
-        batched_mul(hist, kk, vv, use, err);
+        mul_batch<T, 8>(hist, kk, vv, use, err);
     });
 }
 

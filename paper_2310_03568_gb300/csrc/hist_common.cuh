@@ -58,4 +58,49 @@ __device__ __forceinline__ double from_ordered(unsigned long long u) {
         (long long)((u & 0x8000000000000000ull) ? (u & 0x7fffffffffffffffull) : ~u));
 }
 
+// Compare-and-swap on the bit pattern of a float / double; returns the old value.
+__device__ __forceinline__ float cas_val(float *a, float expect, float val) {
+    return __uint_as_float(atomicCAS(reinterpret_cast<unsigned *>(a), __float_as_uint(expect), __float_as_uint(val)));
+}
+__device__ __forceinline__ double cas_val(double *a, double expect, double val) {
+    return __longlong_as_double((long long)atomicCAS(reinterpret_cast<unsigned long long *>(a),
+                                                     (unsigned long long)__double_as_longlong(expect),
+                                                     (unsigned long long)__double_as_longlong(val)));
+}
+__device__ __forceinline__ bool same_bits(float a, float b) { return __float_as_uint(a) == __float_as_uint(b); }
+__device__ __forceinline__ bool same_bits(double a, double b) { return __double_as_longlong(a) == __double_as_longlong(b); }
+
+// Multiplies up to U values into bins base[idx[j]] (global or shared memory)
+// with all compare-and-swaps of a round in flight together, so that U
+// independent round trips overlap.  Bounded rounds; a give-up sets the error
+// word.
+template <typename T, int U>
+__device__ __forceinline__ void mul_batch(T *base, const int32_t (&idx)[U], const T (&v)[U], const bool (&use)[U],
+                                          unsigned *err) {
+    T cur[U];
+    bool todo[U];
+#pragma unroll
+    for (int j = 0; j < U; ++j) {
+        todo[j] = use[j];
+        if (todo[j]) cur[j] = *reinterpret_cast<volatile T *>(base + idx[j]);
+    }
+    for (int round = 0; round < (1 << 20); ++round) {
+        bool any = false;
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (todo[j]) {
+                const T old = cas_val(base + idx[j], cur[j], cur[j] * v[j]);
+                if (same_bits(old, cur[j])) {
+                    todo[j] = false;
+                } else {
+                    cur[j] = old;
+                    any = true;
+                }
+            }
+        }
+        if (!any) return;
+    }
+    set_error(err, kErrCasLimit);
+}
+
 }  // namespace adc

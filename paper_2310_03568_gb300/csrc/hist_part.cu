@@ -38,6 +38,19 @@ constexpr int kPartTableThreads = 1024;
 constexpr size_t kPartTableBudget = 200 * 1024;  // one table block per SM
 constexpr int kPartSlot = 20;                    // workspace counter slot of the count scan
 
+// k / W for in-range keys by a float reciprocal and one correction step: the
+// quotients stay below 2^11, so the float estimate is off by at most one.
+struct BucketDiv {
+    uint32_t W;
+    float inv;
+    __device__ __forceinline__ uint32_t operator()(uint32_t k) const {
+        uint32_t b = __float2uint_rz(__uint2float_rz(k) * inv);
+        if (b * W > k) --b;
+        else if ((b + 1) * W <= k) ++b;
+        return b;
+    }
+};
+
 template <typename T> struct PartOut {
     T *hist;
     const T *h0;
@@ -60,8 +73,12 @@ template <typename T> struct PartTraits<T, kPAdd> {
     static constexpr size_t kEntry = sizeof(T);
     static __device__ __forceinline__ V enc(T v, int64_t) { return v; }
     static __device__ __forceinline__ void init(unsigned char *sm, int, int t) { reinterpret_cast<T *>(sm)[t] = T(0); }
-    static __device__ __forceinline__ void update(unsigned char *sm, int, int u, V v, unsigned *) {
-        atomicAdd(reinterpret_cast<T *>(sm) + u, v);
+    template <int U>
+    static __device__ __forceinline__ void update(unsigned char *sm, int, const int32_t (&u)[U], const V (&v)[U],
+                                                  const bool (&use)[U], unsigned *) {
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (use[j]) atomicAdd(reinterpret_cast<T *>(sm) + u[j], v[j]);
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int, int t, int64_t j, const PartOut<T> &o) {
         const T a = reinterpret_cast<const T *>(sm)[t];
@@ -78,9 +95,17 @@ template <typename T> struct PartTraits<T, kPMul> {
         reinterpret_cast<T *>(sm)[t] = T(1);
         reinterpret_cast<int32_t *>(sm + (size_t)W * sizeof(T))[t] = 0;
     }
-    static __device__ __forceinline__ void update(unsigned char *sm, int W, int u, V v, unsigned *err) {
-        if (v == T(0)) atomicAdd(reinterpret_cast<int32_t *>(sm + (size_t)W * sizeof(T)) + u, 1);
-        else atomic_mul(reinterpret_cast<T *>(sm) + u, v, err);
+    template <int U>
+    static __device__ __forceinline__ void update(unsigned char *sm, int W, const int32_t (&u)[U], const V (&v)[U],
+                                                  const bool (&use)[U], unsigned *err) {
+        // one compare-and-swap chain at a time: in shared memory the chains are
+        // short and batching them only adds registers (measured slower)
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (!use[j]) continue;
+            if (v[j] == T(0)) atomicAdd(reinterpret_cast<int32_t *>(sm + (size_t)W * sizeof(T)) + u[j], 1);
+            else atomic_mul(reinterpret_cast<T *>(sm) + u[j], v[j], err);
+        }
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int W, int t, int64_t j, const PartOut<T> &o) {
         o.p[j] = reinterpret_cast<const T *>(sm)[t];
@@ -96,8 +121,17 @@ template <bool MAX> struct PartSel {
     static __device__ __forceinline__ void init(unsigned char *sm, int, int t) {
         reinterpret_cast<V *>(sm)[t] = Pack<MAX>::kEmpty;
     }
-    static __device__ __forceinline__ void update(unsigned char *sm, int, int u, V v, unsigned *) {
-        Pack<MAX>::update_smem(reinterpret_cast<V *>(sm) + u, v);
+    // Few values per bin at the sizes this strategy serves: most updates win,
+    // so the atomic is issued without a read filter.
+    template <int U>
+    static __device__ __forceinline__ void update(unsigned char *sm, int, const int32_t (&u)[U], const V (&v)[U],
+                                                  const bool (&use)[U], unsigned *) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (!use[j]) continue;
+            if (MAX) atomicMax(reinterpret_cast<V *>(sm) + u[j], v[j]);
+            else atomicMin(reinterpret_cast<V *>(sm) + u[j], v[j]);
+        }
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int, int t, int64_t j,
                                                  const PartOut<float> &o) {
@@ -113,8 +147,12 @@ template <typename T> struct PartTraits<T, kPPrimMul> {
     static constexpr size_t kEntry = sizeof(T);
     static __device__ __forceinline__ V enc(T v, int64_t) { return v; }
     static __device__ __forceinline__ void init(unsigned char *sm, int, int t) { reinterpret_cast<T *>(sm)[t] = T(1); }
-    static __device__ __forceinline__ void update(unsigned char *sm, int, int u, V v, unsigned *err) {
-        atomic_mul(reinterpret_cast<T *>(sm) + u, v, err);
+    template <int U>
+    static __device__ __forceinline__ void update(unsigned char *sm, int, const int32_t (&u)[U], const V (&v)[U],
+                                                  const bool (&use)[U], unsigned *err) {
+#pragma unroll
+        for (int j = 0; j < U; ++j)
+            if (use[j]) atomic_mul(reinterpret_cast<T *>(sm) + u[j], v[j], err);
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int, int t, int64_t j, const PartOut<T> &o) {
         const T a = reinterpret_cast<const T *>(sm)[t];
@@ -129,12 +167,14 @@ template <typename T, bool MAX> struct PartPrimSel {
     static constexpr size_t kEntry = sizeof(V);
     static __device__ __forceinline__ V enc(T v, int64_t) { return (V)ordered_key(v); }
     static __device__ __forceinline__ void init(unsigned char *sm, int, int t) { reinterpret_cast<V *>(sm)[t] = kEmpty; }
-    static __device__ __forceinline__ void update(unsigned char *sm, int, int u, V v, unsigned *) {
-        V *p = reinterpret_cast<V *>(sm) + u;
-        const V cur = *reinterpret_cast<volatile V *>(p);
-        if (MAX ? v > cur : v < cur) {
-            if (MAX) atomicMax(p, v);
-            else atomicMin(p, v);
+    template <int U>
+    static __device__ __forceinline__ void update(unsigned char *sm, int, const int32_t (&u)[U], const V (&v)[U],
+                                                  const bool (&use)[U], unsigned *) {
+#pragma unroll
+        for (int j = 0; j < U; ++j) {
+            if (!use[j]) continue;
+            if (MAX) atomicMax(reinterpret_cast<V *>(sm) + u[j], v[j]);
+            else atomicMin(reinterpret_cast<V *>(sm) + u[j], v[j]);
         }
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int, int t, int64_t j, const PartOut<T> &o) {
@@ -172,7 +212,7 @@ __device__ __forceinline__ void load_group(const int32_t *__restrict__ keys, con
 // 1. counts[b * nchunks + chunk] = elements of the chunk in bucket b; row B is
 // a zero row so that the scanned matrix also gives every bucket's end.
 __global__ void __launch_bounds__(kPartThreads)
-k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const uint32_t W, const int B,
+k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const BucketDiv bdiv, const int B,
              const int64_t nchunks, int32_t *__restrict__ counts) {
     extern __shared__ int32_t s_cnt[];
     for (int b = threadIdx.x; b < B; b += kPartThreads) s_cnt[b] = 0;
@@ -185,7 +225,7 @@ k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m,
         load_group<float>(keys, nullptr, c0 + 4 * ((int64_t)r * kPartThreads + threadIdx.x), n, kk, unused);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (in_range(kk[c], m)) atomicAdd(&s_cnt[(uint32_t)kk[c] / W], 1);
+            if (in_range(kk[c], m)) atomicAdd(&s_cnt[bdiv((uint32_t)kk[c])], 1);
     }
     __syncthreads();
     for (int b = threadIdx.x; b <= B; b += kPartThreads)
@@ -200,7 +240,7 @@ k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m,
 template <typename T, int MODE>
 __global__ void __launch_bounds__(kPartThreads, 2)
 k_part_scatter(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
-               const uint32_t W, const int B, const int64_t nchunks, const int32_t *__restrict__ offs,
+               const BucketDiv bdiv, const int B, const int64_t nchunks, const int32_t *__restrict__ offs,
                uint16_t *__restrict__ obin, typename PartTraits<T, MODE>::V *__restrict__ oval) {
     using Tr = PartTraits<T, MODE>;
     using V = typename Tr::V;
@@ -231,8 +271,8 @@ k_part_scatter(const int32_t *__restrict__ keys, const T *__restrict__ vals, con
             uint32_t rank = 0;
             bk[i] = 0xffffffffu;
             if (in_range(kk[q], m)) {
-                const uint32_t b = (uint32_t)kk[q] / W;
-                bk[i] = (b << 16) | ((uint32_t)kk[q] - b * W);
+                const uint32_t b = bdiv((uint32_t)kk[q]);
+                bk[i] = (b << 16) | ((uint32_t)kk[q] - b * bdiv.W);
                 rank = (uint32_t)atomicAdd(&s_loc[b], 1);
             }
             if (i & 1) rk2[i >> 1] |= rank << 16;
@@ -323,19 +363,19 @@ k_part_table(const uint16_t *__restrict__ obin, const typename PartTraits<T, MOD
     const int64_t start = offs[(int64_t)blockIdx.x * nchunks];
     const int64_t end = offs[(int64_t)(blockIdx.x + 1) * nchunks];
     constexpr int U = 8;
-    int64_t g = start + threadIdx.x;
-    for (; g + (int64_t)(U - 1) * kPartTableThreads < end; g += (int64_t)U * kPartTableThreads) {
-        uint16_t u[U];
+    for (int64_t g0 = start; g0 < end; g0 += (int64_t)U * kPartTableThreads) {
+        int32_t u[U];
         V v[U];
+        bool use[U];
 #pragma unroll
         for (int j = 0; j < U; ++j) {
-            u[j] = __ldcs(obin + g + (int64_t)j * kPartTableThreads);
-            v[j] = __ldcs(oval + g + (int64_t)j * kPartTableThreads);
+            const int64_t g = g0 + (int64_t)j * kPartTableThreads + threadIdx.x;
+            use[j] = g < end;
+            u[j] = use[j] ? (int32_t)__ldcs(obin + g) : 0;
+            v[j] = use[j] ? __ldcs(oval + g) : V(0);
         }
-#pragma unroll
-        for (int j = 0; j < U; ++j) Tr::update(smem_raw, (int)W, u[j], v[j], err);
+        Tr::template update<U>(smem_raw, (int)W, u, v, use, err);
     }
-    for (; g < end; g += kPartTableThreads) Tr::update(smem_raw, (int)W, __ldcs(obin + g), __ldcs(oval + g), err);
     __syncthreads();
     for (int t = threadIdx.x; t < w; t += kPartTableThreads) Tr::flush(smem_raw, (int)W, t, j0 + t, out);
 }
@@ -343,6 +383,7 @@ k_part_table(const uint16_t *__restrict__ obin, const typename PartTraits<T, MOD
 // -------------------------------------------------------------------- host --
 struct PartPlan {
     uint32_t W;
+    float inv;
     int B;
     int64_t nchunks;
     bool ok;
@@ -352,6 +393,7 @@ struct PartPlan {
 // the bucket count is a whole number of waves of one block per SM.
 static PartPlan part_plan(size_t entry, int64_t n, int64_t m) {
     PartPlan P{};
+    P.inv = 0.0f;
     int64_t wmax = (int64_t)(kPartTableBudget / entry);
     if (wmax > 65536) wmax = 65536;
     const int64_t sms = num_sms();
@@ -360,6 +402,7 @@ static PartPlan part_plan(size_t entry, int64_t n, int64_t m) {
     const int64_t W = (m + k * sms - 1) / (k * sms);
     const int64_t B = (m + W - 1) / W;
     P.W = (uint32_t)W;
+    P.inv = (float)(1.0 / (double)W);
     P.B = (int)B;
     P.nchunks = n > 0 ? (n + kPartChunk - 1) / kPartChunk : 1;
     P.ok = B <= kPartMaxBuckets && W <= 65536;
@@ -432,14 +475,15 @@ static adc_status part_run(int64_t n, int64_t m, const int32_t *keys, const T *v
     unsigned *err = reinterpret_cast<unsigned *>(ws);
     const int64_t nc = P.nchunks;
 
-    k_part_count<<<(unsigned)nc, kPartThreads, (size_t)P.B * 4, s>>>(keys, n, m, P.W, P.B, nc, counts);
+    const BucketDiv bdiv{P.W, P.inv};
+    k_part_count<<<(unsigned)nc, kPartThreads, (size_t)P.B * 4, s>>>(keys, n, m, bdiv, P.B, nc, counts);
     adc_status st = check_launch();
     if (st != ADC_OK) return st;
     st = excl_scan_i32(counts, offs, (int64_t)(P.B + 1) * nc, ws, kPartSlot, w + L.scanreg, s);
     if (st != ADC_OK) return st;
     const size_t sm_scatter = (size_t)kPartChunk * (sizeof(V) + 4) + (size_t)P.B * 8;
     if (!smem_attr(k_part_scatter<T, MODE>, sm_scatter)) return ADC_ERR_CUDA;
-    k_part_scatter<T, MODE><<<(unsigned)nc, kPartThreads, sm_scatter, s>>>(keys, vals, n, m, P.W, P.B, nc, offs, obin,
+    k_part_scatter<T, MODE><<<(unsigned)nc, kPartThreads, sm_scatter, s>>>(keys, vals, n, m, bdiv, P.B, nc, offs, obin,
                                                                           oval);
     if ((st = check_launch()) != ADC_OK) return st;
     const size_t sm_table = (size_t)P.W * Tr::kEntry;
