@@ -3,7 +3,8 @@
 * batched hist -> scan -> sum: work-item size (``chunk``) and shared-memory
   table size (``smem_bins``) of the persistent histogram launch;
 * reduce_by_index (single call): the forward strategy -- per-thread tables,
-  per-warp copies, one block-wide table, or global atomics
+  per-warp copies, one block-wide table, global atomics, or partitioning by bin
+  range into shared-memory-sized buckets
   (``adc_debug_force_hist_strategy``; the library validates that the table fits).
 
 Each candidate is timed with CUDA events on the real inputs (warm-up, then the
@@ -27,7 +28,7 @@ _cache = None
 
 BATCHED_CHUNKS = (1 << 14, 1 << 16, 1 << 18)
 BATCHED_SMEM_BINS = (4096, 8192, 16384)
-HIST_STRATEGIES = (3, 0, 1, 2)  # per-thread, per-warp, per-block, global
+HIST_STRATEGIES = (3, 0, 1, 2, 4)  # per-thread, per-warp, per-block, global, partitioned by bin range
 
 
 def cache_path():

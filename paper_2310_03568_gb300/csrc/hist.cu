@@ -836,6 +836,8 @@ size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     if (op == ADC_OP_LIN) return histgen_ws_bytes(dt, n, m);
     if (op != ADC_OP_ADD && op != ADC_OP_MUL && op != ADC_OP_MIN && op != ADC_OP_MAX) return 0;
     const size_t s = dt == ADC_F64 ? 8 : 4;
+    // the partition scratch (about n * (2 + value bytes)) only where it can be chosen
+    if (m < kPartMinBins && g_force_strategy != kPart) return base_ws(op, dt, m);
     const size_t a = part_ws_bytes(part_mode(op, false), s, n, m);
     const size_t b = part_ws_bytes(part_mode(op, true), s, n, m);
     return part_off(op, dt, m) + (a > b ? a : b);
