@@ -36,6 +36,10 @@
  *   LIN (linFnComp)    : (b, c) meaning x -> b + c*x;
  *                        (b1,c1) (.) (b2,c2) = (b2 + c2*b1, c2*c1)     (d = 2)
  *   MM2 (matMul2x2)    : (a, b, c, d) row-major 2x2; X (.) Y = X * Y   (d = 4)
+ *   SOP (sumOfProd)    : (p, s); (p1,s1) (.) (p2,s2) = (p1 + p2 + s1*s2, s1 + s2),
+ *                        associative and commutative (Sec. 3.3's example of an
+ *                        invertible operator); with elements (0, a_i) the
+ *                        reduction gives (sum_{i<j} a_i a_j, sum_i a_i)  (d = 2)
  *
  * Readings of the paper taken here (each also listed in the design notes):
  *   - min/max ties: the lifted operator of Fig. 5 keeps the smaller index; the
@@ -51,12 +55,12 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_ADD = 0, ORC_MUL = 1, ORC_MIN = 2, ORC_MAX = 3, ORC_LIN = 4, ORC_MM2 = 5 };
+enum { ORC_ADD = 0, ORC_MUL = 1, ORC_MIN = 2, ORC_MAX = 3, ORC_LIN = 4, ORC_MM2 = 5, ORC_SOP = 6 };
 
 #define MAXD 4
 
 static int arity(int op) {
-    if (op == ORC_LIN) return 2;
+    if (op == ORC_LIN || op == ORC_SOP) return 2;
     if (op == ORC_MM2) return 4;
     return 1;
 }
@@ -72,6 +76,7 @@ static void neutral(int op, double *e) {
     case ORC_MAX: e[0] = -INFINITY; break;
     case ORC_LIN: e[0] = 0.0; e[1] = 1.0; break;            /* x -> 0 + 1*x */
     case ORC_MM2: e[0] = 1.0; e[1] = 0.0; e[2] = 0.0; e[3] = 1.0; break;
+    case ORC_SOP: e[0] = 0.0; e[1] = 0.0; break;
     }
 }
 
@@ -108,6 +113,10 @@ static void combine(int op, const double *x, const double *y, double *z) {
                 for (int k = 0; k < 2; k++) s += x[2 * i + k] * y[2 * k + j];
                 t[2 * i + j] = s;
             }
+        break;
+    case ORC_SOP:                      /* (p1,s1) (.) (p2,s2) = (p1 + p2 + s1*s2, s1 + s2) */
+        t[0] = x[0] + y[0] + x[1] * y[1];
+        t[1] = x[1] + y[1];
         break;
     }
     memcpy(z, t, sizeof(double) * arity(op));
@@ -150,6 +159,13 @@ static void combine_vjp(int op, const double *x, const double *y, int xwins,
                 yb[2 * k + j] = s;
             }
         break;
+    case ORC_SOP:
+        /* z0 = x0 + y0 + x1*y1, z1 = x1 + y1 */
+        xb[0] = zb[0];
+        xb[1] = y[1] * zb[0] + zb[1];
+        yb[0] = zb[0];
+        yb[1] = x[1] * zb[0] + zb[1];
+        break;
     }
 }
 
@@ -174,6 +190,10 @@ static void combine_jvp(int op, const double *x, const double *y, int xwins,
                     s += xd[2 * i + k] * y[2 * k + j] + x[2 * i + k] * yd[2 * k + j];
                 t[2 * i + j] = s;
             }
+        break;
+    case ORC_SOP:
+        t[0] = xd[0] + yd[0] + xd[1] * y[1] + x[1] * yd[1];
+        t[1] = xd[1] + yd[1];
         break;
     }
     memcpy(zd, t, sizeof(double) * arity(op));

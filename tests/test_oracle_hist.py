@@ -105,7 +105,24 @@ def test_lin_is_the_per_bin_sequential_fold_and_reduces_to_add():
     assert_close(vb[:, 0], vb_add, rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2)])
+def test_sop_per_bin_closed_form_with_hist0():
+    # per bin: hist0 (.) fold of the bin's pairs = (p0 + P + s0 * S, s0 + S) with
+    # P = sum p_i + sum_{i<j} s_i s_j and S = sum s_i (sumOfProd, Sec. 3.3 / Sec. 4);
+    # small integers keep every value exact.  Out-of-range keys are skipped.
+    n, m = 300, 9
+    k = keys_with_out_of_range(n, m)
+    v = np.stack([RNG.integers(-5, 6, n), RNG.integers(-5, 6, n)], 1).astype(np.float64)
+    h0 = np.stack([RNG.integers(-5, 6, m), RNG.integers(-5, 6, m)], 1).astype(np.float64)
+    h = oracle.hist_fwd("sop", m, k, v, h0)
+    for j in range(m):
+        sel = v[k == j]
+        P = sel[:, 0].sum() + (sel[:, 1].sum() ** 2 - (sel[:, 1] ** 2).sum()) / 2
+        S = sel[:, 1].sum()
+        assert h[j, 0] == h0[j, 0] + P + h0[j, 1] * S
+        assert h[j, 1] == h0[j, 1] + S
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("sop", 2)])
 def test_hist_vjp_finite_differences(op, d):
     n, m = 30, 5
     k = keys_with_out_of_range(n, m)
@@ -130,7 +147,7 @@ def test_hist_vjp_finite_differences(op, d):
     assert_close(h0b, fd_vjp(fh, h0, hb), rtol=1e-6, atol=1e-8)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2)])
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("sop", 2)])
 def test_hist_dot_product(op, d):
     n, m = 200, 13
     k = keys_with_out_of_range(n, m)

@@ -124,7 +124,35 @@ def test_mm2_adjoint_matches_general_rule_with_numpy_products():
         assert_close(xb[i].reshape(2, 2), L.T @ Zb @ R.T, rtol=1e-10, atol=1e-13)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("mm2", 4)])
+def test_sop_forward_closed_form():
+    # Sec. 3.3's sumOfProd on (p, s) pairs: the fold of (p_i, s_i) is
+    # (sum p_i + sum_{i<j} s_i s_j, sum s_i); sum_{i<j} s_i s_j = ((sum s)^2 - sum s^2) / 2.
+    # Small integers: every intermediate is exact in fp64.
+    n = 57
+    x = np.stack([RNG.integers(-9, 10, n), RNG.integers(-9, 10, n)], 1).astype(np.float64)
+    p, s = x[:, 0], x[:, 1]
+    y = oracle.reduce_fwd("sop", x)
+    assert y[0] == p.sum() + (s.sum() ** 2 - (s ** 2).sum()) / 2
+    assert y[1] == s.sum()
+    # the paper's use: map (0, a_i), reduce, keep p  ->  sum over pairs i < j of a_i a_j
+    a = np.array([1.0, 2.0, 3.0])
+    assert oracle.reduce_fwd("sop", np.stack([np.zeros(3), a], 1))[0] == 1 * 2 + 1 * 3 + 2 * 3
+
+
+def test_sop_adjoint_is_the_all_but_one_sum():
+    # d/ds_i sum_{j<k} s_j s_k = sum_{j != i} s_j, and d/dp_i of the p-total is 1:
+    # xbar_i = (ybar_p, ybar_p * (S - s_i) + ybar_s), S = sum s.
+    n = 40
+    x = RNG.uniform(-1, 1, (n, 2))
+    yb = RNG.standard_normal(2)
+    xb = oracle.reduce_vjp("sop", x, yb)
+    S = x[:, 1].sum()
+    assert_close(xb[:, 0], np.full(n, yb[0]), rtol=0, atol=1e-15)
+    assert_close(xb[:, 1], yb[0] * (S - x[:, 1]) + yb[1], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("mm2", 4),
+                                  ("sop", 2)])
 def test_vjp_finite_differences(op, d):
     n = 24
     shape = (n,) if d == 1 else (n, d)
@@ -140,7 +168,8 @@ def test_vjp_finite_differences(op, d):
     assert_close(oracle.reduce_vjp(op, x, yb), fd_vjp(f, x, yb), rtol=1e-6, atol=1e-8)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("mm2", 4)])
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("mm2", 4),
+                                  ("sop", 2)])
 def test_dot_product_vjp_vs_jvp(op, d):
     n = 64
     shape = (n,) if d == 1 else (n, d)
