@@ -462,7 +462,8 @@ def run_kernels(args):
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
         vb_bytes = (2 if op == "add" else 4) * n * es
-        variants = [(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] + [(1, 0, "per-tile")]
+        variants = ([(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] +
+                    [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] + [(1, 0, "per-tile")])
         for eng, rt, label in variants:
             adcomb.debug_set_scan_engine(eng)
             adcomb.debug_set_scan_range_tiles(rt)
@@ -473,10 +474,14 @@ def run_kernels(args):
         adcomb.debug_set_scan_engine(0)
         adcomb.debug_set_scan_range_tiles(0)
         del x, y, yb, xb
-    for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000)]:
+    for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000),
+                  ("sop", 50_000_000)]:
         if not want(f"reduce {op}"):
             continue
-        x = torch.from_numpy(synth.scan_values(g, "mm2_orth" if op == "mm2" else "add", n)).to(dev)
+        if op == "sop":
+            x = torch.from_numpy(synth.uniform(g, (n, 2), -1, 1)).to(dev)
+        else:
+            x = torch.from_numpy(synth.scan_values(g, "mm2_orth" if op == "mm2" else "add", n)).to(dev)
         if op == "mul":
             x = x * 0.05 + 1.0
         es = x.element_size() * (x.numel() // n)
@@ -484,20 +489,25 @@ def run_kernels(args):
         yb = torch.ones_like(y)
         xb = torch.empty_like(x)
         row(f"reduce {op} fwd", n, n * es, timeit(lambda: adcomb.reduce_fwd(op, x, y, saved, ws=ws)))
-        vjp_bytes = {"add": n * es, "min": n * es, "mul": 2 * n * es, "mm2": 2 * n * es}[op]
+        vjp_bytes = {"add": n * es, "min": n * es, "mul": 2 * n * es, "mm2": 2 * n * es, "sop": 2 * n * es}[op]
         row(f"reduce {op} vjp", n, vjp_bytes, timeit(lambda: adcomb.reduce_vjp(op, x, y, saved, yb, xbar=xb, ws=ws)))
         del x, xb
-    for op, n, m in [("add", 100_000_000, 1000), ("add", 50_000_000, 10_000_000), ("lin", 10_000_000, 1000)]:
+    for op, n, m in [("add", 100_000_000, 1000), ("add", 50_000_000, 10_000_000), ("lin", 10_000_000, 1000),
+                     ("sop", 50_000_000, 1000), ("sop", 50_000_000, 1_000_000)]:
         if not want(f"hist {op} m={m}"):
             continue
         k = torch.randint(0, m, (n,), dtype=torch.int32, device=dev)
-        v = torch.from_numpy(synth.scan_values(g, op, n)).to(dev)
+        if op == "sop":
+            v = torch.from_numpy(synth.uniform(g, (n, 2), -1, 1)).to(dev)
+        else:
+            v = torch.from_numpy(synth.scan_values(g, op, n)).to(dev)
         es = v.element_size() * (v.numel() // n)
         h, saved = adcomb.hist_fwd(op, m, k, v, ws=ws)
         hb = torch.randn_like(h)
         vb = torch.empty_like(v)
         row(f"hist {op} fwd m={m}", n, n * (4 + es), timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
-        row(f"hist {op} vjp m={m}", n, n * (4 + es),
+        # vjp: keys in, valsbar out, and the values too where the rule reads them
+        row(f"hist {op} vjp m={m}", n, n * (4 + (2 if op in ("lin", "sop") else 1) * es),
             timeit(lambda: adcomb.hist_vjp(op, m, k, v, None, h, saved, hb, valsbar=vb, ws=ws)))
         del k, v, vb
     print(f"| kernel | n | algorithmic bytes | ms | GB/s | frac of {kind} {peak:.0f} GB/s |")

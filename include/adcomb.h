@@ -57,7 +57,10 @@ typedef enum {
     ADC_OP_MIN = 2,   /* min (lifted with the argmin index)  */
     ADC_OP_MAX = 3,   /* max (lifted with the argmax index)  */
     ADC_OP_LIN = 4,   /* linFnComp on (b, c) pairs           */
-    ADC_OP_MM2 = 5    /* 2x2 matrix product                  */
+    ADC_OP_MM2 = 5,   /* 2x2 matrix product                  */
+    ADC_OP_SOP = 6    /* sumOfProd on (p, s) pairs: (p1,s1).(p2,s2) = (p1+p2+s1*s2, s1+s2),
+                         associative, commutative and invertible (Sec. 3.3); reduce and
+                         reduce_by_index only                                              */
 } adc_op;
 
 typedef enum { ADC_F32 = 0, ADC_F64 = 1 } adc_dtype;
@@ -97,7 +100,8 @@ size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int
  *                  of the non-zeros (Fig. 3's lifted primal)
  *           LIN/MM2 -- per-tile exclusive prefix and suffix partials used by
  *                  the general rule (Fig. 2)
- *   ops: ADD, MUL, MIN, MAX, LIN, MM2.  MIN/MAX need n < 2^31.
+ *           SOP -- unused (the invertible-operator rule needs only x and y)
+ *   ops: ADD, MUL, MIN, MAX, LIN, MM2, SOP.  MIN/MAX need n < 2^31.
  */
 adc_status adc_reduce_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
                           void *saved, void *ws, size_t ws_bytes, void *stream);
@@ -109,6 +113,9 @@ adc_status adc_reduce_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, 
  *   MUL     : three-case rule of Fig. 3 (division by x_i when there is no zero)
  *   LIN/MM2 : xbar_i = d(l_i . x_i . r_i)/dx_i ybar with l_i, r_i the exclusive
  *             prefix / suffix (Eq. red-adj, Fig. 2); for MM2 xbar_i = l_i^T ybar r_i^T
+ *   SOP     : invertible-operator rule (Sec. 3.3): b_i = y (.)^-1 x_i, then
+ *             xbar_i = d(b_i . x)/dx at x_i ybar = (ybar.p, ybar.p * (y.s - x_i.s) + ybar.s);
+ *             y is required (the fwd call's output)
  *   x, y and saved are the fwd call's input, output and residuals; ybar is one
  *   element in device memory.
  */
@@ -118,7 +125,7 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, 
 
 /* ------------------------------------------------------------------ scan --
  * Inclusive scan y_i = x_0 . x_1 . ... . x_i                      (Sec. 5.1)
- *   x, y : [n] elements.  ops: ADD, MUL, LIN, MM2.
+ *   x, y : [n] elements.  ops: ADD, MUL, LIN, MM2 (MIN, MAX, SOP: ADC_ERR_UNSUPPORTED).
  */
 adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
                         void *ws, size_t ws_bytes, void *stream);
@@ -171,11 +178,16 @@ adc_status adc_scan_fwd_noalloc(adc_op op, adc_dtype dtype, int64_t n, const voi
  *                   won (hist0 wins ties)             (Sec. 4.2.2, Fig. 5)
  *           MUL -- int32 n0[m] zero counts, then p[m] products of the non-zeros
  *                   (Sec. 4.2.3)
- *           LIN -- the stable sort permutation, the sorted keys and the sorted
- *                   values (general rule, Fig. 4)
- *   ops: ADD, MUL, MIN, MAX, LIN (LIN is not commutative: the fold follows the
- *   index order within each bin, computed through a stable sort).  MM2 is
+ *           SOP -- unused (the vjp reads hist)
+ *           LIN -- for m <= 2047 (fp32) / 1023 (fp64): per (bin, input chunk) the exclusive
+ *                   prefix and suffix of the bin's fold across chunks, and
+ *                   the bin totals (the chunk-local stable sort is redone in
+ *                   the vjp); for larger m: the stable sort permutation, the
+ *                   sorted keys and the sorted values (general rule, Fig. 4)
+ *   ops: ADD, MUL, MIN, MAX, LIN, SOP (LIN is not commutative: the fold follows
+ *   the index order within each bin, computed through a stable sort).  MM2 is
  *   ADC_ERR_UNSUPPORTED.  Requires 1 <= m < 2^31 and n < 2^31.
+ *   ADD and SOP keep no residuals (saved may be NULL).
  *   saved == NULL (MUL, MIN, MAX only) computes the ORIGINAL, un-lifted primal
  *   instead -- the plain product per bin with zeros included, or the plain
  *   min/max value -- and keeps no residuals, so no vjp can follow.  This is the
@@ -193,6 +205,9 @@ adc_status adc_hist_fwd(adc_op op, adc_dtype dtype, int64_t n, int64_t m, const 
  *   MUL     : per-bin zero-count rule                            (Sec. 4.2.3)
  *   LIN     : sorted segmented forward and reverse scans, then
  *             d(l_i . v_i . r_i)/dv_i histbar[k_i], scattered back (Fig. 4)
+ *   SOP     : invertible-operator rule per bin (Sec. 3.3, 4): with y = hist[k_i],
+ *             valsbar_i = (hb.p, hb.p * (y.s - v_i.s) + hb.s), hb = histbar[k_i];
+ *             hist0bar likewise with hist0 in place of v_i.  Needs vals and hist.
  *   hist and saved are the fwd call's output and residuals.
  */
 adc_status adc_hist_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t m, const int32_t *keys,
@@ -291,8 +306,9 @@ void adc_debug_set_stall_tile(int64_t tile);
 /*
  * Test hook: scan engine selection -- 0 automatic (range-partitioned for large
  * n, per-tile look-back otherwise), 1 per-tile look-back only, 2 range-
- * partitioned wherever it applies.  In the fault-injection hook above, the
- * "tile" of the range-partitioned engine is a range.
+ * partitioned wherever it applies, 3 range-partitioned with the range staged
+ * in shared memory by bulk (TMA) copies.  In the fault-injection hook above,
+ * the "tile" of the range engines is a range.
  */
 void adc_debug_set_scan_engine(int engine);
 

@@ -15,9 +15,11 @@ Residual policy (``policy="save"`` or ``"recompute"``):
                    forward scan in backward and keeps only x (less memory, one
                    more pass).
   reduce_by_index +: keys; min/max: keys and is[m]; *: keys, values, (n0, p);
-          lin    : the stable permutation with the sorted keys and values
-                   (16 B/element kept, against re-sorting in backward);
-                   "recompute" re-sorts in backward instead.
+          lin    : m <= 2047: per (bin, input chunk) prefix and suffix tables
+                   (about 16*m*n/4096 bytes; the chunk-local sort is redone in
+                   backward anyway); larger m: the stable permutation with the
+                   sorted keys and values (16 B/element).  "recompute" re-runs
+                   the forward in backward instead.
 """
 from __future__ import annotations
 

@@ -42,7 +42,10 @@ using namespace adc;
 
 namespace {
 
-bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_MM2; }
+bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_SOP; }
+// Operators a scan can take (min/max are reduce-only rules; sumOfProd's
+// invertible rule is a reduce / reduce_by_index rule).
+bool scan_op(adc_op op) { return op == ADC_OP_ADD || op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2; }
 bool valid_dt(adc_dtype dt) { return dt == ADC_F32 || dt == ADC_F64; }
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -85,7 +88,7 @@ size_t adc_workspace_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, in
     switch (kind) {
     case ADC_REDUCE: return reduce_ws_bytes(op, dt, n);
     case ADC_SCAN:
-        if (op == ADC_OP_MIN || op == ADC_OP_MAX) return 0;
+        if (!scan_op(op)) return 0;
         return scan_ws_bytes(op, dt, n);
     case ADC_HIST:
         if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
@@ -98,7 +101,7 @@ size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return 0;
     switch (kind) {
     case ADC_REDUCE: return reduce_saved_bytes(op, dt, n);
-    case ADC_SCAN: return 16;  // scans keep no residuals beyond x and y
+    case ADC_SCAN: return scan_op(op) ? 16 : 0;  // scans keep no residuals beyond x and y
     case ADC_HIST:
         if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
         return hist_saved_bytes(op, dt, n, m);
@@ -111,7 +114,7 @@ adc_status adc_reduce_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, voi
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && n >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(x, n) || !one_ok(y, dt)) return ADC_ERR_INVALID_ARG;
-    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && op != ADC_OP_SOP && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     adc_status st = prologue(ws, ws_bytes, reduce_ws_bytes(op, dt, n), s);
     if (st != ADC_OK) return st;
@@ -123,9 +126,10 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, con
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && n >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(xbar, n) || !one_ok(ybar, dt)) return ADC_ERR_INVALID_ARG;
-    if ((op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2) && !arr_ok(x, n)) return ADC_ERR_INVALID_ARG;
-    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
-    (void)y;
+    if ((op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2 || op == ADC_OP_SOP) && !arr_ok(x, n))
+        return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_SOP && !one_ok(y, dt)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && op != ADC_OP_SOP && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     adc_status st = prologue(ws, ws_bytes, reduce_ws_bytes(op, dt, n), s);
     if (st != ADC_OK) return st;
@@ -135,7 +139,7 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, con
 adc_status adc_scan_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void *y, void *ws, size_t ws_bytes,
                         void *stream) {
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
-    if (op == ADC_OP_MIN || op == ADC_OP_MAX) return ADC_ERR_UNSUPPORTED;
+    if (!scan_op(op)) return ADC_ERR_UNSUPPORTED;
     if (!arr_ok(x, n) || !arr_ok(y, n)) return ADC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     adc_status st = prologue(ws, ws_bytes, scan_ws_bytes(op, dt, n), s);
@@ -146,7 +150,7 @@ adc_status adc_scan_fwd(adc_op op, adc_dtype dt, int64_t n, const void *x, void 
 adc_status adc_scan_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const void *y, const void *ybar,
                         void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
-    if (op == ADC_OP_MIN || op == ADC_OP_MAX) return ADC_ERR_UNSUPPORTED;
+    if (!scan_op(op)) return ADC_ERR_UNSUPPORTED;
     if (!arr_ok(ybar, n) || !arr_ok(xbar, n)) return ADC_ERR_INVALID_ARG;
     if (op != ADC_OP_ADD && (!arr_ok(x, n) || !arr_ok(y, n))) return ADC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
@@ -179,10 +183,11 @@ adc_status adc_hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int
     if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(histbar, m) || !arr_ok(valsbar, n)) return ADC_ERR_INVALID_ARG;
     if (op != ADC_OP_LIN && !arr_ok(keys, n)) return ADC_ERR_INVALID_ARG;
-    if (op == ADC_OP_MUL && !arr_ok(vals, n)) return ADC_ERR_INVALID_ARG;
+    if ((op == ADC_OP_MUL || op == ADC_OP_SOP) && !arr_ok(vals, n)) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_SOP && (hist == nullptr || !aligned(hist, 16))) return ADC_ERR_INVALID_ARG;
     if ((hist0 != nullptr && !aligned(hist0, 16)) || (hist0bar != nullptr && !aligned(hist0bar, 16)))
         return ADC_ERR_INVALID_ARG;
-    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && op != ADC_OP_SOP && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
     cudaStream_t s = as_stream(stream);
     adc_status st = prologue(ws, ws_bytes, hist_ws_bytes(op, dt, n, m), s);
     if (st != ADC_OK) return st;
@@ -202,7 +207,7 @@ void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1
 
 void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
 
-void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 2) ? engine : 0; }
+void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 3) ? engine : 0; }
 void adc_debug_set_scan_range_tiles(int tiles) { g_scan_range_tiles = tiles > 0 ? tiles : 0; }
 
 }  // extern "C"

@@ -834,6 +834,7 @@ static size_t part_off(adc_op op, adc_dtype dt, int64_t m) { return align_up(bas
 
 size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     if (op == ADC_OP_LIN) return histgen_ws_bytes(dt, n, m);
+    if (op == ADC_OP_SOP) return kWsHeader;
     if (op != ADC_OP_ADD && op != ADC_OP_MUL && op != ADC_OP_MIN && op != ADC_OP_MAX) return 0;
     const size_t s = dt == ADC_F64 ? 8 : 4;
     // the partition scratch (about n * (2 + value bytes)) only where it can be chosen
@@ -846,7 +847,8 @@ size_t hist_ws_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
 size_t hist_saved_bytes(adc_op op, adc_dtype dt, int64_t n, int64_t m) {
     const size_t s = dt == ADC_F64 ? 8 : 4;
     switch (op) {
-    case ADC_OP_ADD: return 16;
+    case ADC_OP_ADD:
+    case ADC_OP_SOP: return 16;
     case ADC_OP_MIN:
     case ADC_OP_MAX: return (size_t)m * 4;
     case ADC_OP_MUL: return align_up((size_t)m * 4, 16) + (size_t)m * s;
@@ -1047,6 +1049,7 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
 adc_status hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
                     const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s) {
     if (op == ADC_OP_LIN) return histgen_fwd(dt, n, m, keys, vals, hist0, hist, saved, ws, s);
+    if (op == ADC_OP_SOP) return sop_hist_fwd(dt, n, m, keys, vals, hist0, hist, s);
     if (dt == ADC_F64)
         return hist_fwd_t<double>(op, n, m, keys, static_cast<const double *>(vals), static_cast<const double *>(hist0),
                                   static_cast<double *>(hist), saved, ws, s);
@@ -1097,7 +1100,8 @@ adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t
                     void *hist0bar, int accumulate, void *ws, cudaStream_t s) {
     if (op == ADC_OP_LIN)
         return histgen_vjp(dt, n, m, keys, vals, hist0, hist, saved, histbar, valsbar, hist0bar, accumulate, ws, s);
-    (void)hist;
+    if (op == ADC_OP_SOP)
+        return sop_hist_vjp(dt, n, m, keys, vals, hist0, hist, histbar, valsbar, hist0bar, accumulate, s);
     if (dt == ADC_F64)
         return hist_vjp_t<double>(op, n, m, keys, static_cast<const double *>(vals),
                                   static_cast<const double *>(hist0), saved, static_cast<const double *>(histbar),
@@ -1110,3 +1114,4 @@ adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t
 }  // namespace adc
 
 extern "C" void adc_debug_force_hist_strategy(int s) { adc::g_force_strategy = s; }
+int adc::hist_forced_strategy() { return adc::g_force_strategy; }

@@ -27,7 +27,7 @@ int num_sms();
 // Returns ADC_ERR_CUDA if the last launch failed.
 adc_status check_launch();
 
-inline int arity(adc_op op) { return op == ADC_OP_LIN ? 2 : (op == ADC_OP_MM2 ? 4 : 1); }
+inline int arity(adc_op op) { return (op == ADC_OP_LIN || op == ADC_OP_SOP) ? 2 : (op == ADC_OP_MM2 ? 4 : 1); }
 inline size_t elem_bytes(adc_op op, adc_dtype dt) { return (size_t)arity(op) * (dt == ADC_F64 ? 8 : 4); }
 
 // scan.cu
@@ -65,6 +65,26 @@ adc_status histgen_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, 
 size_t excl_scan_i32_region(int64_t n);
 adc_status excl_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, int slot, void *region,
                          cudaStream_t s);
+
+// hist_lin.cu (general reduce_by_index, linFnComp, m <= 2047 fp32 / 1023 fp64:
+// hierarchical stable sort)
+bool linh_applicable(adc_dtype dt, int64_t m);
+size_t linh_ws_bytes(adc_dtype dt, int64_t n, int64_t m);
+size_t linh_saved_bytes(adc_dtype dt, int64_t n, int64_t m);
+adc_status linh_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
+                    void *hist, void *saved, void *ws, cudaStream_t s);
+adc_status linh_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *saved,
+                    const void *histbar, void *valsbar, void *hist0bar, int accumulate, cudaStream_t s);
+// hist.cu: the strategy forced by the test hook (-1: automatic); for LIN, 2
+// forces the global radix-sort path
+int hist_forced_strategy();
+
+// hist_sop.cu (sumOfProd reduce_by_index, Sec. 3.3)
+adc_status sop_hist_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
+                        void *hist, cudaStream_t s);
+adc_status sop_hist_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
+                        const void *hist, const void *histbar, void *valsbar, void *hist0bar, int accumulate,
+                        cudaStream_t s);
 
 // hist_part.cu (reduce_by_index for tables beyond shared memory: partition by
 // bin range, then per-bucket shared-memory tables)

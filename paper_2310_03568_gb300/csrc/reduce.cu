@@ -60,6 +60,15 @@ template <typename T> struct RMul {
     __device__ State lift(T x, int64_t) const { return x == T(0) ? State{T(1), 1, 0} : State{x, 0, 0}; }
 };
 
+// sumOfProd (Sec. 3.3) on (p, s) = Pair{b: p, c: s}:
+// (p1,s1) . (p2,s2) = (p1 + p2 + s1*s2, s1 + s2); associative and commutative.
+template <typename T> struct RSop {
+    using State = Pair<T>;
+    __device__ State identity() const { return {T(0), T(0)}; }
+    __device__ State combine(const State &a, const State &b) const { return {a.b + b.b + a.c * b.c, a.c + b.c}; }
+    __device__ State lift(const Pair<T> &x, int64_t) const { return x; }
+};
+
 // General operators (non-commutative).
 template <typename T> struct GLin {
     using State = Pair<T>;
@@ -89,7 +98,7 @@ k_reduce_simple(const Op op, const T *__restrict__ x, const int64_t n, const int
         const int64_t c0 = t * TILE + (int64_t)threadIdx.x * ITEMS;
         if (c0 >= n) break;
         T v[ITEMS];
-        load_chunk(x, c0, n, v, T(0));
+        load_chunk(x, c0, n, v, T{});
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k)
             if (c0 + k < n) acc = op.combine(acc, op.lift(v[k], c0 + k));
@@ -121,6 +130,7 @@ template <typename T> __global__ void k_fin_sel(const MinMaxS<T> *r, T *y, int32
     *y = r->v;
     *k = r->i;
 }
+template <typename T> __global__ void k_fin_sop(const Pair<T> *r, Pair<T> *y) { *y = *r; }
 template <typename T> __global__ void k_fin_mul(const MulS<T> *r, T *y, int32_t *n0, T *p) {
     *y = r->z > 0 ? T(0) : r->p;
     *n0 = r->z;
@@ -350,6 +360,27 @@ __global__ void k_vjp_mul(T *__restrict__ xbar, const T *__restrict__ x, const T
 }
 
 // --------------------------------------------------------------- planning --
+// Sec. 3.3, the invertible-operator rule for sumOfProd: with b_i = y (.)^-1 x_i,
+// xbar_i = d(b_i . x)/dx ^T ybar = (ybar.p, ybar.p * b_i.s + ybar.s), b_i.s = y.s - x_i.s.
+template <typename T>
+__global__ void k_vjp_sop(Pair<T> *__restrict__ xbar, const Pair<T> *__restrict__ x, const Pair<T> *__restrict__ ybar,
+                          const Pair<T> *__restrict__ y, const int64_t n, const int accumulate) {
+    const Pair<T> yb = *ybar, yy = *y;
+    constexpr int V = 16 / sizeof(Pair<T>) > 0 ? 16 / sizeof(Pair<T>) : 1;  // pairs per 128-bit word
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c * V < n; c += stride) {
+        Pair<T> xv[V], o[V];
+        load_chunk(x, c * V, n, xv, Pair<T>{T(0), T(0)});
+        if (accumulate) load_chunk(xbar, c * V, n, o, Pair<T>{T(0), T(0)});
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const Pair<T> g{yb.b, yb.b * (yy.c - xv[k].c) + yb.c};
+            o[k] = accumulate ? Pair<T>{o[k].b + g.b, o[k].c + g.c} : g;
+        }
+        store_chunk(xbar, c * V, n, o);
+    }
+}
+
 template <typename T> struct RedItems {
     static constexpr int scalar = 64 / sizeof(T);
     static constexpr int pair = 64 / (2 * sizeof(T));  // 16 KB tiles of (b, c) pairs
@@ -402,12 +433,13 @@ template <typename T> static size_t red_ws_t(adc_op op, int64_t n) {
         const int64_t tiles = general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1;
         return op == ADC_OP_LIN ? general_ws<GLin<T>>(tiles) : general_ws<GMM2<T>>(tiles);
     }
-    const int64_t tiles = (n + kRedThreads * RedItems<T>::scalar - 1) / (kRedThreads * RedItems<T>::scalar);
+    const int items = op == ADC_OP_SOP ? RedItems<T>::pair : RedItems<T>::scalar;
+    const int64_t tiles = (n + kRedThreads * items - 1) / (kRedThreads * items);
     return kWsHeader + (size_t)(simple_grid(tiles) + 1) * 32 + 256;
 }
 
 size_t reduce_ws_bytes(adc_op op, adc_dtype dt, int64_t n) {
-    if (op > ADC_OP_MM2 || op < ADC_OP_ADD) return 0;
+    if (op > ADC_OP_SOP || op < ADC_OP_ADD) return 0;
     return dt == ADC_F64 ? red_ws_t<double>(op, n) : red_ws_t<float>(op, n);
 }
 
@@ -417,6 +449,7 @@ template <typename T> static size_t red_saved_t(adc_op op, int64_t n) {
     case ADC_OP_MIN:
     case ADC_OP_MAX: return 16;
     case ADC_OP_MUL: return 16;
+    case ADC_OP_SOP: return 16;
     case ADC_OP_LIN:
     case ADC_OP_MM2: return 2 * (size_t)(general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1) * general_state_bytes<T>(op);
     default: return 0;
@@ -477,6 +510,15 @@ static adc_status red_fwd_t(adc_op op, int64_t n, const void *xv, void *yv, void
                                      reinterpret_cast<T *>(static_cast<char *>(saved) + 8));
         return check_launch();
     }
+    case ADC_OP_SOP: {
+        RSop<T> o;
+        Pair<T> *r;
+        if ((st = launch_simple<RSop<T>, Pair<T>, RedItems<T>::pair>(o, static_cast<const Pair<T> *>(xv), n, ws, s,
+                                                                     &r)) != ADC_OK)
+            return st;
+        k_fin_sop<T><<<1, 1, 0, s>>>(r, static_cast<Pair<T> *>(yv));
+        return check_launch();
+    }
     case ADC_OP_LIN:
         return general_fwd<GLin<T>, T, RedItems<T>::pair>(n, xv, yv, saved, ws, s);
     case ADC_OP_MM2:
@@ -500,7 +542,6 @@ static unsigned elementwise_grid(int64_t work) {
 template <typename T>
 static adc_status red_vjp_t(adc_op op, int64_t n, const void *xv, const void *yv, const void *saved,
                             const void *ybar, void *xbar, int acc, cudaStream_t s) {
-    (void)yv;
     if (n == 0) return ADC_OK;
     constexpr int V = 16 / sizeof(T);
     switch (op) {
@@ -522,6 +563,13 @@ static adc_status red_vjp_t(adc_op op, int64_t n, const void *xv, const void *yv
             static_cast<const int32_t *>(saved), reinterpret_cast<const T *>(static_cast<const char *>(saved) + 8), n,
             acc);
         return check_launch();
+    case ADC_OP_SOP: {
+        constexpr int PV = 16 / sizeof(Pair<T>) > 0 ? 16 / sizeof(Pair<T>) : 1;
+        k_vjp_sop<T><<<elementwise_grid((n + PV - 1) / PV), 256, 0, s>>>(
+            static_cast<Pair<T> *>(xbar), static_cast<const Pair<T> *>(xv), static_cast<const Pair<T> *>(ybar),
+            static_cast<const Pair<T> *>(yv), n, acc);
+        return check_launch();
+    }
     case ADC_OP_LIN:
     case ADC_OP_MM2: {
         const int64_t Tn = general_tiles<T>(op, n);

@@ -382,11 +382,18 @@ static GenLayout gen_layout(size_t sb, int64_t n, int64_t m) {
     return L;
 }
 
-size_t histgen_ws_bytes(adc_dtype dt, int64_t n, int64_t m) { return gen_layout(dt == ADC_F64 ? 8 : 4, n, m).bytes; }
+// m <= 2047 fp32 / 1023 fp64 (and not forced to the global sort): the hierarchical path of
+// hist_lin.cu; otherwise the global stable radix sort below.
+static bool use_local(adc_dtype dt, int64_t m) { return linh_applicable(dt, m) && hist_forced_strategy() != 2; }
+
+size_t histgen_ws_bytes(adc_dtype dt, int64_t n, int64_t m) {
+    if (use_local(dt, m)) return linh_ws_bytes(dt, n, m);
+    return gen_layout(dt == ADC_F64 ? 8 : 4, n, m).bytes;
+}
 
 // saved: perm [n] i32, sorted keys [n] i32, sorted values [n] pairs
 size_t histgen_saved_bytes(adc_dtype dt, int64_t n, int64_t m) {
-    (void)m;
+    if (use_local(dt, m)) return linh_saved_bytes(dt, n, m);
     const size_t sb = dt == ADC_F64 ? 8 : 4;
     return align_up((size_t)n * 4, 256) * 2 + (size_t)n * 2 * sb + 256;
 }
@@ -492,6 +499,7 @@ adc_status excl_scan_i32(const int32_t *in, int32_t *out, int64_t n, void *ws, i
 
 adc_status histgen_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
                        void *hist, void *saved, void *ws, cudaStream_t s) {
+    if (use_local(dt, m)) return linh_fwd(dt, n, m, keys, vals, hist0, hist, saved, ws, s);
     if (dt == ADC_F64)
         return gen_fwd_t<double>(n, m, keys, static_cast<const Pair<double> *>(vals),
                                  static_cast<const Pair<double> *>(hist0), static_cast<Pair<double> *>(hist), saved, ws,
@@ -503,9 +511,8 @@ adc_status histgen_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, 
 adc_status histgen_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
                        const void *hist, const void *saved, const void *histbar, void *valsbar, void *hist0bar,
                        int accumulate, void *ws, cudaStream_t s) {
-    (void)keys;
-    (void)vals;
     (void)hist;
+    if (use_local(dt, m)) return linh_vjp(dt, n, m, keys, vals, saved, histbar, valsbar, hist0bar, accumulate, s);
     if (dt == ADC_F64)
         return gen_vjp_t<double>(n, m, static_cast<const Pair<double> *>(hist0), saved,
                                  static_cast<const Pair<double> *>(histbar), static_cast<Pair<double> *>(valsbar),

@@ -218,6 +218,46 @@ def test_hist_original_primal(op, dt, strategy):
     adcomb.debug_force_hist_strategy(-1)
 
 
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_hist_sop_invertible_rule(dt):
+    """sumOfProd reduce_by_index (Sec. 3.3 operator, Sec. 4 per bin): forward
+    (atomics split into s_old = atomicAdd(S, s); atomicAdd(P, p + s_old*s)) and
+    the invertible-operator vjp, against the oracle.  M_j bounds every partial
+    result of bin j's fold: |p| <= sum|p| + (sum|s|)^2 over hist0 and the bin."""
+    g = np.random.default_rng(25)
+    rtol = rtol_for(dt)
+    for n, m in CASES:
+        k = keys_oor(g, n, m)
+        v = synth.uniform(g, (n, 2), -1, 1, dt)
+        h0 = synth.uniform(g, (m, 2), -1, 1, dt)
+        for hist0 in (None, h0):
+            h, saved = adcomb.hist_fwd("sop", m, dev(k), dev(v), None if hist0 is None else dev(hist0))
+            ref = oracle.hist_fwd("sop", m, k, v, hist0)
+            inr = (k >= 0) & (k < m)
+            a = np.abs(v.astype(np.float64))
+            sp = np.bincount(k[inr], weights=a[inr, 0], minlength=m)
+            ss = np.bincount(k[inr], weights=a[inr, 1], minlength=m)
+            if hist0 is not None:
+                sp, ss = sp + np.abs(hist0[:, 0]), ss + np.abs(hist0[:, 1])
+            pop, _ = bin_stats(k, v[:, 0] if n else np.zeros(0), m)
+            assert_tol("hist sop fwd", host(h), ref, pop + 1, sp + ss ** 2, rtol)
+            hb = synth.normal(g, (m, 2), dt)
+            for acc in (False, True):
+                old = synth.normal(g, (n, 2), dt)
+                old_h0 = synth.normal(g, (m, 2), dt)
+                vb, h0b = adcomb.hist_vjp("sop", m, dev(k), dev(v), None if hist0 is None else dev(hist0), h, saved,
+                                          dev(hb), valsbar=dev(old) if acc else None,
+                                          hist0bar=dev(old_h0) if acc else None, want_hist0bar=True, accumulate=acc)
+                vr, h0r = oracle.hist_vjp("sop", m, k, v, hb, hist0)
+                kc = np.clip(k, 0, m - 1)
+                Mv = np.abs(hb[:, 0]) * ss + np.abs(hb[:, 1])
+                if acc:
+                    vr, h0r = vr + old, h0r + old_h0
+                assert_tol("hist sop vjp", host(vb), vr, np.where(inr, pop[kc] + 1, 1),
+                           np.where(inr, Mv[kc], 0) + (rowabs(old) if acc else 0), rtol)
+                assert_tol("hist sop hist0bar", host(h0b), h0r, pop + 1, Mv + (rowabs(old_h0) if acc else 0), rtol)
+
+
 # ------------------------------------------------------- general (lin) ----
 def lin_bin_scales(k, v, m, h0):
     """Per bin: max |partial fold| (hist0 first) and max suffix product of c, both >= 1."""
@@ -242,10 +282,18 @@ def lin_bin_scales(k, v, m, h0):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-def test_hist_lin_general_sort_path(dt):
+@pytest.mark.parametrize("path", ["auto", "sort"])
+def test_hist_lin_general_sort_path(dt, path):
+    """linFnComp reduce_by_index (not commutative: index order within a bin).
+    'auto' takes the hierarchical path (chunk-local stable sort + column scans)
+    for m <= 2047 (fp32) / 1023 (fp64) and the global stable radix sort above; 'sort' forces the
+    global sort everywhere (strategy hook 2), whose permutation is checked
+    bit-exact."""
     g = np.random.default_rng(24)
     rtol = rtol_for(dt)
-    for n, m in [(0, 3), (1, 1), (33, 4), (5000, 7), (40_000, 1000), (70_001, 2047), (50_000, 3000), (20_000, 70_000)]:
+    adcomb.debug_force_hist_strategy(2 if path == "sort" else -1)
+    for n, m in [(0, 3), (1, 1), (33, 4), (5000, 7), (40_000, 1000), (70_001, 2047), (50_000, 3000), (20_000, 70_000),
+                 (300_007, 1000)]:
         k = keys_oor(g, n, m)
         v = synth.scan_values(g, "lin", n, dt)
         h0 = synth.scan_values(g, "lin", m, dt)
@@ -255,9 +303,10 @@ def test_hist_lin_general_sort_path(dt):
             pop, _ = bin_stats(k, v[:, 0] if n else np.zeros(0), m)
             A, R = lin_bin_scales(k, v, m, hist0)
             assert_tol("hist lin fwd", host(h), ref, pop + 1, A, rtol)
-            # the sort permutation is unique (stable): bit-exact
-            perm = host(saved[: 4 * n].view(torch.int32)) if n else np.zeros(0, np.int32)
-            assert np.array_equal(perm, oracle.sort_perm(m, k).astype(np.int32))
+            if path == "sort" or m > (2047 if dt == np.float32 else 1023):
+                # the sort permutation is unique (stable): bit-exact
+                perm = host(saved[: 4 * n].view(torch.int32)) if n else np.zeros(0, np.int32)
+                assert np.array_equal(perm, oracle.sort_perm(m, k).astype(np.int32))
             hb = synth.normal(g, (m, 2), dt)
             for acc in (False, True):
                 old = synth.normal(g, (n, 2), dt)
@@ -273,6 +322,7 @@ def test_hist_lin_general_sort_path(dt):
                 assert_tol("hist lin vjp", host(vb), vr, np.where(inr, pop[kc] + 1, 1), scale, rtol)
                 if not acc:
                     assert_tol("hist lin hist0bar", host(h0b), h0r, pop + 1, 3 * A * R * rowabs(hb), rtol)
+    adcomb.debug_force_hist_strategy(-1)
 
 
 def test_hist_unsupported_and_invalid():

@@ -138,3 +138,31 @@ def test_reduce_mm2_equals_last_scan_element():
     lmax = rowabs(oracle.scan_fwd("mm2", x)).max()
     assert_tol("reduce", host(y)[None], ref[None], 70_001, lmax, 1e-5)
     assert_tol("scan last", host(s)[-1][None], ref[None], 70_001, lmax, 1e-5)
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+def test_reduce_sop_invertible_rule(dt):
+    """sumOfProd on (p, s) pairs (Sec. 3.3): forward against the oracle's left
+    fold; vjp by the invertible-operator rule against the oracle's sequential
+    chain rule.  M bounds every partial result of the fold: |p| <= sum|p_i| +
+    (sum|s_i|)^2."""
+    g = np.random.default_rng(14)
+    rtol = rtol_for(dt)
+    for n in SIZES:
+        x = synth.uniform(g, (n, 2), -1, 1, dt)
+        y, _ = adcomb.reduce_fwd("sop", dev(x))
+        ref = oracle.reduce_fwd("sop", x)
+        a = np.abs(x.astype(np.float64))
+        M = a[:, 0].sum() + a[:, 1].sum() ** 2 if n else 0.0
+        assert_tol("reduce sop fwd", host(y).reshape(1, 2), ref.reshape(1, 2), n, M, rtol)
+        yb, ybd = ybar_dev(g, 2, dt)
+        xb = adcomb.reduce_vjp("sop", dev(x), y, None, ybd)
+        xr = oracle.reduce_vjp("sop", x, yb)
+        if n:
+            assert np.array_equal(host(xb)[:, 0], np.full(n, yb[0], dt))  # d/dp_i = 1: a broadcast
+        Mv = abs(float(yb[0])) * (a[:, 1].sum() if n else 0.0) + abs(float(yb[1]))
+        assert_tol("reduce sop vjp", host(xb).reshape(n, 2), xr.reshape(n, 2), n, Mv, rtol)
+        if n:
+            old = synth.normal(g, (n, 2), dt)
+            xb = adcomb.reduce_vjp("sop", dev(x), y, None, ybd, xbar=dev(old), accumulate=True)
+            assert_tol("reduce sop vjp acc", host(xb).reshape(n, 2), xr + old, n, Mv + rowabs(old), rtol)

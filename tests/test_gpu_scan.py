@@ -70,10 +70,11 @@ def lib():
     adcomb.debug_set_scan_range_tiles(0)
 
 
-@pytest.fixture(params=[1, 2], ids=["per-tile", "ranges"])
+@pytest.fixture(params=[1, 2, 3], ids=["per-tile", "ranges", "staged"])
 def engine(request):
-    """Both scan engines: per-tile look-back, and range-partitioned (forced even
-    for small n, where several ranges are empty)."""
+    """All scan engines: per-tile look-back, range-partitioned, and
+    range-partitioned with TMA staging in shared memory (forced even for small
+    n, where a range may be a single ragged tile)."""
     adcomb.debug_set_scan_engine(request.param)
     yield request.param
     adcomb.debug_set_scan_engine(0)
@@ -96,9 +97,10 @@ def test_scan_accumulate(op, engine):
     check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)
 
 
+@pytest.mark.parametrize("engine_id", [0, 3], ids=["auto", "staged"])
 @pytest.mark.parametrize("range_tiles", [0, 3, 16])
 @pytest.mark.parametrize("op", ["add", "lin", "mm2"])
-def test_scan_ranges_engine_many_tiles(op, range_tiles):
+def test_scan_ranges_engine_many_tiles(op, range_tiles, engine_id):
     """Large enough that the automatic choice is the range-partitioned engine
     (several tiles per range); also with more, smaller ranges than resident
     blocks (3 tiles: a ragged last range)."""
@@ -106,10 +108,12 @@ def test_scan_ranges_engine_many_tiles(op, range_tiles):
     n = {"add": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001}[op]
     x = make_x(g, op, n, np.float32)
     try:
+        adcomb.debug_set_scan_engine(engine_id)
         adcomb.debug_set_scan_range_tiles(range_tiles)
         check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
     finally:
         adcomb.debug_set_scan_range_tiles(0)
+        adcomb.debug_set_scan_engine(0)
 
 
 def test_mul_scan_zero_paths_exact():
