@@ -7,9 +7,10 @@ GPU library.
 
 Every function takes numpy arrays, casts them to fp64 (keys to int64) and
 returns fp64 numpy arrays.  Operators are named by strings:
-``"add" "mul" "min" "max" "lin" "mm2" "sop"`` (Fig. 8 of the paper for the tuple
+``"add" "mul" "min" "max" "lin" "mm2" "mm3" "mm5" "sop"`` (Fig. 8 of the paper for the tuple
 operators).  Tuple elements are arrays of shape ``[n, d]`` (d = 2 for lin as
-``(b, c)`` and for sop as ``(p, s)``, d = 4 for mm2 as row-major ``(a, b, c, d)``).
+``(b, c)`` and for sop as ``(p, s)``, d = 4 / 9 / 25 for the row-major 2x2 / 3x3 / 5x5
+matrices).
 
 Parity note: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_*.py`` (closed forms, brute force, finite differences,
@@ -30,8 +31,8 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lock = threading.Lock()
 _lib = None
 
-OPS = {"add": 0, "mul": 1, "min": 2, "max": 3, "lin": 4, "mm2": 5, "sop": 6}
-ARITY = {"add": 1, "mul": 1, "min": 1, "max": 1, "lin": 2, "mm2": 4, "sop": 2}
+OPS = {"add": 0, "mul": 1, "min": 2, "max": 3, "lin": 4, "mm2": 5, "sop": 6, "mm3": 7, "mm5": 8}
+ARITY = {"add": 1, "mul": 1, "min": 1, "max": 1, "lin": 2, "mm2": 4, "sop": 2, "mm3": 9, "mm5": 25}
 
 
 def build(force: bool = False) -> str:

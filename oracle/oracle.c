@@ -36,6 +36,7 @@
  *   LIN (linFnComp)    : (b, c) meaning x -> b + c*x;
  *                        (b1,c1) (.) (b2,c2) = (b2 + c2*b1, c2*c1)     (d = 2)
  *   MM2 (matMul2x2)    : (a, b, c, d) row-major 2x2; X (.) Y = X * Y   (d = 4)
+ *   MM3, MM5           : row-major 3x3 / 5x5 matrices, X (.) Y = X * Y (d = 9, 25)
  *   SOP (sumOfProd)    : (p, s); (p1,s1) (.) (p2,s2) = (p1 + p2 + s1*s2, s1 + s2),
  *                        associative and commutative (Sec. 3.3's example of an
  *                        invertible operator); with elements (0, a_i) the
@@ -55,14 +56,33 @@
 #include <stdlib.h>
 #include <string.h>
 
-enum { ORC_ADD = 0, ORC_MUL = 1, ORC_MIN = 2, ORC_MAX = 3, ORC_LIN = 4, ORC_MM2 = 5, ORC_SOP = 6 };
+enum { ORC_ADD = 0, ORC_MUL = 1, ORC_MIN = 2, ORC_MAX = 3, ORC_LIN = 4, ORC_MM2 = 5, ORC_SOP = 6,
+       ORC_MM3 = 7, ORC_MM5 = 8 };
 
-#define MAXD 4
+#define MAXD 25
+
+/* Side of the square matrix operators, 0 for the others. */
+static int mat_side(int op) {
+    if (op == ORC_MM2) return 2;
+    if (op == ORC_MM3) return 3;
+    if (op == ORC_MM5) return 5;
+    return 0;
+}
 
 static int arity(int op) {
     if (op == ORC_LIN || op == ORC_SOP) return 2;
-    if (op == ORC_MM2) return 4;
+    if (mat_side(op)) return mat_side(op) * mat_side(op);
     return 1;
+}
+
+/* Z = X Y for q x q row-major matrices. */
+static void mat_product(int q, const double *x, const double *y, double *z) {
+    for (int i = 0; i < q; i++)
+        for (int j = 0; j < q; j++) {
+            double s = 0.0;
+            for (int k = 0; k < q; k++) s += x[q * i + k] * y[q * k + j];
+            z[q * i + j] = s;
+        }
 }
 
 int oracle_arity(int op) { return arity(op); }
@@ -75,7 +95,12 @@ static void neutral(int op, double *e) {
     case ORC_MIN: e[0] = INFINITY; break;
     case ORC_MAX: e[0] = -INFINITY; break;
     case ORC_LIN: e[0] = 0.0; e[1] = 1.0; break;            /* x -> 0 + 1*x */
-    case ORC_MM2: e[0] = 1.0; e[1] = 0.0; e[2] = 0.0; e[3] = 1.0; break;
+    case ORC_MM2:
+    case ORC_MM3:
+    case ORC_MM5:
+        for (int i = 0; i < mat_side(op); i++)
+            for (int j = 0; j < mat_side(op); j++) e[mat_side(op) * i + j] = (i == j) ? 1.0 : 0.0;
+        break;
     case ORC_SOP: e[0] = 0.0; e[1] = 0.0; break;
     }
 }
@@ -107,12 +132,9 @@ static void combine(int op, const double *x, const double *y, double *z) {
         t[1] = y[1] * x[1];
         break;
     case ORC_MM2:                      /* Z[i][j] = sum_k X[i][k] * Y[k][j] */
-        for (int i = 0; i < 2; i++)
-            for (int j = 0; j < 2; j++) {
-                double s = 0.0;
-                for (int k = 0; k < 2; k++) s += x[2 * i + k] * y[2 * k + j];
-                t[2 * i + j] = s;
-            }
+    case ORC_MM3:
+    case ORC_MM5:
+        mat_product(mat_side(op), x, y, t);
         break;
     case ORC_SOP:                      /* (p1,s1) (.) (p2,s2) = (p1 + p2 + s1*s2, s1 + s2) */
         t[0] = x[0] + y[0] + x[1] * y[1];
@@ -145,20 +167,24 @@ static void combine_vjp(int op, const double *x, const double *y, int xwins,
         yb[1] = x[0] * zb[0] + x[1] * zb[1];
         break;
     case ORC_MM2:
+    case ORC_MM3:
+    case ORC_MM5: {
         /* Z = X Y:  Xb[i][k] = sum_j Zb[i][j] Y[k][j];  Yb[k][j] = sum_i X[i][k] Zb[i][j] */
-        for (int i = 0; i < 2; i++)
-            for (int k = 0; k < 2; k++) {
+        const int q = mat_side(op);
+        for (int i = 0; i < q; i++)
+            for (int k = 0; k < q; k++) {
                 double s = 0.0;
-                for (int j = 0; j < 2; j++) s += zb[2 * i + j] * y[2 * k + j];
-                xb[2 * i + k] = s;
+                for (int j = 0; j < q; j++) s += zb[q * i + j] * y[q * k + j];
+                xb[q * i + k] = s;
             }
-        for (int k = 0; k < 2; k++)
-            for (int j = 0; j < 2; j++) {
+        for (int k = 0; k < q; k++)
+            for (int j = 0; j < q; j++) {
                 double s = 0.0;
-                for (int i = 0; i < 2; i++) s += x[2 * i + k] * zb[2 * i + j];
-                yb[2 * k + j] = s;
+                for (int i = 0; i < q; i++) s += x[q * i + k] * zb[q * i + j];
+                yb[q * k + j] = s;
             }
         break;
+    }
     case ORC_SOP:
         /* z0 = x0 + y0 + x1*y1, z1 = x1 + y1 */
         xb[0] = zb[0];
@@ -183,14 +209,18 @@ static void combine_jvp(int op, const double *x, const double *y, int xwins,
         t[1] = yd[1] * x[1] + y[1] * xd[1];
         break;
     case ORC_MM2:
-        for (int i = 0; i < 2; i++)
-            for (int j = 0; j < 2; j++) {
+    case ORC_MM3:
+    case ORC_MM5: {
+        const int q = mat_side(op);
+        for (int i = 0; i < q; i++)
+            for (int j = 0; j < q; j++) {
                 double s = 0.0;
-                for (int k = 0; k < 2; k++)
-                    s += xd[2 * i + k] * y[2 * k + j] + x[2 * i + k] * yd[2 * k + j];
-                t[2 * i + j] = s;
+                for (int k = 0; k < q; k++)
+                    s += xd[q * i + k] * y[q * k + j] + x[q * i + k] * yd[q * k + j];
+                t[q * i + j] = s;
             }
         break;
+    }
     case ORC_SOP:
         t[0] = xd[0] + yd[0] + xd[1] * y[1] + x[1] * yd[1];
         t[1] = xd[1] + yd[1];

@@ -151,8 +151,25 @@ def test_sop_adjoint_is_the_all_but_one_sum():
     assert_close(xb[:, 1], yb[0] * (S - x[:, 1]) + yb[1], rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("q,op", [(3, "mm3"), (5, "mm5")])
+def test_mmq_reduce_and_adjoint_match_numpy_products(q, op):
+    # Eq. red-adj for Z = L_i A_i R_i:  Abar_i = L_i^T Zbar R_i^T, with numpy products.
+    n = 10
+    m = RNG.uniform(-1, 1, (n, q * q)) / np.sqrt(q)
+    mats = [a.reshape(q, q) for a in m]
+    assert_close(oracle.reduce_fwd(op, m).reshape(q, q), functools.reduce(np.matmul, mats, np.eye(q)),
+                 rtol=1e-12, atol=1e-15)
+    zb = RNG.standard_normal(q * q)
+    xb = oracle.reduce_vjp(op, m, zb)
+    Zb = zb.reshape(q, q)
+    for i in range(n):
+        L = functools.reduce(np.matmul, mats[:i], np.eye(q))
+        R = functools.reduce(np.matmul, mats[i + 1:], np.eye(q))
+        assert_close(xb[i].reshape(q, q), L.T @ Zb @ R.T, rtol=1e-10, atol=1e-13)
+
+
 @pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("min", 1), ("max", 1), ("lin", 2), ("mm2", 4),
-                                  ("sop", 2)])
+                                  ("sop", 2), ("mm3", 9)])
 def test_vjp_finite_differences(op, d):
     n = 24
     shape = (n,) if d == 1 else (n, d)

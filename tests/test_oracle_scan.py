@@ -137,17 +137,49 @@ def test_mm2_scan_last_equals_reduce():
     assert_close(oracle.scan_fwd("mm2", m)[-1], oracle.reduce_fwd("mm2", m), rtol=0, atol=0)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4)])
+@pytest.mark.parametrize("q,op", [(3, "mm3"), (5, "mm5")])
+def test_mmq_scan_is_the_running_matrix_product(q, op):
+    m = RNG.uniform(-1, 1, (30, q * q)) / np.sqrt(q)
+    acc = np.eye(q)
+    ref = []
+    for a in m:
+        acc = acc @ a.reshape(q, q)
+        ref.append(acc.reshape(-1))
+    assert_close(oracle.scan_fwd(op, m), np.array(ref), rtol=1e-12, atol=1e-14)
+
+
+@pytest.mark.parametrize("q,op", [(3, "mm3"), (5, "mm5")])
+def test_mmq_scan_embeds_mm2_and_its_adjoint(q, op):
+    # M -> blockdiag(M, I): the q x q running product is blockdiag(P, I), and the
+    # adjoint restricted to the 2x2 block is the 2x2 adjoint.
+    n = 25
+    m2 = RNG.uniform(-1, 1, (n, 4))
+    mq = np.zeros((n, q, q))
+    mq[:, :2, :2] = m2.reshape(n, 2, 2)
+    for k in range(2, q):
+        mq[:, k, k] = 1.0
+    P = oracle.scan_fwd(op, mq.reshape(n, -1)).reshape(n, q, q)
+    assert_close(P[:, :2, :2].reshape(n, 4), oracle.scan_fwd("mm2", m2), rtol=1e-12, atol=1e-14)
+    yb2 = RNG.standard_normal((n, 4))
+    ybq = np.zeros((n, q, q))
+    ybq[:, :2, :2] = yb2.reshape(n, 2, 2)
+    Mb = oracle.scan_vjp(op, mq.reshape(n, -1), ybq.reshape(n, -1)).reshape(n, q, q)
+    assert_close(Mb[:, :2, :2].reshape(n, 4), oracle.scan_vjp("mm2", m2, yb2), rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25)])
 def test_scan_vjp_finite_differences(op, d):
     n = 20
     shape = (n,) if d == 1 else (n, d)
     x = RNG.uniform(0.6, 1.3, shape)
+    if op in ("mm3", "mm5"):
+        x = x / np.sqrt(d)  # keep the running products O(1), so differences stay accurate
     yb = RNG.standard_normal(shape)
     assert_close(oracle.scan_vjp(op, x, yb), fd_vjp(lambda z: oracle.scan_fwd(op, z), x, yb),
                  rtol=1e-6, atol=1e-7)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4)])
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25)])
 def test_scan_dot_product(op, d):
     n = 64
     shape = (n,) if d == 1 else (n, d)
