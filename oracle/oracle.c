@@ -326,12 +326,24 @@ void oracle_reduce_mul_lifted(int64_t n, const double *x, int64_t *nzero, double
 /* scan (Sec. 5)                                                             */
 /* ------------------------------------------------------------------------ */
 
+/*
+ * For min/max scans: does the running result rs[i-1] win against as[i]?  The
+ * running result always comes from an earlier index, so it wins ties (Fig. 5's
+ * lifted operator, lowest index first).
+ */
+static int scan_left_wins(int op, const double *prev, const double *xi, int64_t i) {
+    return left_wins(op, prev[0], i - 1, xi[0], i);
+}
+
 /* Inclusive scan by the loop of Sec. 5.1: rs[0] = as[0]; rs[i] = rs[i-1] (.) as[i]. */
 void oracle_scan_fwd(int op, int64_t n, const double *x, double *y) {
     int d = arity(op);
     if (n <= 0) return;
     memcpy(y, x, sizeof(double) * d);
-    for (int64_t i = 1; i < n; i++) combine(op, y + (i - 1) * d, x + i * d, y + i * d);
+    for (int64_t i = 1; i < n; i++) {
+        if (is_select(op)) y[i] = scan_left_wins(op, y + i - 1, x + i, i) ? y[i - 1] : x[i];
+        else combine(op, y + (i - 1) * d, x + i * d, y + i * d);
+    }
 }
 
 /*
@@ -340,8 +352,9 @@ void oracle_scan_fwd(int op, int64_t n, const double *x, double *y) {
  *   for i = n-1 .. 1:  rb[i-1] += d(rs[i-1] (.) as[i])/d rs[i-1] * rb[i]
  *                      ab[i]    = d(rs[i-1] (.) as[i])/d as[i]   * rb[i]
  *   ab[0] = rb[0]
- * (MIN/MAX are not scan operators here.)  rbar, when not NULL, receives the
- * final rb: the adjoint of each scan result rs[i] (lambda_i).
+ * For min/max the step's derivative follows the selected operand (the
+ * earlier one on ties).  rbar, when not NULL, receives the final rb: the
+ * adjoint of each scan result rs[i] (lambda_i).
  */
 void oracle_scan_vjp_rbar(int op, int64_t n, const double *x, const double *ybar, double *xbar,
                           double *rbar) {
@@ -353,7 +366,8 @@ void oracle_scan_vjp_rbar(int op, int64_t n, const double *x, const double *ybar
     oracle_scan_fwd(op, n, x, rs);
     memcpy(rb, ybar, sizeof(double) * d * (size_t)n);
     for (int64_t i = n - 1; i >= 1; i--) {
-        combine_vjp(op, rs + (i - 1) * d, x + i * d, 0, rb + i * d, xb, yb);
+        const int xw = is_select(op) ? scan_left_wins(op, rs + i - 1, x + i, i) : 0;
+        combine_vjp(op, rs + (i - 1) * d, x + i * d, xw, rb + i * d, xb, yb);
         for (int k = 0; k < d; k++) rb[(i - 1) * d + k] += xb[k];
         memcpy(xbar + i * d, yb, sizeof(double) * d);
     }
@@ -374,8 +388,10 @@ void oracle_scan_jvp(int op, int64_t n, const double *x, const double *xdot, dou
     double *rs = (double *)malloc(sizeof(double) * d * (size_t)n);
     oracle_scan_fwd(op, n, x, rs);
     memcpy(ydot, xdot, sizeof(double) * d);
-    for (int64_t i = 1; i < n; i++)
-        combine_jvp(op, rs + (i - 1) * d, x + i * d, 0, ydot + (i - 1) * d, xdot + i * d, ydot + i * d);
+    for (int64_t i = 1; i < n; i++) {
+        const int xw = is_select(op) ? scan_left_wins(op, rs + i - 1, x + i, i) : 0;
+        combine_jvp(op, rs + (i - 1) * d, x + i * d, xw, ydot + (i - 1) * d, xdot + i * d, ydot + i * d);
+    }
     free(rs);
 }
 

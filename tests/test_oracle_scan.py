@@ -167,19 +167,41 @@ def test_mmq_scan_embeds_mm2_and_its_adjoint(q, op):
     assert_close(Mb[:, :2, :2].reshape(n, 4), oracle.scan_vjp("mm2", m2, yb2), rtol=1e-11, atol=1e-13)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25)])
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_scan_is_the_running_extremum_with_one_hot_adjoints(op):
+    # rs_i = min(as_0..as_i) (numpy's accumulate); with ties the earliest
+    # index is selected, so the adjoint of rs_i goes to the first position
+    # of the running extremum (brute force over every output).
+    n = 300
+    x = (RNG.integers(0, 20, n) - 10) / 4.0  # few levels: ties everywhere
+    acc = np.minimum.accumulate if op == "min" else np.maximum.accumulate
+    assert np.array_equal(oracle.scan_fwd(op, x), acc(x))
+    yb = RNG.standard_normal(n)
+    expect = np.zeros(n)
+    for i in range(n):
+        seg = x[: i + 1]
+        j = int(np.argmin(seg) if op == "min" else np.argmax(seg))  # first occurrence
+        expect[j] += yb[i]
+    assert_close(oracle.scan_vjp(op, x, yb), expect, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25),
+                                  ("min", 1), ("max", 1)])
 def test_scan_vjp_finite_differences(op, d):
     n = 20
     shape = (n,) if d == 1 else (n, d)
     x = RNG.uniform(0.6, 1.3, shape)
     if op in ("mm3", "mm5"):
         x = x / np.sqrt(d)  # keep the running products O(1), so differences stay accurate
+    if op in ("min", "max"):
+        x = RNG.permutation(n) / n + 0.1  # distinct values: a differentiable point
     yb = RNG.standard_normal(shape)
     assert_close(oracle.scan_vjp(op, x, yb), fd_vjp(lambda z: oracle.scan_fwd(op, z), x, yb),
                  rtol=1e-6, atol=1e-7)
 
 
-@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25)])
+@pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25),
+                                  ("min", 1), ("max", 1)])
 def test_scan_dot_product(op, d):
     n = 64
     shape = (n,) if d == 1 else (n, d)
