@@ -37,9 +37,24 @@ OPS = ("mul", "min", "max")
 METRIC = "vjp elements/s & % HBM roofline; AD overhead = vjp time / primal time"
 WORKLOAD = ("reduce_by_index specialisations fp32: n=50M uniform int32 bins, m in {31,401,50000,10M}, "
             "ops * (1% zeros), min, max (1024 levels); lifted forward + vjp per (op, m)")
-# our kernels launched per API call (see csrc/hist.cu)
-LAUNCHES = {("fwd", "mul"): 3, ("vjp", "mul"): 1, ("fwd", "min"): 3, ("vjp", "min"): 2,
-            ("fwd", "max"): 3, ("vjp", "max"): 2, ("prim", "mul"): 2, ("prim", "min"): 2, ("prim", "max"): 2}
+# DRAM bytes (read + write) per call measured by ncu on n = 20M, m = 10M and
+# scaled to n by the parts that grow with n (profiles/hist_partition_kernels_n20M_m10M.md):
+# the roofline's `traffic` for the dominant call, when it is one of these.
+TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.0, 106e6), ("fwd", "min", 10_000_000): (29.8, 128e6),
+                    ("fwd", "max", 10_000_000): (29.8, 128e6)}
+
+
+def launches(phase, op, m, n):
+    """Our kernels launched by one call (csrc/hist.cu, hist_part.cu): the lifted
+    forward is init + table kernel + finaliser, or, partitioned by bin range
+    (m >= 2^18), count + count scan + scatter + per-bucket tables + finaliser;
+    the * vjp is coefficient tables + gather; the min/max vjp is a zero-fill +
+    scatter, or one gather pass when bins are sparse (8m > n)."""
+    if phase == "fwd":
+        return 5 if m >= (1 << 18) else 3
+    if op == "mul":
+        return 2
+    return 1 if m * 8 > n else 2
 
 
 def parse():
@@ -247,13 +262,15 @@ def run_ours(args, world, rank, local):
     alg = {"fwd": 8 * n, "vjp": {"mul": 12 * n, "min": 4 * n, "max": 4 * n}[op_d]}[ph_d]
     peak, peak_kind = read_peaks()
     achieved = alg / (call_ms[dom] * 1e-3) / 1e9
+    tr = TRAFFIC_PER_ELEM.get((ph_d, op_d, m_d))
+    traffic = tr[0] * n + tr[1] if tr else None
     total_elems = world * len(BINS) * len(OPS) * n
     value = total_elems / (step_ms * 1e-3)
 
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world)
-    launches = args.steps * sum(LAUNCHES[("fwd", op)] + LAUNCHES[("vjp", op)] for op in OPS) * len(BINS)
+    n_launch = args.steps * sum(launches("fwd", op, m, n) + launches("vjp", op, m, n) for op in OPS for m in BINS)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -274,13 +291,13 @@ def run_ours(args, world, rank, local):
                        "instances_per_step": len(BINS) * len(OPS), "parallelism": f"replicas x{world}",
                        "l2": "inputs larger than L2 (200 MB keys + 200 MB values per instance); no flush"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": traffic,
                          "kernel": f"hist_{ph_d} {op_d} m={m_d}", "algorithmic_bytes": alg,
                          "peak_source": f"{peak_kind} hbm_gbs"},
             "ad_overhead": ad,
             "per_call_ms": {f"{op}/{m}/{ph}": round(v, 4) for (op, m, ph), v in call_ms.items()},
             "primal_ms": {f"{op}/{m}": round(statistics.mean(v), 4) for (op, m, _), v in prim_ms.items()},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches, "clocks": clk,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk,
             "batched": batched,
         }
         print(json.dumps(line))
@@ -310,7 +327,9 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
     hist_d = {i: torch.empty(i[1], dtype=torch.float32, device=dev) for i in inst}
     vb_d = {i: torch.empty(n, dtype=torch.float32, device=dev) for i in inst}
     comp = torch.cuda.current_stream()
-    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    # several copy streams per direction, so that the copy engines work in parallel
+    s_ins = [torch.cuda.Stream(device=dev) for _ in range(2)]
+    s_outs = [torch.cuda.Stream(device=dev) for _ in range(3)]
     ev = lambda: torch.cuda.Event()  # noqa: E731
     prev_done = None                      # compute of the previous step (inputs free)
     prev_read = {i: None for i in inst}   # D2H of the previous step (outputs free)
@@ -320,11 +339,12 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
         nonlocal prev_done, h2d, d2h
         h2d = d2h = 0
         ready_k, ready_v = {}, {}
-        with torch.cuda.stream(s_in):
-            if prev_done is not None:
-                s_in.wait_event(prev_done)
-            order = [("k", BINS[0])] + [("v", op) for op in OPS] + [("k", m) for m in BINS[1:]]
-            for kind, key in order:
+        order = [("k", BINS[0])] + [("v", op) for op in OPS] + [("k", m) for m in BINS[1:]]
+        for j, (kind, key) in enumerate(order):
+            s_in = s_ins[j % len(s_ins)]
+            with torch.cuda.stream(s_in):
+                if prev_done is not None:
+                    s_in.wait_event(prev_done)
                 if kind == "k":
                     k_d[key].copy_(pin_k[key], non_blocking=True)
                     hb_d[key].copy_(pin_h[key], non_blocking=True)
@@ -348,8 +368,9 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
             done[(op, m)] = ev()
             done[(op, m)].record(comp)
         prev_done = done[inst[-1]]
-        with torch.cuda.stream(s_out):
-            for i in inst:
+        for j, i in enumerate(inst):
+            s_out = s_outs[j % len(s_outs)]
+            with torch.cuda.stream(s_out):
                 s_out.wait_event(done[i])
                 out_h[i].copy_(hist_d[i], non_blocking=True)
                 out_v[i].copy_(vb_d[i], non_blocking=True)
@@ -364,13 +385,14 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
     a.record(comp)
     for _ in range(steps):
         step()
-    comp.wait_stream(s_out)
+    for so in s_outs:
+        comp.wait_stream(so)
     b.record(comp)
     torch.cuda.synchronize()
     ms = a.elapsed_time(b) / steps
     return {"value": world * len(BINS) * len(OPS) * n / (ms * 1e-3), "unit": "elements/s",
             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": ms,
-            "overlap": "H2D and D2H on their own streams, ordered by events against the compute stream"}
+            "overlap": "H2D on 2 and D2H on 3 streams of their own, ordered by events against the compute stream"}
 
 
 def run_batched(dev, seed=4):
@@ -453,7 +475,8 @@ def run_kernels(args):
     for op, dt, n in [("add", np.float32, 100_000_000), ("mul", np.float32, 100_000_000),
                       ("lin", np.float32, 100_000_000), ("mm2", np.float32, 10_000_000),
                       ("add", np.float64, 10_000_000), ("mul", np.float64, 10_000_000),
-                      ("lin", np.float64, 10_000_000)]:
+                      ("lin", np.float64, 10_000_000), ("mm3", np.float32, 10_000_000),
+                      ("mm5", np.float32, 4_000_000)]:
         if not want(f"scan {op} {np.dtype(dt).name}"):
             continue
         x = torch.from_numpy(synth.scan_values(g, op, n, dt)).to(dev)

@@ -58,9 +58,11 @@ typedef enum {
     ADC_OP_MAX = 3,   /* max (lifted with the argmax index)  */
     ADC_OP_LIN = 4,   /* linFnComp on (b, c) pairs           */
     ADC_OP_MM2 = 5,   /* 2x2 matrix product                  */
-    ADC_OP_SOP = 6    /* sumOfProd on (p, s) pairs: (p1,s1).(p2,s2) = (p1+p2+s1*s2, s1+s2),
+    ADC_OP_SOP = 6,   /* sumOfProd on (p, s) pairs: (p1,s1).(p2,s2) = (p1+p2+s1*s2, s1+s2),
                          associative, commutative and invertible (Sec. 3.3); reduce and
                          reduce_by_index only                                              */
+    ADC_OP_MM3 = 7,   /* 3x3 matrix product, row-major (9 elements); reduce and scan      */
+    ADC_OP_MM5 = 8    /* 5x5 matrix product, row-major (25 elements); reduce and scan     */
 } adc_op;
 
 typedef enum { ADC_F32 = 0, ADC_F64 = 1 } adc_dtype;
@@ -98,10 +100,10 @@ size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int
  *                   index among equal values, n if none     (Sec. 3.2.2)
  *           MUL -- int32 n0 (number of zeros) then one scalar y>0, the product
  *                  of the non-zeros (Fig. 3's lifted primal)
- *           LIN/MM2 -- per-tile exclusive prefix and suffix partials used by
- *                  the general rule (Fig. 2)
+ *           LIN/MM2/MM3/MM5 -- per-tile exclusive prefix and suffix partials used
+ *                  by the general rule (Fig. 2)
  *           SOP -- unused (the invertible-operator rule needs only x and y)
- *   ops: ADD, MUL, MIN, MAX, LIN, MM2, SOP.  MIN/MAX need n < 2^31.
+ *   ops: ADD, MUL, MIN, MAX, LIN, MM2, MM3, MM5, SOP.  MIN/MAX need n < 2^31.
  */
 adc_status adc_reduce_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
                           void *saved, void *ws, size_t ws_bytes, void *stream);
@@ -113,6 +115,7 @@ adc_status adc_reduce_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, 
  *   MUL     : three-case rule of Fig. 3 (division by x_i when there is no zero)
  *   LIN/MM2 : xbar_i = d(l_i . x_i . r_i)/dx_i ybar with l_i, r_i the exclusive
  *             prefix / suffix (Eq. red-adj, Fig. 2); for MM2 xbar_i = l_i^T ybar r_i^T
+ *   MM3/MM5 : the same rule for 3x3 / 5x5 matrices
  *   SOP     : invertible-operator rule (Sec. 3.3): b_i = y (.)^-1 x_i, then
  *             xbar_i = d(b_i . x)/dx at x_i ybar = (ybar.p, ybar.p * (y.s - x_i.s) + ybar.s);
  *             y is required (the fwd call's output)
@@ -125,7 +128,8 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, 
 
 /* ------------------------------------------------------------------ scan --
  * Inclusive scan y_i = x_0 . x_1 . ... . x_i                      (Sec. 5.1)
- *   x, y : [n] elements.  ops: ADD, MUL, LIN, MM2 (MIN, MAX, SOP: ADC_ERR_UNSUPPORTED).
+ *   x, y : [n] elements.  ops: ADD, MUL, MIN, MAX (running extremum, the
+ *   earlier element wins ties), LIN, MM2, MM3, MM5 (SOP: ADC_ERR_UNSUPPORTED).
  */
 adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
                         void *ws, size_t ws_bytes, void *stream);
@@ -136,7 +140,9 @@ adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, vo
  * c_{i+1} = d(y_i . x_{i+1})/d y_i, solved by one reverse scan of linear-function
  * composition, fused with the map xbar_i = d(y_{i-1} . x_i)/d x_i lambda_i
  * (y_{-1} = e).  The Jacobians are block-diagonal with equal blocks (RBDS,
- * Sec. 5.3.4): a scalar c for ADD/MUL/LIN, M_{i+1}^T for MM2.
+ * Sec. 5.3.4): a scalar c for ADD/MUL/LIN, M_{i+1}^T for MM2/MM3/MM5; for
+ * MIN/MAX the scalar c_{i+1} = [y_i selected] is 0 or 1 and
+ * xbar_i = [x_i selected] lambda_i (the general arity-1 rule).
  *   x, y : the fwd call's input and output; ybar, xbar : [n] elements.
  */
 adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, const void *y,
@@ -186,7 +192,7 @@ adc_status adc_scan_fwd_noalloc(adc_op op, adc_dtype dtype, int64_t n, const voi
  *                   sorted keys and the sorted values (general rule, Fig. 4)
  *   ops: ADD, MUL, MIN, MAX, LIN, SOP (LIN is not commutative: the fold follows
  *   the index order within each bin, computed through a stable sort).  MM2 is
- *   ADC_ERR_UNSUPPORTED.  Requires 1 <= m < 2^31 and n < 2^31.
+ *   ADC_ERR_UNSUPPORTED, and so are MM3 and MM5.  Requires 1 <= m < 2^31 and n < 2^31.
  *   ADD and SOP keep no residuals (saved may be NULL).
  *   saved == NULL (MUL, MIN, MAX only) computes the ORIGINAL, un-lifted primal
  *   instead -- the plain product per bin with zeros included, or the plain

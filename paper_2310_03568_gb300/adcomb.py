@@ -21,8 +21,8 @@ import torch
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libadcomb.so")
 
-OPS = {"add": 0, "mul": 1, "min": 2, "max": 3, "lin": 4, "mm2": 5, "sop": 6}
-ARITY = {"add": 1, "mul": 1, "min": 1, "max": 1, "lin": 2, "mm2": 4, "sop": 2}
+OPS = {"add": 0, "mul": 1, "min": 2, "max": 3, "lin": 4, "mm2": 5, "sop": 6, "mm3": 7, "mm5": 8}
+ARITY = {"add": 1, "mul": 1, "min": 1, "max": 1, "lin": 2, "mm2": 4, "sop": 2, "mm3": 9, "mm5": 25}
 DTYPES = {torch.float32: 0, torch.float64: 1}
 KIND = {"reduce": 0, "scan": 1, "hist": 2}
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "workspace too small", 4: "CUDA error",

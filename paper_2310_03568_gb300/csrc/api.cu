@@ -42,10 +42,11 @@ using namespace adc;
 
 namespace {
 
-bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_SOP; }
-// Operators a scan can take (min/max are reduce-only rules; sumOfProd's
-// invertible rule is a reduce / reduce_by_index rule).
-bool scan_op(adc_op op) { return op == ADC_OP_ADD || op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2; }
+bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_MM5; }
+bool matrix_op(adc_op op) { return op == ADC_OP_MM2 || op == ADC_OP_MM3 || op == ADC_OP_MM5; }
+// Operators a scan can take (sumOfProd's invertible rule is a reduce /
+// reduce_by_index rule).
+bool scan_op(adc_op op) { return op != ADC_OP_SOP && valid_op(op); }
 bool valid_dt(adc_dtype dt) { return dt == ADC_F32 || dt == ADC_F64; }
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 
@@ -91,7 +92,7 @@ size_t adc_workspace_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, in
         if (!scan_op(op)) return 0;
         return scan_ws_bytes(op, dt, n);
     case ADC_HIST:
-        if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
+        if (matrix_op(op) || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
         return hist_ws_bytes(op, dt, n, m);
     default: return 0;
     }
@@ -103,7 +104,7 @@ size_t adc_saved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_
     case ADC_REDUCE: return reduce_saved_bytes(op, dt, n);
     case ADC_SCAN: return scan_op(op) ? 16 : 0;  // scans keep no residuals beyond x and y
     case ADC_HIST:
-        if (op == ADC_OP_MM2 || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
+        if (matrix_op(op) || m < 1 || m > kIdxMax || n > kIdxMax) return 0;
         return hist_saved_bytes(op, dt, n, m);
     default: return 0;
     }
@@ -126,7 +127,7 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, con
     if (!valid_op(op) || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && n >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(xbar, n) || !one_ok(ybar, dt)) return ADC_ERR_INVALID_ARG;
-    if ((op == ADC_OP_MUL || op == ADC_OP_LIN || op == ADC_OP_MM2 || op == ADC_OP_SOP) && !arr_ok(x, n))
+    if ((op == ADC_OP_MUL || op == ADC_OP_LIN || matrix_op(op) || op == ADC_OP_SOP) && !arr_ok(x, n))
         return ADC_ERR_INVALID_ARG;
     if (op == ADC_OP_SOP && !one_ok(y, dt)) return ADC_ERR_INVALID_ARG;
     if (op != ADC_OP_ADD && op != ADC_OP_SOP && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
@@ -162,7 +163,7 @@ adc_status adc_scan_vjp(adc_op op, adc_dtype dt, int64_t n, const void *x, const
 adc_status adc_hist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
                         const void *hist0, void *hist, void *saved, void *ws, size_t ws_bytes, void *stream) {
     if (!valid_op(op) || !valid_dt(dt) || n < 0 || m < 1) return ADC_ERR_INVALID_ARG;
-    if (op == ADC_OP_MM2) return ADC_ERR_UNSUPPORTED;
+    if (matrix_op(op)) return ADC_ERR_UNSUPPORTED;
     if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(keys, n) || !arr_ok(vals, n) || !arr_ok(hist, m)) return ADC_ERR_INVALID_ARG;
     if (hist0 != nullptr && !aligned(hist0, 16)) return ADC_ERR_INVALID_ARG;
@@ -179,7 +180,7 @@ adc_status adc_hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int
                         const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
                         void *hist0bar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
     if (!valid_op(op) || !valid_dt(dt) || n < 0 || m < 1) return ADC_ERR_INVALID_ARG;
-    if (op == ADC_OP_MM2) return ADC_ERR_UNSUPPORTED;
+    if (matrix_op(op)) return ADC_ERR_UNSUPPORTED;
     if (n >= kIdxMax || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
     if (!arr_ok(histbar, m) || !arr_ok(valsbar, n)) return ADC_ERR_INVALID_ARG;
     if (op != ADC_OP_LIN && !arr_ok(keys, n)) return ADC_ERR_INVALID_ARG;

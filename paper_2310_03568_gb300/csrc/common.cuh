@@ -73,6 +73,48 @@ template <typename T> __device__ __forceinline__ Mat2<T> mat_t(const Mat2<T> &x)
 template <typename T> __device__ __forceinline__ Mat2<T> mat_eye() { return {T(1), T(0), T(0), T(1)}; }
 template <typename T> __device__ __forceinline__ Mat2<T> mat_zero() { return {T(0), T(0), T(0), T(0)}; }
 
+// Q x Q row-major matrices (the q = 3, 5 matrix-product operators).
+template <typename T, int Q> struct MatQ { T a[Q * Q]; };
+template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_mul(const MatQ<T, Q> &x, const MatQ<T, Q> &y) {
+    MatQ<T, Q> z;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            T s = x.a[Q * i] * y.a[j];
+#pragma unroll
+            for (int k = 1; k < Q; ++k) s += x.a[Q * i + k] * y.a[Q * k + j];
+            z.a[Q * i + j] = s;
+        }
+    return z;
+}
+template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_add(const MatQ<T, Q> &x, const MatQ<T, Q> &y) {
+    MatQ<T, Q> z;
+#pragma unroll
+    for (int i = 0; i < Q * Q; ++i) z.a[i] = x.a[i] + y.a[i];
+    return z;
+}
+template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_t(const MatQ<T, Q> &x) {
+    MatQ<T, Q> z;
+#pragma unroll
+    for (int i = 0; i < Q; ++i)
+#pragma unroll
+        for (int j = 0; j < Q; ++j) z.a[Q * i + j] = x.a[Q * j + i];
+    return z;
+}
+template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_eye() {
+    MatQ<T, Q> z;
+#pragma unroll
+    for (int i = 0; i < Q * Q; ++i) z.a[i] = (i % (Q + 1) == 0) ? T(1) : T(0);
+    return z;
+}
+template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_zero() {
+    MatQ<T, Q> z;
+#pragma unroll
+    for (int i = 0; i < Q * Q; ++i) z.a[i] = T(0);
+    return z;
+}
+
 // --------------------------------------------------- L2-coherent state I/O --
 // Look-back states are plain structs of T; they are read with ld.global.cg
 // (L2, bypassing the non-coherent L1) after an acquire load of the flag.

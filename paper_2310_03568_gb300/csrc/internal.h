@@ -27,7 +27,16 @@ int num_sms();
 // Returns ADC_ERR_CUDA if the last launch failed.
 adc_status check_launch();
 
-inline int arity(adc_op op) { return (op == ADC_OP_LIN || op == ADC_OP_SOP) ? 2 : (op == ADC_OP_MM2 ? 4 : 1); }
+inline int arity(adc_op op) {
+    switch (op) {
+    case ADC_OP_LIN:
+    case ADC_OP_SOP: return 2;
+    case ADC_OP_MM2: return 4;
+    case ADC_OP_MM3: return 9;
+    case ADC_OP_MM5: return 25;
+    default: return 1;
+    }
+}
 inline size_t elem_bytes(adc_op op, adc_dtype dt) { return (size_t)arity(op) * (dt == ADC_F64 ? 8 : 4); }
 
 // scan.cu

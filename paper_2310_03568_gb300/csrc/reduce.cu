@@ -80,6 +80,11 @@ template <typename T> struct GMM2 {
     __device__ State identity() const { return mat_eye<T>(); }
     __device__ State combine(const State &a, const State &b) const { return mat_mul(a, b); }
 };
+template <typename T, int Q> struct GMMQ {
+    using State = MatQ<T, Q>;
+    __device__ State identity() const { return matq_eye<T, Q>(); }
+    __device__ State combine(const State &a, const State &b) const { return matq_mul(a, b); }
+};
 
 // ------------------------------------------------------- simple reduction --
 // Workspace: [header][ticket u32 @ +8 in header][partials G states]
@@ -228,6 +233,10 @@ template <typename T> __device__ __forceinline__ Pair<T> general_adj(const Pair<
 }
 template <typename T> __device__ __forceinline__ Mat2<T> general_adj(const Mat2<T> &l, const Mat2<T> &r, const Mat2<T> &yb) {
     return mat_mul(mat_mul(mat_t(l), yb), mat_t(r));  // L^T Ybar R^T
+}
+template <typename T, int Q>
+__device__ __forceinline__ MatQ<T, Q> general_adj(const MatQ<T, Q> &l, const MatQ<T, Q> &r, const MatQ<T, Q> &yb) {
+    return matq_mul(matq_mul(matq_t(l), yb), matq_t(r));  // L^T Ybar R^T
 }
 
 template <class Op, typename T, int ITEMS>
@@ -385,7 +394,13 @@ template <typename T> struct RedItems {
     static constexpr int scalar = 64 / sizeof(T);
     static constexpr int pair = 64 / (2 * sizeof(T));  // 16 KB tiles of (b, c) pairs
     static constexpr int mat = 64 / (4 * sizeof(T));   // 16 KB tiles of 2x2 matrices
+    static constexpr int mat3 = sizeof(T) == 4 ? 4 : 2; // 144-byte chunks of 3x3 matrices
+    static constexpr int mat5 = 1;
 };
+
+static bool is_general(adc_op op) {
+    return op == ADC_OP_LIN || op == ADC_OP_MM2 || op == ADC_OP_MM3 || op == ADC_OP_MM5;
+}
 
 static int64_t simple_grid(int64_t tiles) {
     int64_t g = (int64_t)num_sms() * 4;
@@ -393,9 +408,20 @@ static int64_t simple_grid(int64_t tiles) {
     return g < 1 ? 1 : g;
 }
 
-template <typename T> static size_t general_state_bytes(adc_op op) { return op == ADC_OP_LIN ? sizeof(Pair<T>) : sizeof(Mat2<T>); }
+template <typename T> static size_t general_state_bytes(adc_op op) {
+    switch (op) {
+    case ADC_OP_LIN: return sizeof(Pair<T>);
+    case ADC_OP_MM3: return sizeof(MatQ<T, 3>);
+    case ADC_OP_MM5: return sizeof(MatQ<T, 5>);
+    default: return sizeof(Mat2<T>);
+    }
+}
 template <typename T> static int64_t general_tiles(adc_op op, int64_t n) {
-    const int tile = kRedThreads * (op == ADC_OP_LIN ? RedItems<T>::pair : RedItems<T>::mat);
+    int items = RedItems<T>::mat;
+    if (op == ADC_OP_LIN) items = RedItems<T>::pair;
+    if (op == ADC_OP_MM3) items = RedItems<T>::mat3;
+    if (op == ADC_OP_MM5) items = RedItems<T>::mat5;
+    const int tile = kRedThreads * items;
     return (n + tile - 1) / tile;
 }
 
@@ -429,9 +455,14 @@ static adc_status general_fwd(int64_t n, const void *xv, void *yv, void *saved, 
 }
 
 template <typename T> static size_t red_ws_t(adc_op op, int64_t n) {
-    if (op == ADC_OP_LIN || op == ADC_OP_MM2) {
+    if (is_general(op)) {
         const int64_t tiles = general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1;
-        return op == ADC_OP_LIN ? general_ws<GLin<T>>(tiles) : general_ws<GMM2<T>>(tiles);
+        switch (op) {
+        case ADC_OP_LIN: return general_ws<GLin<T>>(tiles);
+        case ADC_OP_MM3: return general_ws<GMMQ<T, 3>>(tiles);
+        case ADC_OP_MM5: return general_ws<GMMQ<T, 5>>(tiles);
+        default: return general_ws<GMM2<T>>(tiles);
+        }
     }
     const int items = op == ADC_OP_SOP ? RedItems<T>::pair : RedItems<T>::scalar;
     const int64_t tiles = (n + kRedThreads * items - 1) / (kRedThreads * items);
@@ -439,7 +470,7 @@ template <typename T> static size_t red_ws_t(adc_op op, int64_t n) {
 }
 
 size_t reduce_ws_bytes(adc_op op, adc_dtype dt, int64_t n) {
-    if (op > ADC_OP_SOP || op < ADC_OP_ADD) return 0;
+    if (op > ADC_OP_MM5 || op < ADC_OP_ADD) return 0;
     return dt == ADC_F64 ? red_ws_t<double>(op, n) : red_ws_t<float>(op, n);
 }
 
@@ -451,7 +482,9 @@ template <typename T> static size_t red_saved_t(adc_op op, int64_t n) {
     case ADC_OP_MUL: return 16;
     case ADC_OP_SOP: return 16;
     case ADC_OP_LIN:
-    case ADC_OP_MM2: return 2 * (size_t)(general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1) * general_state_bytes<T>(op);
+    case ADC_OP_MM2:
+    case ADC_OP_MM3:
+    case ADC_OP_MM5: return 2 * (size_t)(general_tiles<T>(op, n) > 0 ? general_tiles<T>(op, n) : 1) * general_state_bytes<T>(op);
     default: return 0;
     }
 }
@@ -523,6 +556,10 @@ static adc_status red_fwd_t(adc_op op, int64_t n, const void *xv, void *yv, void
         return general_fwd<GLin<T>, T, RedItems<T>::pair>(n, xv, yv, saved, ws, s);
     case ADC_OP_MM2:
         return general_fwd<GMM2<T>, T, RedItems<T>::mat>(n, xv, yv, saved, ws, s);
+    case ADC_OP_MM3:
+        return general_fwd<GMMQ<T, 3>, T, RedItems<T>::mat3>(n, xv, yv, saved, ws, s);
+    case ADC_OP_MM5:
+        return general_fwd<GMMQ<T, 5>, T, RedItems<T>::mat5>(n, xv, yv, saved, ws, s);
     default: return ADC_ERR_UNSUPPORTED;
     }
 }
@@ -586,6 +623,26 @@ static adc_status red_vjp_t(adc_op op, int64_t n, const void *xv, const void *yv
                 GMM2<T>{}, static_cast<const S *>(xv), n, reinterpret_cast<const S *>(sv),
                 reinterpret_cast<const S *>(sv + Tn * sb), static_cast<const S *>(ybar), static_cast<S *>(xbar), acc);
         }
+        return check_launch();
+    }
+    case ADC_OP_MM3: {
+        using S = MatQ<T, 3>;
+        const int64_t Tn = general_tiles<T>(op, n);
+        const char *sv = static_cast<const char *>(saved);
+        k_reduce_general_vjp<GMMQ<T, 3>, T, RedItems<T>::mat3><<<(unsigned)Tn, kRedThreads, 0, s>>>(
+            GMMQ<T, 3>{}, static_cast<const S *>(xv), n, reinterpret_cast<const S *>(sv),
+            reinterpret_cast<const S *>(sv + Tn * sizeof(S)), static_cast<const S *>(ybar), static_cast<S *>(xbar),
+            acc);
+        return check_launch();
+    }
+    case ADC_OP_MM5: {
+        using S = MatQ<T, 5>;
+        const int64_t Tn = general_tiles<T>(op, n);
+        const char *sv = static_cast<const char *>(saved);
+        k_reduce_general_vjp<GMMQ<T, 5>, T, RedItems<T>::mat5><<<(unsigned)Tn, kRedThreads, 0, s>>>(
+            GMMQ<T, 5>{}, static_cast<const S *>(xv), n, reinterpret_cast<const S *>(sv),
+            reinterpret_cast<const S *>(sv + Tn * sizeof(S)), static_cast<const S *>(ybar), static_cast<S *>(xbar),
+            acc);
         return check_launch();
     }
     default: return ADC_ERR_UNSUPPORTED;

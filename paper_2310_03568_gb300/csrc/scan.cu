@@ -95,6 +95,13 @@ template <typename T, int ITEMS> struct FwdMul : PlainScan<T, ITEMS, FwdMul<T, I
     __device__ T combine(T a, T b) const { return a * b; }
 };
 
+// min / max scans: the running extremum; the earlier operand wins ties (the
+// lifted operator of Fig. 5 with the lowest index first).
+template <typename T, int ITEMS, bool MAX> struct FwdSel : PlainScan<T, ITEMS, FwdSel<T, ITEMS, MAX>> {
+    __device__ T identity() const { return MAX ? -Num<T>::inf() : Num<T>::inf(); }
+    __device__ T combine(T a, T b) const { return (MAX ? (b > a) : (b < a)) ? b : a; }
+};
+
 // linFnComp (Fig. 8): (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)
 template <typename T, int ITEMS> struct FwdLin : PlainScan<Pair<T>, ITEMS, FwdLin<T, ITEMS>> {
     __device__ Pair<T> identity() const { return {T(0), T(1)}; }
@@ -188,6 +195,56 @@ template <typename T, int ITEMS> struct VjpMul {
         if (accumulate) load_chunk(xbar, c0, n, out, T(0));
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) out[k] = (accumulate ? out[k] : T(0)) + aux.yprev[k] * st[k].v;
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
+// min / max scan (the general rule of Fig. 7 with a scalar Jacobian): the step
+// y_{i+1} = y_i . x_{i+1} has d/dy_i = c_{i+1} = [y_i selected] and
+// d/dx_{i+1} = 1 - c_{i+1}, so lambda_i = ybar_i + c_{i+1} lambda_{i+1} and
+// xbar_i = [x_i selected at step i] lambda_i (x_0 always is).
+template <typename T, int ITEMS, bool MAX> struct VjpSel {
+    using State = AffS<T>;
+    using Raw = VjpRaw<T, ITEMS>;
+    struct Aux { T sel[ITEMS]; };
+    const T *x, *y, *ybar;
+    T *xbar;
+    int accumulate;
+    static __device__ __forceinline__ bool beats(T a, T b) { return MAX ? (a > b) : (a < b); }
+    __device__ State identity() const { return {T(0), T(1)}; }
+    __device__ State combine(const State &acc, const State &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(ybar, c0, n, r.yb.v, T(0));
+        fetch_next(x, c0, n, r.x, T(0));
+        fetch_prev(y, c0, n, r.y, T(0));
+    }
+    static constexpr int kStreams = 3;
+    using Elem = T;
+    __device__ const T *stream(int s) const { return s == 0 ? ybar : (s == 1 ? x : y); }
+    __device__ void fetch_staged(const T *const (&sm)[3], int64_t lo, int64_t c0, int64_t n, Raw &r) const {
+        load_chunk_sm(sm[0] + lo, c0, n, r.yb.v, T(0));
+        fetch_next_sm(sm[1], lo, c0, n, r.x, T(0));
+        fetch_prev_sm(sm[2], lo, c0, n, r.y, T(0));
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const int64_t i = c0 + k;
+            // y_i is this element's own scan value: the y chunk is the y array at c0
+            const T yi = r.y.v[k];
+            aux.sel[k] = (i == 0 || beats(r.x.v[k], prev_of(r.y, k))) ? T(1) : T(0);
+            const T c = (i + 1 < n && beats(next_of(r.x, k), yi)) ? T(0) : T(1);
+            st[k] = (i < n) ? State{r.yb.v[k], c} : identity();
+        }
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        T out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, T(0));
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const T g = aux.sel[k] * st[k].v;
+            out[k] = accumulate ? out[k] + g : g;
+        }
         store_chunk(xbar, c0, n, out);
     }
 };
@@ -287,6 +344,53 @@ template <typename T, int ITEMS> struct VjpMM2 {
     }
 };
 
+// q x q matrix-product scans (q = 3, 5): the same forward, and the vjp with
+// the RBDS Jacobian M_{i+1}^T (Sec. 5.3.4 for q > 2): f_i(L) = Ybar_i + L M_{i+1}^T,
+// Mbar_i = P_{i-1}^T lambda_i.
+template <typename T, int Q, int ITEMS>
+struct FwdMMQ : PlainScan<MatQ<T, Q>, ITEMS, FwdMMQ<T, Q, ITEMS>> {
+    __device__ MatQ<T, Q> identity() const { return matq_eye<T, Q>(); }
+    __device__ MatQ<T, Q> combine(const MatQ<T, Q> &a, const MatQ<T, Q> &b) const { return matq_mul(a, b); }
+};
+
+template <typename T, int Q> struct AffQ { MatQ<T, Q> v, c; };
+
+template <typename T, int Q, int ITEMS> struct VjpMMQ {
+    using E = MatQ<T, Q>;
+    using State = AffQ<T, Q>;
+    using Raw = VjpRaw<E, ITEMS>;
+    struct Aux { E yprev[ITEMS]; };
+    const E *x, *y, *ybar;
+    E *xbar;
+    int accumulate;
+    __device__ State identity() const { return {matq_zero<T, Q>(), matq_eye<T, Q>()}; }
+    __device__ State combine(const State &acc, const State &e) const {
+        return {matq_add(e.v, matq_mul(acc.v, e.c)), matq_mul(acc.c, e.c)};
+    }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        load_chunk(ybar, c0, n, r.yb.v, matq_zero<T, Q>());
+        fetch_next(x, c0, n, r.x, matq_eye<T, Q>());
+        fetch_prev(y, c0, n, r.y, matq_eye<T, Q>());
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            aux.yprev[k] = prev_of(r.y, k);
+            st[k] = (c0 + k < n) ? State{r.yb.v[k], matq_t(next_of(r.x, k))} : identity();
+        }
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        E out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, matq_zero<T, Q>());
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const E g = matq_mul(matq_t(aux.yprev[k]), st[k].v);
+            out[k] = accumulate ? matq_add(out[k], g) : g;
+        }
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
 // -------------------------------------------------------------- launching --
 // Items per thread: 64 bytes of each streamed array per thread (32 for the
 // three-array vjps), so a tile is 16 KB (8 KB) per array.
@@ -301,6 +405,10 @@ template <typename T> struct Items {
     static constexpr int s_scalar = 16 / sizeof(T);
     static constexpr int s_pair = 16 / (2 * sizeof(T)) > 0 ? 16 / (2 * sizeof(T)) : 1;
     static constexpr int s_mat = 1;
+    // q x q matrices: whole 16-byte words per thread where it stays small
+    static constexpr int mat3 = sizeof(T) == 4 ? 4 : 2;  // 144 bytes
+    static constexpr int mat5 = 1;
+    static constexpr int vmatq = 1;
 };
 
 // Staged (TMA) engine: forced by the test hook (3), chosen automatically for
@@ -332,6 +440,19 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
         a = ScanShape<FwdMM2<T, I::mat>, I::mat>::region(n);
         b = ScanShape<VjpMM2<T, I::vmat>, I::vmat>::region(n);
         break;
+    case ADC_OP_MIN:
+    case ADC_OP_MAX:
+        a = ScanShape<FwdSel<T, I::scalar, false>, I::scalar>::region(n);
+        b = ScanShape<VjpSel<T, I::vscalar, false>, I::vscalar>::region(n);
+        return kWsHeader + (a > b ? a : b);
+    case ADC_OP_MM3:
+        a = ScanShape<FwdMMQ<T, 3, I::mat3>, I::mat3>::region(n);
+        b = ScanShape<VjpMMQ<T, 3, I::vmatq>, I::vmatq>::region(n);
+        return kWsHeader + (a > b ? a : b);
+    case ADC_OP_MM5:
+        a = ScanShape<FwdMMQ<T, 5, I::mat5>, I::mat5>::region(n);
+        b = ScanShape<VjpMMQ<T, 5, I::vmatq>, I::vmatq>::region(n);
+        return kWsHeader + (a > b ? a : b);
     default: return 0;
     }
     size_t c = 0, d = 0;
@@ -373,6 +494,30 @@ static adc_status launch_staged(const Op &o, int64_t n, void *ws, cudaStream_t s
 template <typename T>
 static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
     using I = Items<T>;
+    if (op == ADC_OP_MIN || op == ADC_OP_MAX) {
+        if (op == ADC_OP_MAX) {
+            FwdSel<T, I::scalar, true> o;
+            o.x = static_cast<const T *>(x);
+            o.y = static_cast<T *>(y);
+            return launch<decltype(o), I::scalar, false>(o, n, ws, s);
+        }
+        FwdSel<T, I::scalar, false> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::scalar, false>(o, n, ws, s);
+    }
+    if (op == ADC_OP_MM3) {
+        FwdMMQ<T, 3, I::mat3> o;
+        o.x = static_cast<const MatQ<T, 3> *>(x);
+        o.y = static_cast<MatQ<T, 3> *>(y);
+        return launch<decltype(o), I::mat3, false>(o, n, ws, s);
+    }
+    if (op == ADC_OP_MM5) {
+        FwdMMQ<T, 5, I::mat5> o;
+        o.x = static_cast<const MatQ<T, 5> *>(x);
+        o.y = static_cast<MatQ<T, 5> *>(y);
+        return launch<decltype(o), I::mat5, false>(o, n, ws, s);
+    }
     if (use_staged(n, 0)) {
         switch (op) {
         case ADC_OP_ADD: {
@@ -439,6 +584,28 @@ template <typename T>
 static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y, const void *ybar, void *xbar,
                              int acc, void *ws, cudaStream_t s) {
     using I = Items<T>;
+    if (op == ADC_OP_MIN || op == ADC_OP_MAX) {
+        if (op == ADC_OP_MAX) {
+            VjpSel<T, I::vscalar, true> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                          static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+            return launch<decltype(o), I::vscalar, true>(o, n, ws, s);
+        }
+        VjpSel<T, I::vscalar, false> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                       static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return launch<decltype(o), I::vscalar, true>(o, n, ws, s);
+    }
+    if (op == ADC_OP_MM3 || op == ADC_OP_MM5) {
+        if (op == ADC_OP_MM3) {
+            using M = MatQ<T, 3>;
+            VjpMMQ<T, 3, I::vmatq> o{static_cast<const M *>(x), static_cast<const M *>(y), static_cast<const M *>(ybar),
+                                     static_cast<M *>(xbar), acc};
+            return launch<decltype(o), I::vmatq, true>(o, n, ws, s);
+        }
+        using M = MatQ<T, 5>;
+        VjpMMQ<T, 5, I::vmatq> o{static_cast<const M *>(x), static_cast<const M *>(y), static_cast<const M *>(ybar),
+                                 static_cast<M *>(xbar), acc};
+        return launch<decltype(o), I::vmatq, true>(o, n, ws, s);
+    }
     if (use_staged(n, 0)) {
         switch (op) {
         case ADC_OP_ADD: {

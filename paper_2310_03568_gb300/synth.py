@@ -110,6 +110,15 @@ def scan_values(g, op, n, dtype=np.float32):
         th = g.uniform(0, 2 * np.pi, n)
         c, s = np.cos(th) * rho, np.sin(th) * rho
         return np.ascontiguousarray(np.stack([c, -s, s, c], axis=1).astype(dtype))
+    if op in ("mm3", "mm5"):
+        q = int(op[2])
+        return (uniform(g, q * q * n, -1.0, 1.0, dtype) / np.asarray(np.sqrt(q), dtype)).astype(dtype).reshape(n, q * q)
+    if op in ("mm3_orth", "mm5_orth"):
+        # near-orthogonal q x q: Q of a Gaussian matrix's QR, times rho ~ U(0.999, 1.001)
+        q = int(op[2])
+        Q, _ = np.linalg.qr(g.standard_normal((n, q, q)))
+        rho = g.uniform(0.999, 1.001, (n, 1, 1))
+        return np.ascontiguousarray((Q * rho).reshape(n, q * q).astype(dtype))
     raise ValueError(op)
 
 

@@ -43,7 +43,7 @@ def test_status_strings(L):
 def test_size_queries(L):
     f32 = 0
     assert L.adc_workspace_bytes(1, 0, f32, 1000, 0) >= 256          # scan +
-    assert L.adc_workspace_bytes(1, 2, f32, 1000, 0) == 0            # scan min: unsupported
+    assert L.adc_workspace_bytes(1, 2, f32, 1000, 0) >= 256          # scan min
     assert L.adc_workspace_bytes(2, 5, f32, 1000, 10) == 0           # hist mm2: unsupported
     assert L.adc_workspace_bytes(2, 0, f32, 1000, 0) == 0            # hist with m = 0
     assert L.adc_saved_bytes(2, 2, f32, 1000, 77) >= 77 * 4          # hist min: is[m]
@@ -54,7 +54,10 @@ def test_size_queries(L):
     assert L.adc_workspace_bytes(1, 6, f32, 1000, 0) == 0            # scan sumOfProd: unsupported
     assert L.adc_workspace_bytes(0, 6, f32, 1000, 0) >= 256          # reduce sumOfProd
     assert L.adc_workspace_bytes(2, 6, f32, 1000, 10) >= 256         # hist sumOfProd
-    assert L.adc_workspace_bytes(0, 7, f32, 1000, 0) == 0            # no operator 7
+    assert L.adc_workspace_bytes(0, 7, f32, 1000, 0) >= 256          # reduce 3x3 matrices
+    assert L.adc_workspace_bytes(1, 8, f32, 1000, 0) >= 256          # scan 5x5 matrices
+    assert L.adc_workspace_bytes(2, 7, f32, 1000, 10) == 0           # hist 3x3: unsupported
+    assert L.adc_workspace_bytes(0, 9, f32, 1000, 0) == 0            # no operator 9
 
 
 def test_host_validation_rejects_before_any_device_work(L):
@@ -62,11 +65,10 @@ def test_host_validation_rejects_before_any_device_work(L):
     ws_small = 8
     # bad enums, negative sizes
     assert L.adc_scan_fwd(9, 0, 10, fake, fake, fake, 1 << 20, None) == 1
-    assert L.adc_scan_fwd(7, 0, 10, fake, fake, fake, 1 << 20, None) == 1
+    assert L.adc_scan_fwd(9, 0, 10, fake, fake, fake, 1 << 20, None) == 1
     assert L.adc_scan_fwd(0, 7, 10, fake, fake, fake, 1 << 20, None) == 1
     assert L.adc_scan_fwd(0, 0, -1, fake, fake, fake, 1 << 20, None) == 1
     # unsupported operator / combinator pairs
-    assert L.adc_scan_fwd(2, 0, 10, fake, fake, fake, 1 << 20, None) == 2
     assert L.adc_scan_fwd(6, 0, 10, fake, fake, fake, 1 << 20, None) == 2   # sumOfProd scan
     assert L.adc_hist_fwd(5, 0, 10, 4, fake, fake, None, fake, fake, fake, 1 << 20, None) == 2
     # null / misaligned arrays

@@ -90,9 +90,10 @@ def test_reduce_mul_zero_counting(dt, zeros):
 
 def suffix_partials(op, x):
     """max |R_i| over the suffix folds, via the oracle on the reversed, transposed sequence."""
-    if op == "mm2":
-        xt = x.reshape(-1, 2, 2).transpose(0, 2, 1).reshape(-1, 4)[::-1]
-        return rowabs(oracle.scan_fwd("mm2", xt)).max(initial=1.0)
+    if op in ("mm2", "mm3", "mm5"):
+        q = {"mm2": 2, "mm3": 3, "mm5": 5}[op]
+        xt = x.reshape(-1, q, q).transpose(0, 2, 1).reshape(-1, q * q)[::-1]
+        return rowabs(oracle.scan_fwd(op, xt)).max(initial=1.0)
     # lin as an exact 2x2 embedding M = [[c, 0], [b, 1]] (row-vector convention)
     m = np.stack([x[:, 1], np.zeros(len(x)), x[:, 0], np.ones(len(x))], 1)
     mt = m.reshape(-1, 2, 2).transpose(0, 2, 1).reshape(-1, 4)[::-1]
@@ -100,13 +101,13 @@ def suffix_partials(op, x):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("op", ["lin", "mm2"])
+@pytest.mark.parametrize("op", ["lin", "mm2", "mm3", "mm5"])
 def test_reduce_general(op, dt):
     g = np.random.default_rng(14)
     rtol = rtol_for(dt)
-    d = 2 if op == "lin" else 4
+    d = {"lin": 2, "mm2": 4, "mm3": 9, "mm5": 25}[op]
     for n in SIZES:
-        x = synth.scan_values(g, "lin" if op == "lin" else "mm2_orth", n, dt).reshape(n, d)
+        x = synth.scan_values(g, "lin" if op == "lin" else op + "_orth", n, dt).reshape(n, d)
         y, saved = adcomb.reduce_fwd(op, dev(x))
         yr = oracle.reduce_fwd(op, x)
         lmax = rowabs(oracle.scan_fwd(op, x)).max(initial=1.0)
@@ -116,7 +117,7 @@ def test_reduce_general(op, dt):
             old = synth.normal(g, (n, d), dt)
             xb = adcomb.reduce_vjp(op, dev(x), y, saved, ybd, xbar=dev(old) if acc else None, accumulate=acc)
             ref = oracle.reduce_vjp(op, x, yb) + (old if acc else 0)
-            M = 4 * lmax * suffix_partials(op, x) * np.abs(yb).max() + (rowabs(old) if acc else 0)
+            M = max(d, 4) * lmax * suffix_partials(op, x) * np.abs(yb).max() + (rowabs(old) if acc else 0)
             assert_tol(f"reduce {op} vjp acc={acc}", host(xb), ref, n, M, rtol)
 
 

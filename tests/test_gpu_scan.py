@@ -12,7 +12,8 @@ pytestmark = pytest.mark.gpu
 
 TILE = {("add", 4): 4096, ("mul", 4): 4096, ("lin", 4): 2048, ("mm2", 4): 1024,
         ("add", 8): 2048, ("mul", 8): 2048, ("lin", 8): 1024, ("mm2", 8): 512}
-IDENT = {"add": [0.0], "mul": [1.0], "lin": [0.0, 1.0], "mm2": [1.0, 0.0, 0.0, 1.0]}
+IDENT = {"add": [0.0], "mul": [1.0], "lin": [0.0, 1.0], "mm2": [1.0, 0.0, 0.0, 1.0],
+         "mm3": list(np.eye(3).reshape(-1)), "mm5": list(np.eye(5).reshape(-1))}
 
 
 def sizes(op, dt):
@@ -21,6 +22,8 @@ def sizes(op, dt):
 
 
 def make_x(g, op, n, dt):
+    if op in ("mm3", "mm5"):
+        return synth.scan_values(g, op + "_orth" if n > 64 else op, n, dt)
     if op == "add":
         return synth.uniform(g, n, -1, 1, dt)
     if op == "mul":
@@ -167,3 +170,50 @@ def test_mm2_scan_full_size(op):
     w = synth.scan_spec(op, n=10_000_000, dtype=np.float32)
     check_scan("mm2", w["x"], w["ybar"], np.float32)
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("engine_id", [0, 1, 2], ids=["auto", "per-tile", "ranges"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("op", ["mm3", "mm5"])
+def test_mmq_scan(op, dt, engine_id):
+    """q x q matrix-product scans (q = 3, 5): forward and the RBDS vjp with
+    M_{i+1}^T, at sizes spanning several tiles (forward tiles of 1024 / 512 /
+    256 matrices, vjp tiles of 256) and ragged tails."""
+    g = np.random.default_rng(31 + len(op))
+    try:
+        adcomb.debug_set_scan_engine(engine_id)
+        for n in [0, 1, 2, 33, 255, 256, 257, 1025, 3 * 1024 + 1, 20_003]:
+            x = make_x(g, op, n, dt)
+            check_scan(op, x, synth.normal(g, x.shape, dt), dt)
+        x = make_x(g, op, 3001, dt)
+        check_scan(op, x, synth.normal(g, x.shape, dt), dt, accumulate=True)
+    finally:
+        adcomb.debug_set_scan_engine(0)
+
+
+@pytest.mark.parametrize("engine_id", [1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_scan(op, dt, engine_id):
+    """Running min / max (the earlier element wins ties) and its vjp by the
+    general arity-1 rule: forward and the selection are bit-exact; the adjoint
+    sums ybar over the outputs each element is selected for (a subset of a
+    suffix: nj = suffix length, M = largest |ybar| in it)."""
+    g = np.random.default_rng(41 + len(op))
+    rtol = rtol_for(dt)
+    try:
+        adcomb.debug_set_scan_engine(engine_id)
+        for n in sizes("add", dt) + [1_000_003]:
+            x = ((g.integers(0, 64, n) - 32) / 8.0).astype(dt)  # 64 levels: ties everywhere
+            yb = synth.normal(g, n, dt)
+            xd = dev(x)
+            y = adcomb.scan_fwd(op, xd)
+            assert np.array_equal(host(y), oracle.scan_fwd(op, x).astype(dt))
+            for acc in (False, True):
+                old = synth.normal(g, n, dt)
+                xb = adcomb.scan_vjp(op, xd, y, dev(yb), xbar=dev(old) if acc else None, accumulate=acc)
+                ref = oracle.scan_vjp(op, x, yb) + (old if acc else 0)
+                assert_tol(f"scan {op} vjp", host(xb), ref, n - np.arange(n),
+                           suffix_max(yb) + (np.abs(old) if acc else 0), rtol)
+    finally:
+        adcomb.debug_set_scan_engine(0)
