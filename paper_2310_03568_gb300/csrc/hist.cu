@@ -6,6 +6,9 @@
 //               the global result -- for histograms of up to a few KB.
 //   SMEM_BLOCK: one sub-histogram per 1024-thread block filling most of the
 //               SM's shared memory -- for histograms up to ~200 KB.
+//   SPLIT     : lifted min/max tables of 2-4 block tables: S blocks read the
+//               same elements, each owns 1/S of the bins in its shared
+//               memory, then flushes them (filtered global atomics).
 //   PART      : for tables beyond shared memory: the elements are first
 //               partitioned by bin range so that every range's bins fit one
 //               block's shared memory (hist_part.cu) -- no global atomics.
@@ -33,7 +36,7 @@
 
 namespace adc {
 
-enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4 };
+enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4, kSplit = 5 };
 
 // ------------------------------------------------------------ element loop --
 // Calls f(key, value, index) for every element, grid-stride over 4-element
@@ -210,6 +213,41 @@ __global__ void k_hist_sel_global(const int32_t *__restrict__ keys, const float 
             }
         }
     });
+}
+
+// SPLIT: blocks come in groups of S that read the same elements; block p of a
+// group keeps bins [p*W, (p+1)*W) in shared memory and skips the others.
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_hist_sel_split(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                 const int S, const int64_t W, unsigned long long *__restrict__ tab) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *sh = reinterpret_cast<unsigned long long *>(smem_raw);
+    const int64_t group = blockIdx.x / S, groups = gridDim.x / S;
+    const int64_t lo = (int64_t)(blockIdx.x % S) * W;
+    const int64_t w = (m - lo) < W ? (m - lo) : W;
+    for (int64_t j = threadIdx.x; j < w; j += blockDim.x) sh[j] = Pack<MAX>::kEmpty;
+    __syncthreads();
+    // the element loop of for_each_elem over the group's virtual grid
+    const int64_t gtid = group * blockDim.x + threadIdx.x, stride = groups * blockDim.x;
+    const int64_t nv = n / 4;
+    auto upd = [&](int32_t k, float v, int64_t i) {
+        const int64_t b = (int64_t)k - lo;
+        if (in_range(k, m) && b >= 0 && b < w) Pack<MAX>::update_smem(sh + b, Pack<MAX>::key(v, i));
+    };
+    for (int64_t v = gtid; v < nv; v += stride) {
+        const int4 k4 = __ldcg(reinterpret_cast<const int4 *>(keys) + v);
+        float a[4];
+        load_chunk(vals, v * 4, n, a, 0.f);
+        upd(k4.x, a[0], 4 * v);
+        upd(k4.y, a[1], 4 * v + 1);
+        upd(k4.z, a[2], 4 * v + 2);
+        upd(k4.w, a[3], 4 * v + 3);
+    }
+    for (int64_t i = nv * 4 + gtid; i < n; i += stride) upd(keys[i], vals[i], i);
+    __syncthreads();
+    for (int64_t j = threadIdx.x; j < w; j += blockDim.x)
+        if (sh[j] != Pack<MAX>::kEmpty) Pack<MAX>::update(tab + lo + j, sh[j]);
 }
 
 // Decode the packed table, fold hist0 in (it wins ties), write hist and is.
@@ -780,6 +818,9 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
     case kSmemThread: return (size_t)m * e * kThrThreads <= kThrBudget;
     case kSmemWarp: return (size_t)m * e * 8 <= kWarpBudget;
     case kSmemBlock: return (size_t)m * e <= kBlockBudget;
+    case kSplit:
+        return (op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 4 && (size_t)m * 8 > kBlockBudget &&
+               (size_t)m * 8 <= 4 * kBlockBudget;
     default: return true;
     }
 }
@@ -788,12 +829,14 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
 // always uses the two global phases.
 static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
-    if (g_force_strategy >= 0 && g_force_strategy <= 4 && fits(op, s, (HistStrategy)g_force_strategy, m))
+    if (g_force_strategy >= 0 && g_force_strategy <= 5 && fits(op, s, (HistStrategy)g_force_strategy, m))
         return (HistStrategy)g_force_strategy;
     // min/max updates are rare after the first few values of a bin (a read
     // filters them), so per-warp copies beat per-thread tables there: the
     // latter's larger footprint costs occupancy.
     const bool select = op == ADC_OP_MIN || op == ADC_OP_MAX;
+    // (SPLIT is not chosen automatically: at m = 50,000 it measured no faster
+    // than the filtered global atomics.)
     for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
         if (!(select && st == kSmemThread) && fits(op, s, st, m)) return st;
     if (m >= kPartMinBins && fits(op, s, kPart, m)) return kPart;
@@ -1012,6 +1055,14 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
                 if (st == kGlobal) {
                     if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
                     else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
+                } else if (st == kSplit) {
+                    const int S = (int)(((size_t)m * 8 + kBlockBudget - 1) / kBlockBudget);
+                    const int64_t W = (m + S - 1) / S;
+                    const size_t smem = (size_t)W * 8;
+                    auto kern = mx ? k_hist_sel_split<true> : k_hist_sel_split<false>;
+                    if (!set_smem(kern, smem)) return ADC_ERR_CUDA;
+                    const int groups = num_sms() / S > 0 ? num_sms() / S : 1;
+                    kern<<<(unsigned)(groups * S), 1024, smem, s>>>(keys, vals, n, m, S, W, tab);
                 } else if (st == kSmemThread) {
                     auto kern = mx ? k_hist_sel_thread<true> : k_hist_sel_thread<false>;
                     if (!set_smem(kern, L.smem)) return ADC_ERR_CUDA;

@@ -56,7 +56,7 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2, 3, 4]  # auto, per-warp, per-block, global, per-thread, partitioned by bin range
+STRATS = [-1, 0, 1, 2, 3, 4, 5]  # auto, per-warp, per-block, global, per-thread, partitioned, split tables
 
 
 def fits(op, dt, m, s):
@@ -67,6 +67,8 @@ def fits(op, dt, m, s):
         return s in (-1, 2)
     if s == 4:
         return True
+    if s == 5:  # lifted fp32 min/max whose packed table needs 2-4 block tables
+        return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 4 * 200 * 1024
     e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
     if s == 3:
         return m * e * 256 <= 64 * 1024
