@@ -294,6 +294,50 @@ adc_status adc_batched_hist_scan_vjp(const adc_instance *desc, int32_t count, co
  * Waits for `stream`, reads the workspace's device error word and returns
  * ADC_OK or the recorded error (ADC_ERR_TIMEOUT).  This call synchronises.
  */
+/* ----------------------------------------------------- vectorised operators --
+ * reduce, scan and reduce_by_index whose operator is map2 (.) over rows of d
+ * elements, (.) in ADD, MUL, MIN, MAX (Sec. 3.2 "Vectorized Operators": the
+ * Irwim rule; Sec. 5.3: the Iswim rule; the same interchange for
+ * reduce_by_index).  Computed as the rules rewrite them: the [n][d] operands
+ * are transposed to [d][n], each column runs through the scalar entry point's
+ * kernels (so each column follows that operator's specialised rule: zero
+ * counting, lowest-index argmin, ...), and [n][d] / [m][d] results are
+ * transposed back.  Arrays are row-major and 16-byte aligned; 1 <= d <= 64.
+ *   vreduce : x [n][d] -> y [d]; saved = d column residuals (adc_vsaved_bytes)
+ *   vscan   : x [n][d] -> y [n][d]; vjp reads x, y (not for ADD) and ybar [n][d]
+ *   vhist   : keys [n], vals [n][d], hist0 [m][d] or NULL -> hist [m][d];
+ *             saved == NULL computes the original primal (MUL, MIN, MAX)
+ * The workspace holds the transposed planes and one scalar workspace per
+ * column (adc_vworkspace_bytes); a timeout in any column is reported by
+ * adc_check_device_error on this workspace.  Other operators:
+ * ADC_ERR_UNSUPPORTED.
+ */
+size_t adc_vworkspace_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d);
+size_t adc_vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d);
+adc_status adc_vreduce_fwd(adc_op op, adc_dtype dtype, int64_t n, int64_t d, const void *x, void *y, void *saved,
+                           void *ws, size_t ws_bytes, void *stream);
+adc_status adc_vreduce_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t d, const void *x, const void *y,
+                           const void *saved, const void *ybar, void *xbar, int accumulate, void *ws,
+                           size_t ws_bytes, void *stream);
+adc_status adc_vscan_fwd(adc_op op, adc_dtype dtype, int64_t n, int64_t d, const void *x, void *y, void *ws,
+                         size_t ws_bytes, void *stream);
+adc_status adc_vscan_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t d, const void *x, const void *y,
+                         const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream);
+adc_status adc_vhist_fwd(adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d, const int32_t *keys,
+                         const void *vals, const void *hist0, void *hist, void *saved, void *ws, size_t ws_bytes,
+                         void *stream);
+adc_status adc_vhist_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d, const int32_t *keys,
+                         const void *vals, const void *hist0, const void *hist, const void *saved,
+                         const void *histbar, void *valsbar, void *hist0bar, int accumulate, void *ws,
+                         size_t ws_bytes, void *stream);
+
+/*
+ * dst = transpose(src) for a rows x cols row-major matrix of dtype elements
+ * (the layout change of the rewrites above), through shared-memory tiles.
+ * src and dst must not overlap.  Asynchronous on the stream.
+ */
+adc_status adc_transpose(adc_dtype dtype, int64_t rows, int64_t cols, const void *src, void *dst, void *stream);
+
 adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream);
 
 /*

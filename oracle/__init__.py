@@ -245,3 +245,48 @@ def sort_perm(m, keys):
     perm = np.zeros(max(k.shape[0], 1), dtype=np.int64)
     _load().oracle_sort_perm(k.shape[0], m, _p(k), _p(perm))
     return perm[: k.shape[0]]
+
+
+# ---------------------------------------------------- vectorised operators --
+# reduce / scan / reduce_by_index with map2 (op) over rows of d elements: by
+# definition each output column is the scalar combinator of the same input
+# column (map2 never mixes columns), so the sequential definition is the scalar
+# oracle applied column by column.
+
+def vreduce_fwd(op, x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.array([np.atleast_1d(reduce_fwd(op, x[:, c]))[0] for c in range(x.shape[1])])
+
+
+def vreduce_vjp(op, x, ybar):
+    x = np.asarray(x, dtype=np.float64)
+    ybar = np.asarray(ybar, dtype=np.float64)
+    return np.stack([reduce_vjp(op, x[:, c], ybar[c:c + 1]) for c in range(x.shape[1])], 1)
+
+
+def vscan_fwd(op, x):
+    x = np.asarray(x, dtype=np.float64)
+    return np.stack([scan_fwd(op, x[:, c]) for c in range(x.shape[1])], 1)
+
+
+def vscan_vjp(op, x, ybar):
+    x = np.asarray(x, dtype=np.float64)
+    ybar = np.asarray(ybar, dtype=np.float64)
+    return np.stack([scan_vjp(op, x[:, c], ybar[:, c]) for c in range(x.shape[1])], 1)
+
+
+def vhist_fwd(op, m, keys, vals, hist0=None):
+    vals = np.asarray(vals, dtype=np.float64)
+    cols = [hist_fwd(op, m, keys, vals[:, c], None if hist0 is None else np.asarray(hist0)[:, c])
+            for c in range(vals.shape[1])]
+    if op in ("min", "max"):
+        return np.stack([c[0] for c in cols], 1), np.stack([c[1] for c in cols], 1)
+    return np.stack(cols, 1)
+
+
+def vhist_vjp(op, m, keys, vals, histbar, hist0=None):
+    vals = np.asarray(vals, dtype=np.float64)
+    histbar = np.asarray(histbar, dtype=np.float64)
+    outs = [hist_vjp(op, m, keys, vals[:, c], histbar[:, c], None if hist0 is None else np.asarray(hist0)[:, c])
+            for c in range(vals.shape[1])]
+    return np.stack([o[0] for o in outs], 1), np.stack([o[1] for o in outs], 1)

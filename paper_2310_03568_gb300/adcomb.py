@@ -59,6 +59,15 @@ def lib():
                 "adc_hist_fwd": ([i32, i32, i64, i64, p, p, p, p, p, p, sz, p], i32),
                 "adc_hist_vjp": ([i32, i32, i64, i64, p, p, p, p, p, p, p, p, i32, p, sz, p], i32),
                 "adc_check_device_error": ([p, sz, p], i32),
+                "adc_transpose": ([i32, i64, i64, p, p, p], i32),
+                "adc_vworkspace_bytes": ([i32, i32, i32, i64, i64, i64], sz),
+                "adc_vsaved_bytes": ([i32, i32, i32, i64, i64, i64], sz),
+                "adc_vreduce_fwd": ([i32, i32, i64, i64, p, p, p, p, sz, p], i32),
+                "adc_vreduce_vjp": ([i32, i32, i64, i64, p, p, p, p, p, i32, p, sz, p], i32),
+                "adc_vscan_fwd": ([i32, i32, i64, i64, p, p, p, sz, p], i32),
+                "adc_vscan_vjp": ([i32, i32, i64, i64, p, p, p, p, i32, p, sz, p], i32),
+                "adc_vhist_fwd": ([i32, i32, i64, i64, i64, p, p, p, p, p, p, sz, p], i32),
+                "adc_vhist_vjp": ([i32, i32, i64, i64, i64, p, p, p, p, p, p, p, p, i32, p, sz, p], i32),
                 "adc_set_spin_limit": ([i64], None),
                 "adc_debug_set_stall_tile": ([i64], None),
                 "adc_debug_force_hist_strategy": ([i32], None),
@@ -262,6 +271,104 @@ def debug_set_scan_engine(engine):
 def debug_set_scan_range_tiles(tiles):
     """Tiles per range of the range-partitioned scan engine; 0 lets the library choose."""
     lib().adc_debug_set_scan_range_tiles(int(tiles))
+
+
+# ------------------------------------------------- vectorised operators ----
+# reduce / scan / reduce_by_index with the elementwise operator map2 (op) over
+# rows of d elements (Irwim / Iswim rewrites: transpose + per-column scalar
+# kernels, all in libadcomb).  x is [n][d].
+
+
+def transpose(x, out=None, stream=None):
+    """[rows][cols] -> [cols][rows]."""
+    rows, cols = x.shape
+    if out is None:
+        out = torch.empty((cols, rows), dtype=x.dtype, device=x.device)
+    _check("adc_transpose", lib().adc_transpose(_dt(x), rows, cols, _ptr(x), _ptr(out), _stream(stream)))
+    return out
+
+
+def _vws(kind, op, x, n, m, d, ws):
+    need = int(lib().adc_vworkspace_bytes(KIND[kind], OPS[op], _dt(x), int(n), int(m), int(d)))
+    w = (ws or default_workspace(x.device)).get(need, x.device)
+    return w, w.numel()
+
+
+def vsaved_bytes(kind, op, dtype, n, m, d):
+    return int(lib().adc_vsaved_bytes(KIND[kind], OPS[op], DTYPES[dtype], int(n), int(m), int(d)))
+
+
+def vreduce_fwd(op, x, y=None, saved=None, ws=None, stream=None):
+    n, d = x.shape
+    if y is None:
+        y = torch.empty(d, dtype=x.dtype, device=x.device)
+    if saved is None:
+        saved = torch.empty(max(vsaved_bytes("reduce", op, x.dtype, n, 0, d), 16), dtype=torch.uint8,
+                            device=x.device)
+    w, wb = _vws("reduce", op, x, n, 0, d, ws)
+    _check("adc_vreduce_fwd", lib().adc_vreduce_fwd(OPS[op], _dt(x), n, d, _ptr(x), _ptr(y), _ptr(saved), _ptr(w), wb,
+                                                     _stream(stream)))
+    return y, saved
+
+
+def vreduce_vjp(op, x, y, saved, ybar, xbar=None, accumulate=False, ws=None, stream=None):
+    n, d = x.shape
+    if xbar is None:
+        xbar = torch.empty_like(x)
+    w, wb = _vws("reduce", op, x, n, 0, d, ws)
+    _check("adc_vreduce_vjp", lib().adc_vreduce_vjp(OPS[op], _dt(x), n, d, _ptr(x), _ptr(y), _ptr(saved),
+                                                     _ptr(ybar), _ptr(xbar), int(bool(accumulate)), _ptr(w), wb,
+                                                     _stream(stream)))
+    return xbar
+
+
+def vscan_fwd(op, x, y=None, ws=None, stream=None):
+    n, d = x.shape
+    if y is None:
+        y = torch.empty_like(x)
+    w, wb = _vws("scan", op, x, n, 0, d, ws)
+    _check("adc_vscan_fwd", lib().adc_vscan_fwd(OPS[op], _dt(x), n, d, _ptr(x), _ptr(y), _ptr(w), wb,
+                                                 _stream(stream)))
+    return y
+
+
+def vscan_vjp(op, x, y, ybar, xbar=None, accumulate=False, ws=None, stream=None):
+    n, d = ybar.shape
+    if xbar is None:
+        xbar = torch.empty_like(ybar)
+    w, wb = _vws("scan", op, ybar, n, 0, d, ws)
+    _check("adc_vscan_vjp", lib().adc_vscan_vjp(OPS[op], _dt(ybar), n, d, _ptr(x), _ptr(y), _ptr(ybar), _ptr(xbar),
+                                                 int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return xbar
+
+
+def vhist_fwd(op, m, keys, vals, hist0=None, hist=None, saved=None, primal=False, ws=None, stream=None):
+    """Returns (hist [m][d], saved); primal=True runs the original program (no residuals)."""
+    n, d = vals.shape
+    if hist is None:
+        hist = torch.empty((m, d), dtype=vals.dtype, device=vals.device)
+    if saved is None and not primal:
+        saved = torch.empty(max(vsaved_bytes("hist", op, vals.dtype, n, m, d), 16), dtype=torch.uint8,
+                            device=vals.device)
+    w, wb = _vws("hist", op, vals, n, m, d, ws)
+    _check("adc_vhist_fwd", lib().adc_vhist_fwd(OPS[op], _dt(vals), n, int(m), d, _ptr(keys), _ptr(vals), _ptr(hist0),
+                                                 _ptr(hist), None if primal else _ptr(saved), _ptr(w), wb,
+                                                 _stream(stream)))
+    return hist, saved
+
+
+def vhist_vjp(op, m, keys, vals, hist0, hist, saved, histbar, valsbar=None, hist0bar=None, want_hist0bar=False,
+              accumulate=False, ws=None, stream=None):
+    n, d = vals.shape
+    if valsbar is None:
+        valsbar = torch.empty_like(vals)
+    if hist0bar is None and want_hist0bar:
+        hist0bar = torch.empty_like(histbar)
+    w, wb = _vws("hist", op, vals, n, m, d, ws)
+    _check("adc_vhist_vjp", lib().adc_vhist_vjp(OPS[op], _dt(vals), n, int(m), d, _ptr(keys), _ptr(vals), _ptr(hist0),
+                                                 _ptr(hist), _ptr(saved), _ptr(histbar), _ptr(valsbar),
+                                                 _ptr(hist0bar), int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return valsbar, hist0bar
 
 
 def status_string(code):

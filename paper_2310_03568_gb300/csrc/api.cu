@@ -65,6 +65,12 @@ adc_status prologue(void *ws, size_t ws_bytes, size_t need, cudaStream_t s) {
 }
 
 constexpr int64_t kIdxMax = 0x7fffffffll;
+constexpr int64_t kMaxVecWidth = 64;  // row width d of the vectorised operators
+
+bool vec_op(adc_op op) { return op == ADC_OP_ADD || op == ADC_OP_MUL || op == ADC_OP_MIN || op == ADC_OP_MAX; }
+bool vec_ok(adc_op op, adc_dtype dt, int64_t n, int64_t d) {
+    return vec_op(op) && valid_dt(dt) && n >= 0 && n < kIdxMax && d >= 1 && d <= kMaxVecWidth;
+}
 
 }  // namespace
 
@@ -194,6 +200,104 @@ adc_status adc_hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int
     if (st != ADC_OK) return st;
     return hist_vjp(op, dt, n, m, keys, vals, hist0, hist, saved, histbar, valsbar, hist0bar, accumulate ? 1 : 0, ws,
                     s);
+}
+
+// ------------------------------------------------------ vectorised operators --
+adc_status adc_transpose(adc_dtype dt, int64_t rows, int64_t cols, const void *src, void *dst, void *stream) {
+    if (!valid_dt(dt) || rows < 0 || cols < 0) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(src, rows * cols) || !arr_ok(dst, rows * cols) || (rows * cols > 0 && src == dst))
+        return ADC_ERR_INVALID_ARG;
+    return transpose(dt, rows, cols, src, dst, as_stream(stream));
+}
+
+size_t adc_vworkspace_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
+    if (!vec_ok(op, dt, n, d)) return 0;
+    if (kind == ADC_HIST && (m < 1 || m >= kIdxMax)) return 0;
+    if (kind != ADC_REDUCE && kind != ADC_SCAN && kind != ADC_HIST) return 0;
+    return vws_bytes(kind, op, dt, n, m, d);
+}
+
+size_t adc_vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
+    if (!vec_ok(op, dt, n, d)) return 0;
+    if (kind == ADC_HIST && (m < 1 || m >= kIdxMax)) return 0;
+    if (kind != ADC_REDUCE && kind != ADC_SCAN && kind != ADC_HIST) return 0;
+    return vsaved_bytes(kind, op, dt, n, m, d);
+}
+
+adc_status adc_vreduce_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *saved,
+                           void *ws, size_t ws_bytes, void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(x, n * d) || !arr_ok(y, d)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_REDUCE, op, dt, n, 0, d), s);
+    if (st != ADC_OK) return st;
+    return vreduce_fwd(op, dt, n, d, x, y, saved, ws, s);
+}
+
+adc_status adc_vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y,
+                           const void *saved, const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes,
+                           void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(xbar, n * d) || !arr_ok(ybar, d)) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MUL && !arr_ok(x, n * d)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_REDUCE, op, dt, n, 0, d), s);
+    if (st != ADC_OK) return st;
+    return vreduce_vjp(op, dt, n, d, op == ADC_OP_MUL ? x : nullptr, y, saved, ybar, xbar, accumulate ? 1 : 0, ws, s);
+}
+
+adc_status adc_vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws,
+                         size_t ws_bytes, void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(x, n * d) || !arr_ok(y, n * d)) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_SCAN, op, dt, n, 0, d), s);
+    if (st != ADC_OK) return st;
+    return vscan_fwd(op, dt, n, d, x, y, ws, s);
+}
+
+adc_status adc_vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y,
+                         const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (!arr_ok(ybar, n * d) || !arr_ok(xbar, n * d)) return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (!arr_ok(x, n * d) || !arr_ok(y, n * d))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_SCAN, op, dt, n, 0, d), s);
+    if (st != ADC_OK) return st;
+    return vscan_vjp(op, dt, n, d, x, y, ybar, xbar, accumulate ? 1 : 0, ws, s);
+}
+
+adc_status adc_vhist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys,
+                         const void *vals, const void *hist0, void *hist, void *saved, void *ws, size_t ws_bytes,
+                         void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (m < 1 || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(keys, n) || !arr_ok(vals, n * d) || !arr_ok(hist, m * d)) return ADC_ERR_INVALID_ARG;
+    if ((hist0 != nullptr && !aligned(hist0, 16)) || (saved != nullptr && !aligned(saved, 16)))
+        return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_HIST, op, dt, n, m, d), s);
+    if (st != ADC_OK) return st;
+    return vhist_fwd(op, dt, n, m, d, keys, vals, hist0, hist, saved, ws, s);
+}
+
+adc_status adc_vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys,
+                         const void *vals, const void *hist0, const void *hist, const void *saved, const void *histbar,
+                         void *valsbar, void *hist0bar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    if (!vec_ok(op, dt, n, d)) return vec_op(op) ? ADC_ERR_INVALID_ARG : ADC_ERR_UNSUPPORTED;
+    if (m < 1 || m >= kIdxMax) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(keys, n) || !arr_ok(histbar, m * d) || !arr_ok(valsbar, n * d)) return ADC_ERR_INVALID_ARG;
+    if (op == ADC_OP_MUL && !arr_ok(vals, n * d)) return ADC_ERR_INVALID_ARG;
+    if ((hist0 != nullptr && !aligned(hist0, 16)) || (hist0bar != nullptr && !aligned(hist0bar, 16)))
+        return ADC_ERR_INVALID_ARG;
+    if (op != ADC_OP_ADD && (saved == nullptr || !aligned(saved, 16))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    adc_status st = prologue(ws, ws_bytes, vws_bytes(ADC_HIST, op, dt, n, m, d), s);
+    if (st != ADC_OK) return st;
+    return vhist_vjp(op, dt, n, m, d, keys, op == ADC_OP_MUL ? vals : nullptr, hist0, hist, saved, histbar, valsbar,
+                     hist0bar, accumulate ? 1 : 0, ws, s);
 }
 
 adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream) {

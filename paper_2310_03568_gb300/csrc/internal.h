@@ -88,6 +88,23 @@ adc_status linh_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, con
 // forces the global radix-sort path
 int hist_forced_strategy();
 
+// vector.cu (vectorised operators: transpose + per-column scalar combinators)
+adc_status transpose(adc_dtype dt, int64_t rows, int64_t cols, const void *src, void *dst, cudaStream_t s);
+size_t vws_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d);
+size_t vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d);
+adc_status vreduce_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *saved, void *ws,
+                       cudaStream_t s);
+adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *saved,
+                       const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s);
+adc_status vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s);
+adc_status vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
+                     void *xbar, int accumulate, void *ws, cudaStream_t s);
+adc_status vhist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys, const void *vals,
+                     const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s);
+adc_status vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys, const void *vals,
+                     const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
+                     void *hist0bar, int accumulate, void *ws, cudaStream_t s);
+
 // hist_sop.cu (sumOfProd reduce_by_index, Sec. 3.3)
 adc_status sop_hist_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
                         void *hist, cudaStream_t s);
