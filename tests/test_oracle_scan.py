@@ -185,8 +185,51 @@ def test_minmax_scan_is_the_running_extremum_with_one_hot_adjoints(op):
     assert_close(oracle.scan_vjp(op, x, yb), expect, rtol=1e-12, atol=1e-12)
 
 
+def test_sop_scan_closed_form():
+    # sumOfProd (Fig. 8): scanning (p_i, s_i) gives S_k = sum_{j<=k} s_j and
+    # P_k = sum_{j<=k} p_j + sum_{j<l<=k} s_j s_l = cumsum(p) + (S_k^2 - cumsum(s^2)) / 2.
+    n = 300
+    x = np.stack([RNG.standard_normal(n), RNG.uniform(-1, 1, n)], 1)
+    S = np.cumsum(x[:, 1])
+    P = np.cumsum(x[:, 0]) + (S * S - np.cumsum(x[:, 1] ** 2)) / 2
+    assert_close(oracle.scan_fwd("sop", x), np.stack([P, S], 1), rtol=1e-12, atol=1e-12)
+    # with elements (0, a_i) the last result is (sum_{i<j} a_i a_j, sum_i a_i), by brute force
+    a = RNG.uniform(-1, 1, 12)
+    brute = sum(a[i] * a[j] for i in range(12) for j in range(i + 1, 12))
+    assert_close(oracle.scan_fwd("sop", np.stack([np.zeros(12), a], 1))[-1], [brute, a.sum()],
+                 rtol=1e-13, atol=1e-13)
+
+
+def test_sop_scan_adjoint_closed_form():
+    # From the closed form: dP_k/dp_i = [i <= k], dS_k/ds_i = [i <= k],
+    # dP_k/ds_i = [i <= k] (S_k - s_i), so
+    #   pbar_i = sum_{k>=i} Pbar_k,   sbar_i = sum_{k>=i} (Sbar_k + Pbar_k (S_k - s_i)).
+    n = 200
+    x = np.stack([RNG.standard_normal(n), RNG.uniform(-1, 1, n)], 1)
+    yb = RNG.standard_normal((n, 2))
+    S = np.cumsum(x[:, 1])
+    suf = lambda v: np.cumsum(v[::-1])[::-1]
+    pbar = suf(yb[:, 0])
+    sbar = suf(yb[:, 1]) + suf(yb[:, 0] * S) - x[:, 1] * suf(yb[:, 0])
+    assert_close(oracle.scan_vjp("sop", x, yb), np.stack([pbar, sbar], 1), rtol=1e-11, atol=1e-11)
+
+
+def test_sop_scan_jacobians_are_unit_upper_triangular():
+    # The step y_i = y_{i-1} (.) x_i has dy_i/dy_{i-1} = [[1, s_i], [0, 1]]: the reverse
+    # recurrence is lam_{i-1} = ybar_{i-1} + (lam_i.p, s_i lam_i.p + lam_i.s).
+    n = 40
+    x = np.stack([RNG.standard_normal(n), RNG.uniform(-1, 1, n)], 1)
+    yb = RNG.standard_normal((n, 2))
+    _, lam = oracle.scan_vjp_rbar("sop", x, yb)
+    ref = np.zeros((n, 2))
+    ref[n - 1] = yb[n - 1]
+    for i in range(n - 1, 0, -1):
+        ref[i - 1] = yb[i - 1] + [ref[i, 0], x[i, 1] * ref[i, 0] + ref[i, 1]]
+    assert_close(lam, ref, rtol=1e-12, atol=1e-12)
+
+
 @pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25),
-                                  ("min", 1), ("max", 1)])
+                                  ("min", 1), ("max", 1), ("sop", 2)])
 def test_scan_vjp_finite_differences(op, d):
     n = 20
     shape = (n,) if d == 1 else (n, d)
@@ -201,7 +244,7 @@ def test_scan_vjp_finite_differences(op, d):
 
 
 @pytest.mark.parametrize("op,d", [("add", 1), ("mul", 1), ("lin", 2), ("mm2", 4), ("mm3", 9), ("mm5", 25),
-                                  ("min", 1), ("max", 1)])
+                                  ("min", 1), ("max", 1), ("sop", 2)])
 def test_scan_dot_product(op, d):
     n = 64
     shape = (n,) if d == 1 else (n, d)
