@@ -290,3 +290,42 @@ def vhist_vjp(op, m, keys, vals, histbar, hist0=None):
     outs = [hist_vjp(op, m, keys, vals[:, c], histbar[:, c], None if hist0 is None else np.asarray(hist0)[:, c])
             for c in range(vals.shape[1])]
     return np.stack([o[0] for o in outs], 1), np.stack([o[1] for o in outs], 1)
+
+
+# ------------------------------------------------------------- tuple scans --
+# Scans whose element is a tuple of k blocks that combine independently:
+# block c of a row is an element of operator ops[c] (arity a_c), the row is the
+# blocks one after another (width D = sum a_c), and the tuple operator applies
+# ops[c] to block c.  The Jacobian of every step is then block-diagonal with k
+# blocks of a_c x a_c (Sec. 5.3.3).  By that definition block c of the scan
+# (and of its vjp / jvp) is the scan of operator ops[c] over block c's columns.
+
+def tuple_blocks(ops):
+    """[(op, first column, arity)] for a list of operator names."""
+    out, o = [], 0
+    for op in ops:
+        out.append((op, o, ARITY[op]))
+        o += ARITY[op]
+    return out
+
+
+def _tuple_apply(ops, fn, *arrays):
+    arrays = [np.asarray(a, dtype=np.float64) for a in arrays]
+    n = arrays[0].shape[0]
+    out = np.zeros((n, sum(ARITY[op] for op in ops)))
+    for op, o, a in tuple_blocks(ops):
+        cols = [arr[:, o:o + a] if a > 1 else arr[:, o] for arr in arrays]
+        out[:, o:o + a] = np.asarray(fn(op, *cols)).reshape(n, a)
+    return out
+
+
+def tscan_fwd(ops, x):
+    return _tuple_apply(ops, scan_fwd, x)
+
+
+def tscan_vjp(ops, x, ybar):
+    return _tuple_apply(ops, scan_vjp, x, ybar)
+
+
+def tscan_jvp(ops, x, xdot):
+    return _tuple_apply(ops, scan_jvp, x, xdot)
