@@ -476,7 +476,7 @@ def run_kernels(args):
                       ("lin", np.float32, 100_000_000), ("mm2", np.float32, 10_000_000),
                       ("add", np.float64, 10_000_000), ("mul", np.float64, 10_000_000),
                       ("lin", np.float64, 10_000_000), ("mm3", np.float32, 10_000_000),
-                      ("mm5", np.float32, 4_000_000)]:
+                      ("mm5", np.float32, 4_000_000), ("sop", np.float32, 100_000_000)]:
         if not want(f"scan {op} {np.dtype(dt).name}"):
             continue
         x = torch.from_numpy(synth.scan_values(g, op, n, dt)).to(dev)

@@ -129,7 +129,7 @@ adc_status adc_reduce_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, 
 /* ------------------------------------------------------------------ scan --
  * Inclusive scan y_i = x_0 . x_1 . ... . x_i                      (Sec. 5.1)
  *   x, y : [n] elements.  ops: ADD, MUL, MIN, MAX (running extremum, the
- *   earlier element wins ties), LIN, MM2, MM3, MM5 (SOP: ADC_ERR_UNSUPPORTED).
+ *   earlier element wins ties), LIN, MM2, MM3, MM5, SOP.
  */
 adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, void *y,
                         void *ws, size_t ws_bytes, void *stream);
@@ -142,7 +142,10 @@ adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, vo
  * (y_{-1} = e).  The Jacobians are block-diagonal with equal blocks (RBDS,
  * Sec. 5.3.4): a scalar c for ADD/MUL/LIN, M_{i+1}^T for MM2/MM3/MM5; for
  * MIN/MAX the scalar c_{i+1} = [y_i selected] is 0 or 1 and
- * xbar_i = [x_i selected] lambda_i (the general arity-1 rule).
+ * xbar_i = [x_i selected] lambda_i (the general arity-1 rule).  SOP takes the
+ * general arity-2 rule: c_{i+1} = [[1, s(x_{i+1})], [0, 1]] (not block-redundant),
+ * composed as the single corner entry because unit upper-triangular matrices
+ * multiply by adding it; xbar_i = (lambda.p, s(y_{i-1}) lambda.p + lambda.s).
  *   x, y : the fwd call's input and output; ybar, xbar : [n] elements.
  */
 adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, const void *y,

@@ -46,7 +46,7 @@ bool valid_op(adc_op op) { return op >= ADC_OP_ADD && op <= ADC_OP_MM5; }
 bool matrix_op(adc_op op) { return op == ADC_OP_MM2 || op == ADC_OP_MM3 || op == ADC_OP_MM5; }
 // Operators a scan can take (sumOfProd's invertible rule is a reduce /
 // reduce_by_index rule).
-bool scan_op(adc_op op) { return op != ADC_OP_SOP && valid_op(op); }
+bool scan_op(adc_op op) { return valid_op(op); }
 bool valid_dt(adc_dtype dt) { return dt == ADC_F32 || dt == ADC_F64; }
 bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 

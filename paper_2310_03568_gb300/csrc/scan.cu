@@ -1,5 +1,6 @@
-// Scan forward passes (Sec. 5.1) and their vjps (Fig. 7 with the RBDS
-// specialisation of Sec. 5.3.4), each one decoupled-look-back launch.
+// Scan forward passes (Sec. 5.1) and their vjps (Fig. 7, with the RBDS
+// specialisation of Sec. 5.3.4 where the Jacobians allow it), each one
+// decoupled-look-back launch.
 //
 // vjp: the backward recurrence lambda_i = ybar_i + lambda_{i+1} * J_{i+1} with
 // J_{i+1} = d(y_i . x_{i+1}) / d y_i is solved as a reverse scan whose element
@@ -106,6 +107,14 @@ template <typename T, int ITEMS, bool MAX> struct FwdSel : PlainScan<T, ITEMS, F
 template <typename T, int ITEMS> struct FwdLin : PlainScan<Pair<T>, ITEMS, FwdLin<T, ITEMS>> {
     __device__ Pair<T> identity() const { return {T(0), T(1)}; }
     __device__ Pair<T> combine(const Pair<T> &a, const Pair<T> &b) const { return {b.b + b.c * a.b, b.c * a.c}; }
+};
+
+// sumOfProd (Fig. 8): (p1,s1) . (p2,s2) = (p1 + p2 + s1*s2, s1 + s2)
+template <typename T, int ITEMS> struct FwdSop : PlainScan<Pair<T>, ITEMS, FwdSop<T, ITEMS>> {
+    __device__ Pair<T> identity() const { return {T(0), T(0)}; }
+    __device__ Pair<T> combine(const Pair<T> &a, const Pair<T> &b) const {
+        return {a.b + b.b + a.c * b.c, a.c + b.c};
+    }
 };
 
 template <typename T, int ITEMS> struct FwdMM2 : PlainScan<Mat2<T>, ITEMS, FwdMM2<T, ITEMS>> {
@@ -298,6 +307,64 @@ template <typename T, int ITEMS> struct VjpLin {
     }
 };
 
+// sumOfProd scan by the general rule of Fig. 7 (arity 2, Jacobian blocks not
+// redundant): the step y_{i+1} = y_i . x_{i+1} has
+//   d y_{i+1} / d y_i     = [[1, s(x_{i+1})], [0, 1]],
+//   d y_{i+1} / d x_{i+1} = [[1, s(y_i)],     [0, 1]]     (rows p, s; columns p, s),
+// so lambda_i = ybar_i + (lambda_{i+1}.p, s(x_{i+1}) lambda_{i+1}.p + lambda_{i+1}.s) and
+// xbar_i = (lambda_i.p, s(y_{i-1}) lambda_i.p + lambda_i.s), y_{-1} = (0, 0).
+// Unit upper-triangular 2x2 matrices multiply by adding their corner entries,
+// so the composed coefficient of lin_o is carried as that one entry (sig):
+// the affine map lambda -> v + lambda [[1, sig], [0, 1]] is 3 values, not 2 + 4.
+template <typename T> struct AffU { T vp, vs, sig; };
+
+template <typename T, int ITEMS> struct VjpSop {
+    static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
+    using State = AffU<T>;
+    using Raw = VjpRaw<Pair<T>, ITEMS>;
+    struct Aux { T sprev[ITEMS]; };
+    const Pair<T> *x, *y, *ybar;
+    Pair<T> *xbar;
+    int accumulate;
+    __device__ State identity() const { return {T(0), T(0), T(0)}; }
+    __device__ State combine(const State &acc, const State &e) const {
+        return {e.vp + acc.vp, e.vs + e.sig * acc.vp + acc.vs, acc.sig + e.sig};
+    }
+    __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
+        const Pair<T> z{T(0), T(0)};
+        load_chunk(ybar, c0, n, r.yb.v, z);
+        fetch_next(x, c0, n, r.x, z);
+        fetch_prev(y, c0, n, r.y, z);
+    }
+    static constexpr int kStreams = 3;
+    using Elem = Pair<T>;
+    __device__ const Pair<T> *stream(int s) const { return s == 0 ? ybar : (s == 1 ? x : y); }
+    __device__ void fetch_staged(const Pair<T> *const (&sm)[3], int64_t lo, int64_t c0, int64_t n, Raw &r) const {
+        const Pair<T> z{T(0), T(0)};
+        load_chunk_sm(sm[0] + lo, c0, n, r.yb.v, z);
+        fetch_next_sm(sm[1], lo, c0, n, r.x, z);
+        fetch_prev_sm(sm[2], lo, c0, n, r.y, z);
+    }
+    __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            aux.sprev[k] = prev_of(r.y, k).c;
+            st[k] = (c0 + k < n) ? State{r.yb.v[k].b, r.yb.v[k].c, next_of(r.x, k).c} : identity();
+        }
+    }
+    __device__ void store(int64_t c0, int64_t n, const State (&st)[ITEMS], const Aux &aux) const {
+        Pair<T> out[ITEMS];
+        if (accumulate) load_chunk(xbar, c0, n, out, Pair<T>{T(0), T(0)});
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const T gp = st[k].vp;
+            const T gs = aux.sprev[k] * st[k].vp + st[k].vs;
+            out[k] = accumulate ? Pair<T>{out[k].b + gp, out[k].c + gs} : Pair<T>{gp, gs};
+        }
+        store_chunk(xbar, c0, n, out);
+    }
+};
+
 // 2x2 matrix-product scan: f_i(L) = Ybar_i + L * M_{i+1}^T;  Mbar_i = P_{i-1}^T * lambda_i, P_{-1} = I.
 template <typename T> struct AffM { Mat2<T> v, c; };
 
@@ -420,9 +487,14 @@ static bool use_staged(int64_t n, int64_t regular_tile) {
     return false;
 }
 
+static size_t max4(size_t a, size_t b, size_t c, size_t d) {
+    const size_t ab = a > b ? a : b, cd = c > d ? c : d;
+    return ab > cd ? ab : cd;
+}
+
 template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
     using I = Items<T>;
-    size_t a = 0, b = 0;
+    size_t a = 0, b = 0, c = 0, d = 0;
     switch (op) {
     case ADC_OP_ADD:
         a = ScanShape<FwdAdd<T, I::scalar>, I::scalar>::region(n);
@@ -445,6 +517,12 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
         a = ScanShape<FwdSel<T, I::scalar, false>, I::scalar>::region(n);
         b = ScanShape<VjpSel<T, I::vscalar, false>, I::vscalar>::region(n);
         return kWsHeader + (a > b ? a : b);
+    case ADC_OP_SOP:
+        a = ScanShape<FwdSop<T, I::pair>, I::pair>::region(n);
+        b = ScanShape<VjpSop<T, I::vpair>, I::vpair>::region(n);
+        c = ScanShape<FwdSop<T, I::s_pair>, I::s_pair>::region(n);
+        d = ScanShape<VjpSop<T, I::s_pair>, I::s_pair>::region(n);
+        return kWsHeader + max4(a, b, c, d);
     case ADC_OP_MM3:
         a = ScanShape<FwdMMQ<T, 3, I::mat3>, I::mat3>::region(n);
         b = ScanShape<VjpMMQ<T, 3, I::vmatq>, I::vmatq>::region(n);
@@ -455,7 +533,6 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
         return kWsHeader + (a > b ? a : b);
     default: return 0;
     }
-    size_t c = 0, d = 0;
     switch (op) {
     case ADC_OP_ADD:
         c = ScanShape<FwdAdd<T, I::s_scalar>, I::s_scalar>::region(n);
@@ -474,8 +551,7 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
         d = ScanShape<VjpMM2<T, I::s_mat>, I::s_mat>::region(n);
         break;
     }
-    const size_t ab = a > b ? a : b, cd = c > d ? c : d;
-    return kWsHeader + (ab > cd ? ab : cd);
+    return kWsHeader + max4(a, b, c, d);
 }
 
 size_t scan_ws_bytes(adc_op op, adc_dtype dt, int64_t n) {
@@ -544,6 +620,12 @@ static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void 
             o.y = static_cast<Mat2<T> *>(y);
             return launch_staged<decltype(o), I::s_mat, false>(o, n, ws, s);
         }
+        case ADC_OP_SOP: {
+            FwdSop<T, I::s_pair> o;
+            o.x = static_cast<const Pair<T> *>(x);
+            o.y = static_cast<Pair<T> *>(y);
+            return launch_staged<decltype(o), I::s_pair, false>(o, n, ws, s);
+        }
         default: return ADC_ERR_UNSUPPORTED;
         }
     }
@@ -571,6 +653,12 @@ static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void 
         o.x = static_cast<const Mat2<T> *>(x);
         o.y = static_cast<Mat2<T> *>(y);
         return launch<decltype(o), I::mat, false>(o, n, ws, s);
+    }
+    case ADC_OP_SOP: {
+        FwdSop<T, I::pair> o;
+        o.x = static_cast<const Pair<T> *>(x);
+        o.y = static_cast<Pair<T> *>(y);
+        return launch<decltype(o), I::pair, false>(o, n, ws, s);
     }
     default: return ADC_ERR_UNSUPPORTED;
     }
@@ -627,6 +715,11 @@ static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y,
                                   static_cast<const Mat2<T> *>(ybar), static_cast<Mat2<T> *>(xbar), acc};
             return launch_staged<decltype(o), I::s_mat, true>(o, n, ws, s);
         }
+        case ADC_OP_SOP: {
+            VjpSop<T, I::s_pair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
+                                   static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
+            return launch_staged<decltype(o), I::s_pair, true>(o, n, ws, s);
+        }
         default: return ADC_ERR_UNSUPPORTED;
         }
     }
@@ -649,6 +742,11 @@ static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y,
         VjpMM2<T, I::vmat> o{static_cast<const Mat2<T> *>(x), static_cast<const Mat2<T> *>(y),
                              static_cast<const Mat2<T> *>(ybar), static_cast<Mat2<T> *>(xbar), acc};
         return launch<decltype(o), I::vmat, true>(o, n, ws, s);
+    }
+    case ADC_OP_SOP: {
+        VjpSop<T, I::vpair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
+                              static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
+        return launch<decltype(o), I::vpair, true>(o, n, ws, s);
     }
     default: return ADC_ERR_UNSUPPORTED;
     }

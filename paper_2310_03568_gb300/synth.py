@@ -103,6 +103,9 @@ def scan_values(g, op, n, dtype=np.float32):
         b = normal(g, n, dtype)
         c = uniform(g, n, 0.95, 1.05, dtype)
         return np.ascontiguousarray(np.stack([b, c], axis=1))
+    if op == "sop":
+        # sumOfProd pairs (p, s): both U(-1, 1)
+        return np.ascontiguousarray(uniform(g, 2 * n, -1.0, 1.0, dtype).reshape(n, 2))
     if op == "mm2":
         return (uniform(g, 4 * n, -1.0, 1.0, dtype) / np.asarray(np.sqrt(2.0), dtype)).astype(dtype).reshape(n, 4)
     if op == "mm2_orth":

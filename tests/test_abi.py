@@ -51,7 +51,7 @@ def test_size_queries(L):
     assert L.adc_saved_bytes(2, 4, f32, 1000, 77) >= 3 * 77 * 8       # hist lin, m <= 2047: L, R, A per bin
     assert L.adc_saved_bytes(2, 4, f32, 1000, 5000) >= 1000 * 16     # hist lin, larger m: perm, keys, values
     assert L.adc_saved_bytes(0, 5, f32, 10 ** 6, 0) > 0              # reduce mm2: tile prefixes
-    assert L.adc_workspace_bytes(1, 6, f32, 1000, 0) == 0            # scan sumOfProd: unsupported
+    assert L.adc_workspace_bytes(1, 6, f32, 1000, 0) >= 256          # scan sumOfProd
     assert L.adc_workspace_bytes(0, 6, f32, 1000, 0) >= 256          # reduce sumOfProd
     assert L.adc_workspace_bytes(2, 6, f32, 1000, 10) >= 256         # hist sumOfProd
     assert L.adc_workspace_bytes(0, 7, f32, 1000, 0) >= 256          # reduce 3x3 matrices
@@ -69,7 +69,7 @@ def test_host_validation_rejects_before_any_device_work(L):
     assert L.adc_scan_fwd(0, 7, 10, fake, fake, fake, 1 << 20, None) == 1
     assert L.adc_scan_fwd(0, 0, -1, fake, fake, fake, 1 << 20, None) == 1
     # unsupported operator / combinator pairs
-    assert L.adc_scan_fwd(6, 0, 10, fake, fake, fake, 1 << 20, None) == 2   # sumOfProd scan
+    assert L.adc_hist_fwd(7, 0, 10, 4, fake, fake, None, fake, fake, fake, 1 << 20, None) == 2  # 3x3 hist
     assert L.adc_hist_fwd(5, 0, 10, 4, fake, fake, None, fake, fake, fake, 1 << 20, None) == 2
     # null / misaligned arrays
     assert L.adc_scan_fwd(0, 0, 10, None, fake, fake, 1 << 20, None) == 1

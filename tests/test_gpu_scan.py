@@ -10,9 +10,9 @@ from tests._tol import assert_tol, prefix_max, rowabs, rtol_for, shift_prev, suf
 
 pytestmark = pytest.mark.gpu
 
-TILE = {("add", 4): 4096, ("mul", 4): 4096, ("lin", 4): 2048, ("mm2", 4): 1024,
-        ("add", 8): 2048, ("mul", 8): 2048, ("lin", 8): 1024, ("mm2", 8): 512}
-IDENT = {"add": [0.0], "mul": [1.0], "lin": [0.0, 1.0], "mm2": [1.0, 0.0, 0.0, 1.0],
+TILE = {("add", 4): 4096, ("mul", 4): 4096, ("lin", 4): 2048, ("mm2", 4): 1024, ("sop", 4): 2048,
+        ("add", 8): 2048, ("mul", 8): 2048, ("lin", 8): 1024, ("mm2", 8): 512, ("sop", 8): 1024}
+IDENT = {"add": [0.0], "mul": [1.0], "lin": [0.0, 1.0], "mm2": [1.0, 0.0, 0.0, 1.0], "sop": [0.0, 0.0],
          "mm3": list(np.eye(3).reshape(-1)), "mm5": list(np.eye(5).reshape(-1))}
 
 
@@ -28,8 +28,8 @@ def make_x(g, op, n, dt):
         return synth.uniform(g, n, -1, 1, dt)
     if op == "mul":
         return synth.with_zeros(g, synth.uniform(g, n, 0.9, 1.1, dt), 0.001)
-    if op == "lin":
-        return synth.scan_values(g, "lin", n, dt)
+    if op in ("lin", "sop"):
+        return synth.scan_values(g, op, n, dt)
     return synth.scan_values(g, "mm2_orth" if n > 64 else "mm2", n, dt)
 
 
@@ -84,7 +84,7 @@ def engine(request):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2"])
+@pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2", "sop"])
 def test_scan_sizes(op, dt, engine):
     g = np.random.default_rng(1000 + len(op))
     for n in sizes(op, dt):
@@ -93,7 +93,7 @@ def test_scan_sizes(op, dt, engine):
         check_scan(op, x, ybar, dt)
 
 
-@pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2"])
+@pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2", "sop"])
 def test_scan_accumulate(op, engine):
     g = np.random.default_rng(7)
     x = make_x(g, op, 9001, np.float32)
@@ -102,13 +102,13 @@ def test_scan_accumulate(op, engine):
 
 @pytest.mark.parametrize("engine_id", [0, 3], ids=["auto", "staged"])
 @pytest.mark.parametrize("range_tiles", [0, 3, 16])
-@pytest.mark.parametrize("op", ["add", "lin", "mm2"])
+@pytest.mark.parametrize("op", ["add", "lin", "mm2", "sop"])
 def test_scan_ranges_engine_many_tiles(op, range_tiles, engine_id):
     """Large enough that the automatic choice is the range-partitioned engine
     (several tiles per range); also with more, smaller ranges than resident
     blocks (3 tiles: a ragged last range)."""
     g = np.random.default_rng(17)
-    n = {"add": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001}[op]
+    n = {"add": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001, "sop": 6_000_001}[op]
     x = make_x(g, op, n, np.float32)
     try:
         adcomb.debug_set_scan_engine(engine_id)
@@ -156,7 +156,8 @@ def test_mm2_scan_matches_lin_embedding():
 @pytest.mark.slow
 @pytest.mark.parametrize("op,dt,n", [("add", np.float32, 100_000_000), ("mul", np.float32, 100_000_000),
                                      ("lin", np.float32, 100_000_000), ("add", np.float64, 10_000_000),
-                                     ("mul", np.float64, 10_000_000), ("lin", np.float64, 10_000_000)])
+                                     ("mul", np.float64, 10_000_000), ("lin", np.float64, 10_000_000),
+                                     ("sop", np.float32, 100_000_000)])
 def test_scan_full_size(op, dt, n):
     """The scan workloads at their full sizes (1e8 fp32, 1e7 fp64), every element checked."""
     w = synth.scan_spec(op, n=n, dtype=dt)
