@@ -497,6 +497,28 @@ def run_kernels(args):
         adcomb.debug_set_scan_engine(0)
         adcomb.debug_set_scan_range_tiles(0)
         del x, y, yb, xb
+    # tuple scans (block-diagonal Jacobians): rows [n][D] and one array per block
+    for ops, n in [(("sop",) * 16, 10_000_000), (("add", "mul", "lin", "sop", "mm2", "min"), 20_000_000)]:
+        name = f"{ops[0]}x{len(ops)}" if len(set(ops)) == 1 else "-".join(ops)
+        if not want(f"tscan {name}"):
+            continue
+        blocks = [torch.from_numpy(synth.scan_values(g, op, n) if op not in ("add", "min") else
+                                   synth.uniform(g, n, -1, 1)).to(dev).reshape(n, -1) for op in ops]
+        x = torch.cat(blocks, 1).contiguous()
+        D = x.shape[1]
+        y = adcomb.tscan_fwd(ops, x, ws=ws)
+        yb = torch.randn_like(x)
+        xb = torch.empty_like(x)
+        row(f"tscan {name} fwd rows", n, 2 * n * D * 4, timeit(lambda: adcomb.tscan_fwd(ops, x, y, ws=ws)))
+        row(f"tscan {name} vjp rows", n, 4 * n * D * 4, timeit(lambda: adcomb.tscan_vjp(ops, x, y, yb, xbar=xb, ws=ws)))
+        xs = [b.contiguous().squeeze(1) if b.shape[1] == 1 else b.contiguous() for b in blocks]
+        ys = adcomb.tscan_fwd_blocks(ops, xs, ws=ws)
+        ybs = [torch.randn_like(t) for t in xs]
+        xbs = [torch.empty_like(t) for t in xs]
+        row(f"tscan {name} fwd blocks", n, 2 * n * D * 4, timeit(lambda: adcomb.tscan_fwd_blocks(ops, xs, ys, ws=ws)))
+        row(f"tscan {name} vjp blocks", n, 4 * n * D * 4,
+            timeit(lambda: adcomb.tscan_vjp_blocks(ops, xs, ys, ybs, xbars=xbs, ws=ws)))
+        del x, y, yb, xb, xs, ys, ybs, xbs, blocks
     for op, n in [("add", 100_000_000), ("mul", 100_000_000), ("min", 100_000_000), ("mm2", 10_000_000),
                   ("sop", 50_000_000)]:
         if not want(f"reduce {op}"):

@@ -334,6 +334,48 @@ adc_status adc_vhist_vjp(adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64
                          const void *histbar, void *valsbar, void *hist0bar, int accumulate, void *ws,
                          size_t ws_bytes, void *stream);
 
+/* ----------------------------------------------------------- tuple scans --
+ * Scans whose element is a tuple of k blocks that combine independently
+ * (Sec. 5.3.3, block-diagonal sparsity): block c is an element of operator
+ * ops[c] (an adc_op code, arity a_c: 1 for ADD/MUL/MIN/MAX, 2 LIN/SOP, 4 MM2,
+ * 9 MM3, 25 MM5) and the tuple operator applies ops[c] to block c alone, so
+ * every step's Jacobian is block-diagonal with k blocks of a_c x a_c.  The vjp
+ * is the BDS rule: k reverse scans, block c by its own operator's rule (the
+ * same results as adc_scan_fwd / adc_scan_vjp on that block).  1 <= k <= 64;
+ * ops is a host array of k codes.
+ *
+ * Rows layout (adc_tscan_fwd / _vjp): x, y, ybar, xbar are [n][D] row-major,
+ * D = sum a_c <= 64, block c at columns [sum_{b<c} a_b, + a_c) of every row;
+ * 16-byte aligned.  The rows are split into per-block planes in the
+ * workspace, scanned, and merged back (k = 1: scanned in place).  In the vjp
+ * x and y may be NULL when every block is ADD.
+ *
+ * Blocks layout (adc_tscan_fwd_blocks / _vjp_blocks): the tuple of arrays --
+ * x, y, ybar, xbar are host arrays of k device pointers, entry c an [n][a_c]
+ * array (16-byte aligned); nothing is copied.  In the vjp, x and y (or their
+ * entries for ADD blocks) may be NULL.
+ *
+ * Workspace: adc_tscan_workspace_bytes(k, ops, dtype, n, rows) (rows = 1 for
+ * the rows layout, 0 for blocks); it holds one scan workspace per block (and
+ * the planes for rows); a timeout in any block is reported by
+ * adc_check_device_error on it.  Returns 0 for invalid arguments.
+ * Errors: ADC_ERR_INVALID_ARG for k, codes, D or arrays out of range;
+ * ADC_ERR_WORKSPACE when ws_bytes is too small.
+ */
+size_t adc_tscan_workspace_bytes(int32_t k, const int32_t *ops, adc_dtype dtype, int64_t n, int32_t rows);
+adc_status adc_tscan_fwd(int32_t k, const int32_t *ops, adc_dtype dtype, int64_t n, const void *x, void *y,
+                         void *ws, size_t ws_bytes, void *stream);
+adc_status adc_tscan_vjp(int32_t k, const int32_t *ops, adc_dtype dtype, int64_t n, const void *x,
+                         const void *y, const void *ybar, void *xbar, int accumulate, void *ws,
+                         size_t ws_bytes, void *stream);
+adc_status adc_tscan_fwd_blocks(int32_t k, const int32_t *ops, adc_dtype dtype, int64_t n,
+                                const void *const *x, void *const *y, void *ws, size_t ws_bytes,
+                                void *stream);
+adc_status adc_tscan_vjp_blocks(int32_t k, const int32_t *ops, adc_dtype dtype, int64_t n,
+                                const void *const *x, const void *const *y, const void *const *ybar,
+                                void *const *xbar, int accumulate, void *ws, size_t ws_bytes,
+                                void *stream);
+
 /*
  * dst = transpose(src) for a rows x cols row-major matrix of dtype elements
  * (the layout change of the rewrites above), through shared-memory tiles.

@@ -68,6 +68,11 @@ def lib():
                 "adc_vscan_vjp": ([i32, i32, i64, i64, p, p, p, p, i32, p, sz, p], i32),
                 "adc_vhist_fwd": ([i32, i32, i64, i64, i64, p, p, p, p, p, p, sz, p], i32),
                 "adc_vhist_vjp": ([i32, i32, i64, i64, i64, p, p, p, p, p, p, p, p, i32, p, sz, p], i32),
+                "adc_tscan_workspace_bytes": ([i32, p, i32, i64, i32], sz),
+                "adc_tscan_fwd": ([i32, p, i32, i64, p, p, p, sz, p], i32),
+                "adc_tscan_vjp": ([i32, p, i32, i64, p, p, p, p, i32, p, sz, p], i32),
+                "adc_tscan_fwd_blocks": ([i32, p, i32, i64, p, p, p, sz, p], i32),
+                "adc_tscan_vjp_blocks": ([i32, p, i32, i64, p, p, p, p, i32, p, sz, p], i32),
                 "adc_set_spin_limit": ([i64], None),
                 "adc_debug_set_stall_tile": ([i64], None),
                 "adc_debug_force_hist_strategy": ([i32], None),
@@ -377,3 +382,85 @@ def status_string(code):
 
 def version():
     return lib().adc_version().decode()
+
+
+# ------------------------------------------------------------- tuple scans --
+# Tuple operators whose blocks combine independently (block-diagonal
+# Jacobians): ``ops`` names each block's operator; rows are [n][D] with the
+# blocks side by side (D = sum of arities), or, for the *_blocks calls, one
+# [n][a_c] tensor per block.
+
+def _codes(ops):
+    arr = (ctypes.c_int32 * len(ops))(*[OPS[o] for o in ops])
+    return arr, ctypes.cast(arr, ctypes.c_void_p)
+
+
+def _ptrs(ts):
+    """Host array of device pointers (None entries stay NULL), or NULL for None."""
+    if ts is None:
+        return None, None
+    arr = (ctypes.c_void_p * len(ts))(*[None if t is None else t.data_ptr() for t in ts])
+    return arr, ctypes.cast(arr, ctypes.c_void_p)
+
+
+def tscan_workspace_bytes(ops, dtype, n, rows=True):
+    keep, codes = _codes(ops)
+    return int(lib().adc_tscan_workspace_bytes(len(ops), codes, DTYPES[dtype], int(n), int(bool(rows))))
+
+
+def _tws(ops, t, n, rows, ws):
+    need = tscan_workspace_bytes(ops, t.dtype, n, rows)
+    if need == 0:
+        raise AdcError("adc_tscan_workspace_bytes", 1)
+    w = (ws or default_workspace(t.device)).get(need, t.device)
+    return w, w.numel()
+
+
+def tscan_fwd(ops, x, y=None, ws=None, stream=None):
+    n = x.shape[0]
+    if y is None:
+        y = torch.empty_like(x)
+    w, wb = _tws(ops, x, n, True, ws)
+    keep, codes = _codes(ops)
+    _check("adc_tscan_fwd", lib().adc_tscan_fwd(len(ops), codes, _dt(x), n, _ptr(x), _ptr(y), _ptr(w), wb,
+                                                 _stream(stream)))
+    return y
+
+
+def tscan_vjp(ops, x, y, ybar, xbar=None, accumulate=False, ws=None, stream=None):
+    n = ybar.shape[0]
+    if xbar is None:
+        xbar = torch.empty_like(ybar)
+    w, wb = _tws(ops, ybar, n, True, ws)
+    keep, codes = _codes(ops)
+    _check("adc_tscan_vjp", lib().adc_tscan_vjp(len(ops), codes, _dt(ybar), n, _ptr(x), _ptr(y), _ptr(ybar),
+                                                 _ptr(xbar), int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return xbar
+
+
+def tscan_fwd_blocks(ops, xs, ys=None, ws=None, stream=None):
+    n = xs[0].shape[0]
+    if ys is None:
+        ys = [torch.empty_like(x) for x in xs]
+    w, wb = _tws(ops, xs[0], n, False, ws)
+    keep, codes = _codes(ops)
+    kx, px = _ptrs(xs)
+    ky, py = _ptrs(ys)
+    _check("adc_tscan_fwd_blocks", lib().adc_tscan_fwd_blocks(len(ops), codes, _dt(xs[0]), n, px, py, _ptr(w), wb,
+                                                               _stream(stream)))
+    return ys
+
+
+def tscan_vjp_blocks(ops, xs, ys, ybars, xbars=None, accumulate=False, ws=None, stream=None):
+    n = ybars[0].shape[0]
+    if xbars is None:
+        xbars = [torch.empty_like(t) for t in ybars]
+    w, wb = _tws(ops, ybars[0], n, False, ws)
+    keep, codes = _codes(ops)
+    kx, px = _ptrs(xs)
+    ky, py = _ptrs(ys)
+    kb, pb = _ptrs(ybars)
+    kxb, pxb = _ptrs(xbars)
+    _check("adc_tscan_vjp_blocks", lib().adc_tscan_vjp_blocks(len(ops), codes, _dt(ybars[0]), n, px, py, pb, pxb,
+                                                               int(bool(accumulate)), _ptr(w), wb, _stream(stream)))
+    return xbars

@@ -72,6 +72,23 @@ bool vec_ok(adc_op op, adc_dtype dt, int64_t n, int64_t d) {
     return vec_op(op) && valid_dt(dt) && n >= 0 && n < kIdxMax && d >= 1 && d <= kMaxVecWidth;
 }
 
+// Copies and checks the block operators: 1 <= k <= kMaxTupleBlocks, every one a
+// scan operator; *width receives the row width sum of arities.
+adc_status tuple_ops(int32_t k, const int32_t *codes, adc_dtype dt, int64_t n, adc_op *ops, int64_t *width) {
+    if (k < 1 || k > kMaxTupleBlocks || codes == nullptr || !valid_dt(dt) || n < 0) return ADC_ERR_INVALID_ARG;
+    int64_t w = 0;
+    for (int c = 0; c < k; ++c) {
+        if (codes[c] < (int32_t)ADC_OP_ADD || codes[c] > (int32_t)ADC_OP_MM5) return ADC_ERR_INVALID_ARG;
+        const adc_op op = static_cast<adc_op>(codes[c]);
+        if (!valid_op(op)) return ADC_ERR_INVALID_ARG;
+        if (!scan_op(op)) return ADC_ERR_UNSUPPORTED;
+        ops[c] = op;
+        w += arity(op);
+    }
+    *width = w;
+    return ADC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -298,6 +315,83 @@ adc_status adc_vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t 
     if (st != ADC_OK) return st;
     return vhist_vjp(op, dt, n, m, d, keys, op == ADC_OP_MUL ? vals : nullptr, hist0, hist, saved, histbar, valsbar,
                      hist0bar, accumulate ? 1 : 0, ws, s);
+}
+
+// ----------------------------------------------------------- tuple scans --
+
+size_t adc_tscan_workspace_bytes(int32_t k, const int32_t *ops, adc_dtype dt, int64_t n, int32_t rows) {
+    adc_op o[kMaxTupleBlocks];
+    int64_t w = 0;
+    if (tuple_ops(k, ops, dt, n, o, &w) != ADC_OK) return 0;
+    if (rows && w > kMaxTupleBlocks) return 0;
+    return tscan_ws_bytes(k, o, dt, n, rows != 0);
+}
+
+adc_status adc_tscan_fwd(int32_t k, const int32_t *ops, adc_dtype dt, int64_t n, const void *x, void *y, void *ws,
+                         size_t ws_bytes, void *stream) {
+    adc_op o[kMaxTupleBlocks];
+    int64_t w = 0;
+    adc_status st = tuple_ops(k, ops, dt, n, o, &w);
+    if (st != ADC_OK) return st;
+    if (w > kMaxTupleBlocks) return ADC_ERR_INVALID_ARG;
+    if (!arr_ok(x, n * w) || !arr_ok(y, n * w)) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if ((st = prologue(ws, ws_bytes, tscan_ws_bytes(k, o, dt, n, true), s)) != ADC_OK) return st;
+    return tscan_fwd_rows(k, o, dt, n, x, y, ws, s);
+}
+
+adc_status adc_tscan_vjp(int32_t k, const int32_t *ops, adc_dtype dt, int64_t n, const void *x, const void *y,
+                         const void *ybar, void *xbar, int accumulate, void *ws, size_t ws_bytes, void *stream) {
+    adc_op o[kMaxTupleBlocks];
+    int64_t w = 0;
+    adc_status st = tuple_ops(k, ops, dt, n, o, &w);
+    if (st != ADC_OK) return st;
+    if (w > kMaxTupleBlocks) return ADC_ERR_INVALID_ARG;
+    bool all_add = true;
+    for (int c = 0; c < k; ++c) all_add = all_add && o[c] == ADC_OP_ADD;
+    if (!arr_ok(ybar, n * w) || !arr_ok(xbar, n * w)) return ADC_ERR_INVALID_ARG;
+    if (!all_add && (!arr_ok(x, n * w) || !arr_ok(y, n * w))) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if ((st = prologue(ws, ws_bytes, tscan_ws_bytes(k, o, dt, n, true), s)) != ADC_OK) return st;
+    return tscan_vjp_rows(k, o, dt, n, x, y, ybar, xbar, accumulate ? 1 : 0, ws, s);
+}
+
+adc_status adc_tscan_fwd_blocks(int32_t k, const int32_t *ops, adc_dtype dt, int64_t n, const void *const *x,
+                                void *const *y, void *ws, size_t ws_bytes, void *stream) {
+    adc_op o[kMaxTupleBlocks];
+    int64_t w = 0;
+    adc_status st = tuple_ops(k, ops, dt, n, o, &w);
+    if (st != ADC_OK) return st;
+    if (x == nullptr || y == nullptr) return ADC_ERR_INVALID_ARG;
+    for (int c = 0; c < k; ++c)
+        if (!arr_ok(x[c], n) || !arr_ok(y[c], n)) return ADC_ERR_INVALID_ARG;
+    cudaStream_t s = as_stream(stream);
+    if ((st = prologue(ws, ws_bytes, tscan_ws_bytes(k, o, dt, n, false), s)) != ADC_OK) return st;
+    return tscan_fwd_blocks(k, o, dt, n, x, y, ws, s);
+}
+
+adc_status adc_tscan_vjp_blocks(int32_t k, const int32_t *ops, adc_dtype dt, int64_t n, const void *const *x,
+                                const void *const *y, const void *const *ybar, void *const *xbar, int accumulate,
+                                void *ws, size_t ws_bytes, void *stream) {
+    adc_op o[kMaxTupleBlocks];
+    int64_t w = 0;
+    adc_status st = tuple_ops(k, ops, dt, n, o, &w);
+    if (st != ADC_OK) return st;
+    if (ybar == nullptr || xbar == nullptr) return ADC_ERR_INVALID_ARG;
+    for (int c = 0; c < k; ++c) {
+        if (!arr_ok(ybar[c], n) || !arr_ok(xbar[c], n)) return ADC_ERR_INVALID_ARG;
+        if (o[c] != ADC_OP_ADD && (x == nullptr || y == nullptr || !arr_ok(x[c], n) || !arr_ok(y[c], n)))
+            return ADC_ERR_INVALID_ARG;
+    }
+    // + blocks read neither x nor y: hand them null arrays when none were given
+    const void *xs[kMaxTupleBlocks], *ys[kMaxTupleBlocks];
+    for (int c = 0; c < k; ++c) {
+        xs[c] = x ? x[c] : nullptr;
+        ys[c] = y ? y[c] : nullptr;
+    }
+    cudaStream_t s = as_stream(stream);
+    if ((st = prologue(ws, ws_bytes, tscan_ws_bytes(k, o, dt, n, false), s)) != ADC_OK) return st;
+    return tscan_vjp_blocks(k, o, dt, n, xs, ys, ybar, xbar, accumulate ? 1 : 0, ws, s);
 }
 
 adc_status adc_check_device_error(const void *ws, size_t ws_bytes, void *stream) {

@@ -105,6 +105,20 @@ adc_status vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, c
                      const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
                      void *hist0bar, int accumulate, void *ws, cudaStream_t s);
 
+// tuple.cu (tuple scans with block-diagonal Jacobians, Sec. 5.3.3): at most
+// kMaxTupleBlocks blocks; in the rows layout at most kMaxTupleBlocks scalars a row
+constexpr int kMaxTupleBlocks = 64;
+size_t tscan_ws_bytes(int k, const adc_op *ops, adc_dtype dt, int64_t n, bool rows);
+adc_status tscan_fwd_blocks(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *const *x, void *const *y,
+                            void *ws, cudaStream_t s);
+adc_status tscan_vjp_blocks(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *const *x,
+                            const void *const *y, const void *const *ybar, void *const *xbar, int accumulate, void *ws,
+                            cudaStream_t s);
+adc_status tscan_fwd_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *x, void *y, void *ws,
+                          cudaStream_t s);
+adc_status tscan_vjp_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *x, const void *y,
+                          const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s);
+
 // hist_sop.cu (sumOfProd reduce_by_index, Sec. 3.3)
 adc_status sop_hist_fwd(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals, const void *hist0,
                         void *hist, cudaStream_t s);

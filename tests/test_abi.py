@@ -60,6 +60,33 @@ def test_size_queries(L):
     assert L.adc_workspace_bytes(0, 9, f32, 1000, 0) == 0            # no operator 9
 
 
+def test_tuple_size_queries(L):
+    f32 = 0
+    codes = lambda *c: (ctypes.c_int32 * len(c))(*c)
+    assert L.adc_tscan_workspace_bytes(3, codes(6, 4, 0), f32, 1000, 1) >= 4 * 256   # rows: planes + 3 block ws
+    assert L.adc_tscan_workspace_bytes(3, codes(6, 4, 0), f32, 1000, 0) >= 4 * 256   # blocks: 3 block ws
+    assert L.adc_tscan_workspace_bytes(1, codes(6), f32, 1000, 1) == L.adc_workspace_bytes(1, 6, f32, 1000, 0)
+    assert L.adc_tscan_workspace_bytes(3, codes(8, 8, 8), f32, 10, 1) == 0           # rows of 75 > 64 scalars
+    assert L.adc_tscan_workspace_bytes(3, codes(8, 8, 8), f32, 10, 0) > 0            # as separate arrays: fine
+    assert L.adc_tscan_workspace_bytes(0, codes(0), f32, 10, 1) == 0                  # no blocks
+    assert L.adc_tscan_workspace_bytes(2, codes(0, 9), f32, 10, 1) == 0               # no operator 9
+    assert L.adc_tscan_workspace_bytes(2, None, f32, 10, 1) == 0
+
+
+def test_tuple_host_validation(L):
+    fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation first
+    codes = lambda *c: (ctypes.c_int32 * len(c))(*c)
+    many = (ctypes.c_int32 * 65)(*([0] * 65))
+    assert L.adc_tscan_fwd(65, many, 0, 10, fake, fake, fake, 1 << 20, None) == 1          # k > 64
+    assert L.adc_tscan_fwd(2, codes(0, -1), 0, 10, fake, fake, fake, 1 << 20, None) == 1   # bad code
+    assert L.adc_tscan_fwd(3, codes(8, 8, 8), 0, 10, fake, fake, fake, 1 << 20, None) == 1  # row width 75
+    assert L.adc_tscan_fwd(2, codes(0, 6), 0, 10, None, fake, fake, 1 << 20, None) == 1    # null x
+    assert L.adc_tscan_fwd(2, codes(0, 6), 0, 10, fake, fake, fake, 8, None) == 3          # workspace too small
+    assert L.adc_tscan_fwd_blocks(2, codes(0, 6), 0, 10, None, None, fake, 1 << 20, None) == 1
+    ptrs = (ctypes.c_void_p * 2)(1 << 20, (1 << 20) + 4)                                   # misaligned block
+    assert L.adc_tscan_fwd_blocks(2, codes(0, 6), 0, 10, ptrs, ptrs, fake, 1 << 20, None) == 1
+
+
 def test_host_validation_rejects_before_any_device_work(L):
     fake = ctypes.c_void_p(1 << 20)  # never dereferenced: every call below fails validation first
     ws_small = 8
