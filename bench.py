@@ -555,6 +555,28 @@ def run_kernels(args):
         row(f"hist {op} vjp m={m}", n, n * (4 + (2 if op in ("lin", "sop") else 1) * es),
             timeit(lambda: adcomb.hist_vjp(op, m, k, v, None, h, saved, hb, valsbar=vb, ws=ws)))
         del k, v, vb
+    # the benchmark's reduce-by-index instances (n = 50M fp32): lifted forward, and the
+    # min/max vjp in both of its forms
+    if args.only is not None and args.only.startswith("bench"):
+        keys_h, vals_h, hbar_h = make_inputs(N)
+        for m in BINS:
+            k = torch.from_numpy(keys_h[m]).to(dev)
+            hb = torch.from_numpy(hbar_h[m]).to(dev)
+            for op in OPS:
+                if not want(f"bench {op} m={m}"):
+                    continue
+                v = torch.from_numpy(vals_h[op]).to(dev)
+                h, saved = adcomb.hist_fwd(op, m, k, v, ws=ws)
+                vb = torch.empty_like(v)
+                row(f"bench {op} m={m} fwd", N, 8 * N, timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
+                forms = [(1, "gather"), (2, "scatter")] if op != "mul" else [(0, "")]
+                for f, label in forms:
+                    adcomb.debug_set_sel_vjp_form(f)
+                    row(f"bench {op} m={m} vjp {label}".strip(), N, (12 if op == "mul" else 4) * N,
+                        timeit(lambda: adcomb.hist_vjp(op, m, k, v, None, h, saved, hb, valsbar=vb, ws=ws)))
+                adcomb.debug_set_sel_vjp_form(0)
+                del v, vb
+            del k, hb
     print(f"| kernel | n | algorithmic bytes | ms | GB/s | frac of {kind} {peak:.0f} GB/s |")
     print("|---|---|---|---|---|---|")
     for name, n, nb, ms, gbs, fr in rows:

@@ -426,6 +426,14 @@ void adc_debug_set_scan_range_tiles(int tiles);
  */
 void adc_debug_force_hist_strategy(int strategy);
 
+/*
+ * Tuning hook: form of the min/max reduce-by-index vjp -- 0 automatic (a
+ * gather pass over the keys when bins are sparse, 8m > n; else a zero-fill
+ * plus a scatter of the m adjoints), 1 always the gather, 2 always the
+ * zero-fill + scatter.  Results are identical.
+ */
+void adc_debug_set_sel_vjp_form(int form);
+
 #ifdef __cplusplus
 }
 #endif

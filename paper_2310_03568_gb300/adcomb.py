@@ -76,6 +76,7 @@ def lib():
                 "adc_set_spin_limit": ([i64], None),
                 "adc_debug_set_stall_tile": ([i64], None),
                 "adc_debug_force_hist_strategy": ([i32], None),
+                "adc_debug_set_sel_vjp_form": ([i32], None),
                 "adc_debug_set_scan_engine": ([i32], None),
                 "adc_debug_set_scan_range_tiles": ([i32], None),
                 "adc_status_string": ([i32], ctypes.c_char_p),
@@ -262,6 +263,11 @@ def set_spin_limit(iterations):
 
 def debug_set_stall_tile(tile):
     lib().adc_debug_set_stall_tile(int(tile))
+
+
+def debug_set_sel_vjp_form(form):
+    """min/max reduce-by-index vjp: 0 automatic, 1 gather pass, 2 zero-fill + scatter."""
+    lib().adc_debug_set_sel_vjp_form(int(form))
 
 
 def debug_force_hist_strategy(strategy):

@@ -742,21 +742,23 @@ __global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__rest
         if (!in_range(k, m)) return T(0);
         return v != T(0) ? __ldg(anz + k) / v : __ldg(az + k);
     };
-    const int64_t nv = n / 4;
+    // two 4-element groups per thread and step: both groups' loads issued first
+    const int64_t nv = n / 8;
     for (int64_t v = g; v < nv; v += stride) {
-        const int4 k = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
-        T a[4], o[4];
-        load_chunk(vals, v * 4, n, a, T(1));
-        if (accumulate) load_chunk(vb, v * 4, n, o, T(0));
-        const int kk[4] = {k.x, k.y, k.z, k.w};
+        const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + 2 * v);
+        const int4 k1 = __ldcs(reinterpret_cast<const int4 *>(keys) + 2 * v + 1);
+        T a[8], o[8];
+        load_chunk(vals, v * 8, n, a, T(1));
+        if (accumulate) load_chunk(vb, v * 8, n, o, T(0));
+        const int kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
+        for (int c = 0; c < 8; ++c) {
             const T gv = grad(kk[c], a[c]);
             o[c] = accumulate ? o[c] + gv : gv;
         }
-        store_chunk(vb, v * 4, n, o);
+        store_chunk(vb, v * 8, n, o);
     }
-    for (int64_t i = nv * 4 + g; i < n; i += stride) {
+    for (int64_t i = nv * 8 + g; i < n; i += stride) {
         const T gv = grad(keys[i], vals[i]);
         vb[i] = accumulate ? vb[i] + gv : gv;
     }
@@ -780,6 +782,7 @@ static unsigned grid_for(int64_t work, int per_sm) {
 }
 
 static int g_force_strategy = -1;  // tests: force a strategy (-1: automatic)
+static int g_sel_vjp_form = 0;     // min/max vjp: 0 automatic, 1 gather, 2 zero-fill + scatter
 
 constexpr size_t kThrBudget = 64 * 1024;    // per-thread tables: 3 blocks of 256 threads per SM
 constexpr size_t kWarpBudget = 48 * 1024;   // 8 per-warp copies, 4 blocks per SM
@@ -1113,6 +1116,7 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
                              const void *saved, const T *hb, T *vb, T *h0b, int acc, void *ws, cudaStream_t s) {
     const unsigned gm = grid_for(m, 4);
     const unsigned gn = grid_for(n / 4 + 1, 8);
+    const unsigned gn8 = grid_for(n / 8 + 1, 8);  // the * vjp: 8 elements per step
     switch (op) {
     case ADC_OP_ADD:
         if (n > 0) k_hist_add_vjp<T><<<gn, 256, 0, s>>>(keys, hb, vb, n, m, acc);
@@ -1121,7 +1125,8 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
     case ADC_OP_MIN:
     case ADC_OP_MAX: {
         const int32_t *is = static_cast<const int32_t *>(saved);
-        if (m * 8 > n) {  // few values per bin: one gather pass
+        const bool gather = g_sel_vjp_form == 1 || (g_sel_vjp_form == 0 && m * 8 > n);
+        if (gather) {  // few values per bin: one gather pass
             if (n > 0) k_hist_sel_vjp_gather<T><<<gn, 256, 0, s>>>(keys, is, hb, vb, n, m, acc);
             if (h0b) k_h0bar_sel<T><<<gm, 256, 0, s>>>(is, hb, h0b, m, n, acc);
         } else {          // many values per bin: zero-fill, then scatter m adjoints
@@ -1137,7 +1142,7 @@ static adc_status hist_vjp_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         T *az = reinterpret_cast<T *>(static_cast<char *>(ws) + kWsHeader + align_up((size_t)m * sizeof(T), 256));
         if (n > 0) {
             k_mul_vjp_prep<T><<<gm, 256, 0, s>>>(n0, p, h0, hb, anz, az, m);
-            k_hist_mul_vjp<T><<<gn, 256, 0, s>>>(keys, vals, anz, az, vb, n, m, acc);
+            k_hist_mul_vjp<T><<<gn8, 256, 0, s>>>(keys, vals, anz, az, vb, n, m, acc);
         }
         if (h0b) k_h0bar_mul<T><<<gm, 256, 0, s>>>(n0, p, hb, h0b, m, acc);
         return check_launch();
@@ -1165,4 +1170,5 @@ adc_status hist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, const int32_t
 }  // namespace adc
 
 extern "C" void adc_debug_force_hist_strategy(int s) { adc::g_force_strategy = s; }
+extern "C" void adc_debug_set_sel_vjp_form(int f) { adc::g_sel_vjp_form = (f >= 0 && f <= 2) ? f : 0; }
 int adc::hist_forced_strategy() { return adc::g_force_strategy; }

@@ -336,3 +336,29 @@ def test_hist_unsupported_and_invalid():
     with pytest.raises(adcomb.AdcError) as e:
         adcomb.hist_fwd("add", 0, k, dev(np.zeros(4, np.float32)))
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_hist_sel_vjp_forms(op, dt):
+    """Both forms of the min/max vjp (gather pass; zero-fill + scatter), forced
+    on both sides of the automatic threshold, equal the oracle bit-exactly
+    (each adjoint is one histbar value or zero; with accumulate, one add)."""
+    g = np.random.default_rng(61)
+    try:
+        for n, m in [(0, 5), (7, 3), (100_003, 31), (100_003, 50_000), (1_000_003, 400_000), (20_001, 200_000)]:
+            k = keys_oor(g, n, m)
+            v = ((g.integers(0, 64, n) - 32) / 8.0).astype(dt)
+            hb = synth.normal(g, m, dt)
+            h, saved = adcomb.hist_fwd(op, m, dev(k), dev(v))
+            ref, _ = oracle.hist_vjp(op, m, k, v, hb)
+            old = synth.normal(g, n, dt)
+            for form in (0, 1, 2):
+                adcomb.debug_set_sel_vjp_form(form)
+                vb, _ = adcomb.hist_vjp(op, m, dev(k), dev(v), None, h, saved, dev(hb))
+                assert np.array_equal(host(vb), ref.astype(dt)), (n, m, form)
+                vb2, _ = adcomb.hist_vjp(op, m, dev(k), dev(v), None, h, saved, dev(hb), valsbar=dev(old),
+                                         accumulate=True)
+                assert np.array_equal(host(vb2), (old + ref.astype(dt)).astype(dt)), (n, m, form)
+    finally:
+        adcomb.debug_set_sel_vjp_form(0)
