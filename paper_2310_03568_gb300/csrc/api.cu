@@ -13,6 +13,8 @@ static long long g_stall_tile = -1;
 int g_scan_engine = 0;
 int g_scan_range_tiles = 0;
 
+long long spin_limit() { return g_spin_limit; }
+
 DevCtl make_ctl(void *ws, int slot) {
     DevCtl c;
     c.err = static_cast<unsigned *>(ws);

@@ -15,7 +15,8 @@
 //   3. scatter each chunk is counting-sorted by bucket in shared memory and
 //              written out as contiguous runs of (bin within the bucket, 16
 //              bits; payload), the payload being the value (+, *) or the packed
-//              (value, index) key (lifted min/max);
+//              (value, index) key (lifted min/max); for fp32 a persistent block
+//              per SM with the chunks staged by bulk (TMA) copies one ahead;
 //   4. table   one block per bucket streams its run into a shared-memory table
 //              of W bins and writes them out.  Every bin belongs to exactly one
 //              bucket, so there are no global atomics at all.
@@ -27,6 +28,7 @@
 #include "hist_common.cuh"
 #include "internal.h"
 #include "tile_io.cuh"
+#include "tma.cuh"
 
 namespace adc {
 
@@ -209,27 +211,63 @@ __device__ __forceinline__ void load_group(const int32_t *__restrict__ keys, con
     }
 }
 
-// 1. counts[b * nchunks + chunk] = elements of the chunk in bucket b; row B is
-// a zero row so that the scanned matrix also gives every bucket's end.
-__global__ void __launch_bounds__(kPartThreads)
-k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const BucketDiv bdiv, const int B,
-             const int64_t nchunks, int32_t *__restrict__ counts) {
-    extern __shared__ int32_t s_cnt[];
-    for (int b = threadIdx.x; b < B; b += kPartThreads) s_cnt[b] = 0;
-    __syncthreads();
-    const int64_t c0 = (int64_t)blockIdx.x * kPartChunk;
-#pragma unroll
-    for (int r = 0; r < kPartItems / 4; ++r) {
-        int32_t kk[4];
-        float unused[4];
-        load_group<float>(keys, nullptr, c0 + 4 * ((int64_t)r * kPartThreads + threadIdx.x), n, kk, unused);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (in_range(kk[c], m)) atomicAdd(&s_cnt[bdiv((uint32_t)kk[c])], 1);
+// 1. counts[b * nchunks + chunk] = elements of the chunk in bucket b (row B is
+// a zero row, so that the scanned matrix also gives every bucket's end).  One
+// block per SM walks chunks b, b + G, ...: the next chunk's keys are loaded
+// into registers while this chunk's are counted in shared memory, and each
+// bucket counter is written out and cleared by one thread.
+constexpr int kCountThreads = 1024;
+constexpr int kCountVecs = kPartChunk / (4 * kCountThreads);  // int4 loads per thread per chunk (2)
+
+__device__ __forceinline__ void load_keys_vec(const int32_t *__restrict__ keys, int64_t e, int64_t n, int4 &k) {
+    if (e + 4 <= n) {
+        k = __ldcs(reinterpret_cast<const int4 *>(keys + e));
+    } else {
+        k.x = e < n ? keys[e] : -1;
+        k.y = e + 1 < n ? keys[e + 1] : -1;
+        k.z = e + 2 < n ? keys[e + 2] : -1;
+        k.w = e + 3 < n ? keys[e + 3] : -1;
     }
+}
+
+__global__ void __launch_bounds__(kCountThreads)
+k_part_count_p(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const BucketDiv bdiv, const int B,
+               const int64_t nchunks, int32_t *__restrict__ counts) {
+    extern __shared__ int32_t s_cnt[];
+    const int tid = threadIdx.x;
+    const int64_t G = gridDim.x;
+    for (int b = tid; b < B; b += kCountThreads) s_cnt[b] = 0;
+    if (blockIdx.x == 0)  // the zero row B
+        for (int64_t c = tid; c < nchunks; c += kCountThreads) counts[(int64_t)B * nchunks + c] = 0;
+    int4 cur[kCountVecs];
+    const auto load = [&](int64_t c, int4 (&k)[kCountVecs]) {
+#pragma unroll
+        for (int r = 0; r < kCountVecs; ++r)
+            load_keys_vec(keys, c * kPartChunk + 4 * ((int64_t)r * kCountThreads + tid), n, k[r]);
+    };
+    if ((int64_t)blockIdx.x < nchunks) load(blockIdx.x, cur);
     __syncthreads();
-    for (int b = threadIdx.x; b <= B; b += kPartThreads)
-        counts[(int64_t)b * nchunks + blockIdx.x] = b < B ? s_cnt[b] : 0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += G) {
+        int4 nxt[kCountVecs];
+        if (c + G < nchunks) load(c + G, nxt);
+#pragma unroll
+        for (int r = 0; r < kCountVecs; ++r) {
+            const int kk[4] = {cur[r].x, cur[r].y, cur[r].z, cur[r].w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (in_range(kk[q], m)) atomicAdd(&s_cnt[bdiv((uint32_t)kk[q])], 1);
+        }
+        __syncthreads();
+        for (int b = tid; b < B; b += kCountThreads) {
+            counts[(int64_t)b * nchunks + c] = s_cnt[b];
+            s_cnt[b] = 0;
+        }
+        __syncthreads();
+        if (c + G < nchunks) {
+#pragma unroll
+            for (int r = 0; r < kCountVecs; ++r) cur[r] = nxt[r];
+        }
+    }
 }
 
 // 3. Counting sort of one chunk by bucket in shared memory, then contiguous
@@ -343,6 +381,174 @@ k_part_scatter(const int32_t *__restrict__ keys, const T *__restrict__ vals, con
         const int64_t g = (int64_t)s_dst[x >> 16] + pos;
         obin[g] = (uint16_t)(x & 0xffffu);
         oval[g] = s_v[pos];
+    }
+}
+
+// 3 (fp32). The same counting sort as a persistent, double-buffered pipeline:
+// block b owns chunks b, b + G, b + 2G, ... (G blocks, one per SM); each
+// whole chunk's keys and values arrive in shared memory by two bulk copies
+// issued one chunk ahead, so the DRAM reads of the next chunk overlap the
+// ranking, the bucket scan and the writes of this one.  The chunk is ranked
+// by bucket as above; a 16-bit permutation (bucket order -> element) takes
+// the place of the sorted payload copy, and the readout gathers key and value
+// from the staged chunk.  The ragged last chunk is loaded by plain loads.
+constexpr int kScatThreads = 1024;
+constexpr int kScatItems = kPartChunk / kScatThreads;  // 8 elements per thread
+
+template <int MODE>
+__global__ void __launch_bounds__(kScatThreads, 1)
+k_part_scatter_tma(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                   const BucketDiv bdiv, const int B, const int64_t nchunks, const int32_t *__restrict__ offs,
+                   uint16_t *__restrict__ obin, typename PartTraits<float, MODE>::V *__restrict__ oval,
+                   unsigned *__restrict__ err, const long long spin_limit) {
+    using Tr = PartTraits<float, MODE>;
+    constexpr int NW = kScatThreads / kWarp;
+    constexpr int PER = kPartMaxBuckets / kScatThreads;  // buckets per thread in the local scan
+    constexpr uint32_t kChunkBytes = kPartChunk * 4u;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    int32_t *const s_key0 = reinterpret_cast<int32_t *>(smem_raw);        // [2][kPartChunk] keys
+    float *const s_val0 = reinterpret_cast<float *>(s_key0 + 2 * kPartChunk);  // [2][kPartChunk] values
+    uint16_t *const s_perm = reinterpret_cast<uint16_t *>(s_val0 + 2 * kPartChunk);  // [kPartChunk]
+    int32_t *const s_loc = reinterpret_cast<int32_t *>(s_perm + kPartChunk);        // [B]
+    int32_t *const s_dst = s_loc + B;                                                // [B]
+    __shared__ __align__(8) unsigned long long s_bar[2];
+    __shared__ int32_t s_part[NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t G = gridDim.x;
+    const auto whole = [&](int64_t c) { return (c + 1) * (int64_t)kPartChunk <= n; };
+    // thread 0: keys and values of chunk c into buffer `buf`
+    const auto issue = [&](int64_t c, int buf) {
+        fence_proxy_async_smem();
+        mbar_expect_tx(&s_bar[buf], 2u * kChunkBytes);
+        bulk_g2s(s_key0 + buf * kPartChunk, keys + c * kPartChunk, kChunkBytes, &s_bar[buf]);
+        bulk_g2s(s_val0 + buf * kPartChunk, vals + c * kPartChunk, kChunkBytes, &s_bar[buf]);
+    };
+    if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_init_fence();
+    }
+    for (int b = tid; b < B; b += kScatThreads) s_loc[b] = 0;
+    __syncthreads();
+    if (tid == 0 && (int64_t)blockIdx.x < nchunks && whole(blockIdx.x)) issue(blockIdx.x, 0);
+    uint32_t used0 = 0u, used1 = 0u;  // completed copy phases consumed, per buffer (same in every thread)
+    int j = 0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += G, ++j) {
+        const int buf = j & 1;
+        const int64_t cn = c + G;
+        const bool next_staged = cn < nchunks && whole(cn);
+        if (tid == 0 && next_staged) issue(cn, buf ^ 1);  // that buffer's readers passed the last barrier
+        int32_t *const sk = s_key0 + buf * kPartChunk;
+        float *const sv = s_val0 + buf * kPartChunk;
+        const int64_t e0 = c * kPartChunk;
+        const int len = (int)((n - e0) < kPartChunk ? (n - e0) : kPartChunk);
+        if (whole(c)) {
+            const uint32_t mine = buf ? used1 : used0, other = buf ? used0 : used1;
+            const bool ok = mbar_wait_bounded(&s_bar[buf], mine & 1u, spin_limit);
+            if (buf) ++used1;
+            else ++used0;
+            if (!__syncthreads_and(ok)) {
+                // give up: report, let the copy in flight into the other buffer land, leave
+                if (tid == 0) {
+                    set_error(err, kErrTimeout);
+                    if (next_staged) mbar_wait_bounded(&s_bar[buf ^ 1], other & 1u, spin_limit);
+                }
+                return;
+            }
+        } else {
+            for (int i = tid; i < len; i += kScatThreads) {
+                sk[i] = keys[e0 + i];
+                sv[i] = vals[e0 + i];
+            }
+            __syncthreads();
+        }
+
+        // this chunk's run starts of the thread's buckets in the scan below: loaded
+        // now, so that their latency hides behind the ranking
+        int32_t gofs[PER];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int b = tid * PER + q;
+            gofs[q] = b < B ? __ldg(offs + (int64_t)b * nchunks + c) : 0;
+        }
+
+        // rank every in-range element within its bucket
+        uint32_t bk[kScatItems];       // bucket << 16 | bin, or ~0u: absent or out of range
+        uint32_t rk2[kScatItems / 2];  // two 16-bit ranks per word
+#pragma unroll
+        for (int r = 0; r < kScatItems; ++r) {
+            const int i = r * kScatThreads + tid;
+            uint32_t rank = 0;
+            bk[r] = 0xffffffffu;
+            if (i < len) {
+                const int32_t k = sk[i];
+                if (in_range(k, m)) {
+                    const uint32_t b = bdiv((uint32_t)k);
+                    bk[r] = (b << 16) | ((uint32_t)k - b * bdiv.W);
+                    rank = (uint32_t)atomicAdd(&s_loc[b], 1);
+                }
+            }
+            if (r & 1) rk2[r >> 1] |= rank << 16;
+            else rk2[r >> 1] = rank;
+        }
+        __syncthreads();
+
+        // exclusive scan of the B bucket counts (PER consecutive buckets per thread)
+        int32_t own[PER], sum = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int b = tid * PER + q;
+            own[q] = b < B ? s_loc[b] : 0;
+            sum += own[q];
+        }
+        int32_t inc = sum;
+#pragma unroll
+        for (int o = 1; o < kWarp; o <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == kWarp - 1) s_part[warp] = inc;
+        __syncthreads();
+        int32_t before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const int32_t x = s_part[w];
+            if (w < warp) before += x;
+            total += x;
+        }
+        int32_t run = before + inc - sum;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int b = tid * PER + q;
+            if (b < B) {
+                s_loc[b] = run;
+                s_dst[b] = gofs[q] - run;
+                run += own[q];
+            }
+        }
+        __syncthreads();
+
+        // the permutation: position in bucket order -> element of the chunk
+#pragma unroll
+        for (int r = 0; r < kScatItems; ++r) {
+            if (bk[r] != 0xffffffffu) {
+                const uint32_t rank = (r & 1) ? (rk2[r >> 1] >> 16) : (rk2[r >> 1] & 0xffffu);
+                s_perm[s_loc[bk[r] >> 16] + (int)rank] = (uint16_t)(r * kScatThreads + tid);
+            }
+        }
+        __syncthreads();
+
+        // contiguous runs out; the bucket counters are cleared for the next chunk
+        for (int pos = tid; pos < total; pos += kScatThreads) {
+            const int i = s_perm[pos];
+            const uint32_t k = (uint32_t)sk[i];
+            const uint32_t b = bdiv(k);
+            const int64_t g = (int64_t)s_dst[b] + pos;
+            obin[g] = (uint16_t)(k - b * bdiv.W);
+            oval[g] = Tr::enc(sv[i], e0 + i);
+        }
+        for (int b = tid; b < B; b += kScatThreads) s_loc[b] = 0;
+        __syncthreads();
     }
 }
 
@@ -476,15 +682,27 @@ static adc_status part_run(int64_t n, int64_t m, const int32_t *keys, const T *v
     const int64_t nc = P.nchunks;
 
     const BucketDiv bdiv{P.W, P.inv};
-    k_part_count<<<(unsigned)nc, kPartThreads, (size_t)P.B * 4, s>>>(keys, n, m, bdiv, P.B, nc, counts);
+    {
+        const int64_t grid = nc < num_sms() ? nc : num_sms();
+        k_part_count_p<<<(unsigned)grid, kCountThreads, (size_t)P.B * 4, s>>>(keys, n, m, bdiv, P.B, nc, counts);
+    }
     adc_status st = check_launch();
     if (st != ADC_OK) return st;
     st = excl_scan_i32(counts, offs, (int64_t)(P.B + 1) * nc, ws, kPartSlot, w + L.scanreg, s);
     if (st != ADC_OK) return st;
-    const size_t sm_scatter = (size_t)kPartChunk * (sizeof(V) + 4) + (size_t)P.B * 8;
-    if (!smem_attr(k_part_scatter<T, MODE>, sm_scatter)) return ADC_ERR_CUDA;
-    k_part_scatter<T, MODE><<<(unsigned)nc, kPartThreads, sm_scatter, s>>>(keys, vals, n, m, bdiv, P.B, nc, offs, obin,
-                                                                          oval);
+    if constexpr (sizeof(T) == 4) {
+        // staged pipeline: 2 x (keys + values) + the permutation + the bucket arrays
+        const size_t sm_tma = (size_t)kPartChunk * (4 * 4 + 2) + (size_t)P.B * 8;
+        if (!smem_attr(k_part_scatter_tma<MODE>, sm_tma)) return ADC_ERR_CUDA;
+        const int64_t grid = nc < num_sms() ? nc : num_sms();
+        k_part_scatter_tma<MODE><<<(unsigned)grid, kScatThreads, sm_tma, s>>>(keys, vals, n, m, bdiv, P.B, nc, offs,
+                                                                             obin, oval, err, spin_limit());
+    } else {
+        const size_t sm_scatter = (size_t)kPartChunk * (sizeof(V) + 4) + (size_t)P.B * 8;
+        if (!smem_attr(k_part_scatter<T, MODE>, sm_scatter)) return ADC_ERR_CUDA;
+        k_part_scatter<T, MODE><<<(unsigned)nc, kPartThreads, sm_scatter, s>>>(keys, vals, n, m, bdiv, P.B, nc, offs,
+                                                                              obin, oval);
+    }
     if ((st = check_launch()) != ADC_OK) return st;
     const size_t sm_table = (size_t)P.W * Tr::kEntry;
     if (!smem_attr(k_part_table<T, MODE>, sm_table)) return ADC_ERR_CUDA;

@@ -19,6 +19,7 @@ constexpr int kMaxSlots = 48;
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 DevCtl make_ctl(void *ws, int slot);
+long long spin_limit();  // the polling bound of every device-side wait (adc_set_spin_limit)
 inline unsigned *counter_slot(void *ws, int slot) {
     return reinterpret_cast<unsigned *>(static_cast<char *>(ws) + 4 + 4 * slot);
 }
