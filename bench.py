@@ -38,20 +38,22 @@ METRIC = "vjp elements/s & % HBM roofline; AD overhead = vjp time / primal time"
 WORKLOAD = ("reduce_by_index specialisations fp32: n=50M uniform int32 bins, m in {31,401,50000,10M}, "
             "ops * (1% zeros), min, max (1024 levels); lifted forward + vjp per (op, m)")
 # DRAM bytes (read + write) per call measured by ncu on n = 20M, m = 10M and
-# scaled to n by the parts that grow with n (profiles/hist_partition_kernels_n20M_m10M.md):
-# the roofline's `traffic` for the dominant call, when it is one of these.
-TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.0, 106e6), ("fwd", "min", 10_000_000): (29.8, 128e6),
-                    ("fwd", "max", 10_000_000): (29.8, 128e6)}
+# scaled to n by the parts that grow with n, plus the m-sized outputs
+# (profiles/hist_partition_kernels_n20M_m10M.md): the roofline's `traffic`
+# for the dominant call, when it is one of these.
+TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.1, 120e6), ("fwd", "min", 10_000_000): (29.7, 80e6),
+                    ("fwd", "max", 10_000_000): (29.7, 80e6)}
 
 
 def launches(phase, op, m, n):
     """Our kernels launched by one call (csrc/hist.cu, hist_part.cu): the lifted
     forward is init + table kernel + finaliser, or, partitioned by bin range
-    (m >= 2^18), count + count scan + scatter + per-bucket tables + finaliser;
+    (m >= 2^18), count + count scan + scatter + per-bucket tables (which also
+    finalise);
     the * vjp is coefficient tables + gather; the min/max vjp is a zero-fill +
     scatter, or one gather pass when bins are sparse (8m > n)."""
     if phase == "fwd":
-        return 5 if m >= (1 << 18) else 3
+        return 4 if m >= (1 << 18) else 3
     if op == "mul":
         return 2
     return 1 if m * 8 > n else 2
@@ -558,7 +560,8 @@ def run_kernels(args):
     # the benchmark's reduce-by-index instances (n = 50M fp32): lifted forward, and the
     # min/max vjp in both of its forms
     if args.only is not None and args.only.startswith("bench"):
-        keys_h, vals_h, hbar_h = make_inputs(N)
+        NB = args.n
+        keys_h, vals_h, hbar_h = make_inputs(NB)
         for m in BINS:
             k = torch.from_numpy(keys_h[m]).to(dev)
             hb = torch.from_numpy(hbar_h[m]).to(dev)
@@ -568,11 +571,12 @@ def run_kernels(args):
                 v = torch.from_numpy(vals_h[op]).to(dev)
                 h, saved = adcomb.hist_fwd(op, m, k, v, ws=ws)
                 vb = torch.empty_like(v)
-                row(f"bench {op} m={m} fwd", N, 8 * N, timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
+                row(f"bench {op} m={m} fwd", NB, 8 * NB,
+                    timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
                 forms = [(1, "gather"), (2, "scatter")] if op != "mul" else [(0, "")]
                 for f, label in forms:
                     adcomb.debug_set_sel_vjp_form(f)
-                    row(f"bench {op} m={m} vjp {label}".strip(), N, (12 if op == "mul" else 4) * N,
+                    row(f"bench {op} m={m} vjp {label}".strip(), NB, (12 if op == "mul" else 4) * NB,
                         timeit(lambda: adcomb.hist_vjp(op, m, k, v, None, h, saved, hb, valsbar=vb, ws=ws)))
                 adcomb.debug_set_sel_vjp_form(0)
                 del v, vb

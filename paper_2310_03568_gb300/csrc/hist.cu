@@ -1017,9 +1017,9 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         int32_t *n0 = static_cast<int32_t *>(saved);
         T *p = reinterpret_cast<T *>(static_cast<char *>(saved) + align_up((size_t)m * 4, 16));
         if (st == kPart && n > 0) {
-            const adc_status r = part_fwd(kPMul, dt_of<T>(), n, m, keys, vals, h0, nullptr, n0, p, nullptr, ws,
-                                          part_off(op, dt_of<T>(), m), s);
-            if (r != ADC_OK) return r;
+            // the table blocks write n0, p and hist: no finaliser
+            return part_fwd(kPMul, dt_of<T>(), n, m, keys, vals, h0, hist, n0, p, nullptr, ws,
+                            part_off(op, dt_of<T>(), m), s);
         } else {
             k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
         }
@@ -1047,9 +1047,9 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
         int32_t *is = static_cast<int32_t *>(saved);
         if constexpr (sizeof(T) == 4) {
             if (st == kPart && n > 0) {
-                const adc_status r = part_fwd(mx ? kPMax : kPMin, ADC_F32, n, m, keys, vals, h0, nullptr, nullptr,
-                                              nullptr, tab, ws, part_off(op, ADC_F32, m), s);
-                if (r != ADC_OK) return r;
+                // the table blocks decode their bins into hist and is: no finaliser
+                return part_fwd(mx ? kPMax : kPMin, ADC_F32, n, m, keys, vals, h0, hist, nullptr, nullptr, is, ws,
+                                part_off(op, ADC_F32, m), s);
             } else {
                 if (mx) k_pack_init<true><<<gm, 256, 0, s>>>(tab, m);
                 else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);

@@ -58,7 +58,9 @@ template <typename T> struct PartOut {
     const T *h0;
     int32_t *n0;
     T *p;
-    unsigned long long *tab;
+    int32_t *is;     // lifted min/max: selected index per bin
+    const T *vals;   // lifted min/max: the input values (a selected zero's sign)
+    int64_t n;
 };
 
 // Order-preserving key type of a value type (un-lifted min/max).
@@ -110,8 +112,12 @@ template <typename T> struct PartTraits<T, kPMul> {
         }
     }
     static __device__ __forceinline__ void flush(const unsigned char *sm, int W, int t, int64_t j, const PartOut<T> &o) {
-        o.p[j] = reinterpret_cast<const T *>(sm)[t];
-        o.n0[j] = reinterpret_cast<const int32_t *>(sm + (size_t)W * sizeof(T))[t];
+        const T p = reinterpret_cast<const T *>(sm)[t];
+        const int32_t z = reinterpret_cast<const int32_t *>(sm + (size_t)W * sizeof(T))[t];
+        o.p[j] = p;
+        o.n0[j] = z;
+        const T xs = z > 0 ? T(0) : p;  // the bin's product (Fig. 3's lifted primal)
+        o.hist[j] = o.h0 ? o.h0[j] * xs : xs;
     }
 };
 
@@ -135,9 +141,28 @@ template <bool MAX> struct PartSel {
             else atomicMin(reinterpret_cast<V *>(sm) + u[j], v[j]);
         }
     }
+    // Decode the bin's key, fold hist0 in (it wins ties), write hist and is.
     static __device__ __forceinline__ void flush(const unsigned char *sm, int, int t, int64_t j,
                                                  const PartOut<float> &o) {
-        o.tab[j] = reinterpret_cast<const V *>(sm)[t];
+        const V key = reinterpret_cast<const V *>(sm)[t];
+        float v = MAX ? -Num<float>::inf() : Num<float>::inf();
+        int64_t idx = o.n;
+        if (key != Pack<MAX>::kEmpty) {
+            idx = Pack<MAX>::index(key);
+            // the key holds the value; only a zero needs the stored element
+            // (the key folds -0.0 onto +0.0)
+            v = from_ordered((uint32_t)(key >> 32));
+            if (v == 0.0f) v = o.vals[idx];
+        }
+        if (o.h0) {
+            const float a = o.h0[j];
+            if (MAX ? (a >= v) : (a <= v)) {
+                v = a;
+                idx = o.n;
+            }
+        }
+        o.hist[j] = v;
+        o.is[j] = (int32_t)idx;
     }
 };
 template <> struct PartTraits<float, kPMin> : PartSel<false> {};
@@ -211,63 +236,27 @@ __device__ __forceinline__ void load_group(const int32_t *__restrict__ keys, con
     }
 }
 
-// 1. counts[b * nchunks + chunk] = elements of the chunk in bucket b (row B is
-// a zero row, so that the scanned matrix also gives every bucket's end).  One
-// block per SM walks chunks b, b + G, ...: the next chunk's keys are loaded
-// into registers while this chunk's are counted in shared memory, and each
-// bucket counter is written out and cleared by one thread.
-constexpr int kCountThreads = 1024;
-constexpr int kCountVecs = kPartChunk / (4 * kCountThreads);  // int4 loads per thread per chunk (2)
-
-__device__ __forceinline__ void load_keys_vec(const int32_t *__restrict__ keys, int64_t e, int64_t n, int4 &k) {
-    if (e + 4 <= n) {
-        k = __ldcs(reinterpret_cast<const int4 *>(keys + e));
-    } else {
-        k.x = e < n ? keys[e] : -1;
-        k.y = e + 1 < n ? keys[e + 1] : -1;
-        k.z = e + 2 < n ? keys[e + 2] : -1;
-        k.w = e + 3 < n ? keys[e + 3] : -1;
-    }
-}
-
-__global__ void __launch_bounds__(kCountThreads)
-k_part_count_p(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const BucketDiv bdiv, const int B,
-               const int64_t nchunks, int32_t *__restrict__ counts) {
+// 1. counts[b * nchunks + chunk] = elements of the chunk in bucket b; row B is
+// a zero row so that the scanned matrix also gives every bucket's end.
+__global__ void __launch_bounds__(kPartThreads)
+k_part_count(const int32_t *__restrict__ keys, const int64_t n, const int64_t m, const BucketDiv bdiv, const int B,
+             const int64_t nchunks, int32_t *__restrict__ counts) {
     extern __shared__ int32_t s_cnt[];
-    const int tid = threadIdx.x;
-    const int64_t G = gridDim.x;
-    for (int b = tid; b < B; b += kCountThreads) s_cnt[b] = 0;
-    if (blockIdx.x == 0)  // the zero row B
-        for (int64_t c = tid; c < nchunks; c += kCountThreads) counts[(int64_t)B * nchunks + c] = 0;
-    int4 cur[kCountVecs];
-    const auto load = [&](int64_t c, int4 (&k)[kCountVecs]) {
-#pragma unroll
-        for (int r = 0; r < kCountVecs; ++r)
-            load_keys_vec(keys, c * kPartChunk + 4 * ((int64_t)r * kCountThreads + tid), n, k[r]);
-    };
-    if ((int64_t)blockIdx.x < nchunks) load(blockIdx.x, cur);
+    for (int b = threadIdx.x; b < B; b += kPartThreads) s_cnt[b] = 0;
     __syncthreads();
-    for (int64_t c = blockIdx.x; c < nchunks; c += G) {
-        int4 nxt[kCountVecs];
-        if (c + G < nchunks) load(c + G, nxt);
+    const int64_t c0 = (int64_t)blockIdx.x * kPartChunk;
 #pragma unroll
-        for (int r = 0; r < kCountVecs; ++r) {
-            const int kk[4] = {cur[r].x, cur[r].y, cur[r].z, cur[r].w};
+    for (int r = 0; r < kPartItems / 4; ++r) {
+        int32_t kk[4];
+        float unused[4];
+        load_group<float>(keys, nullptr, c0 + 4 * ((int64_t)r * kPartThreads + threadIdx.x), n, kk, unused);
 #pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (in_range(kk[q], m)) atomicAdd(&s_cnt[bdiv((uint32_t)kk[q])], 1);
-        }
-        __syncthreads();
-        for (int b = tid; b < B; b += kCountThreads) {
-            counts[(int64_t)b * nchunks + c] = s_cnt[b];
-            s_cnt[b] = 0;
-        }
-        __syncthreads();
-        if (c + G < nchunks) {
-#pragma unroll
-            for (int r = 0; r < kCountVecs; ++r) cur[r] = nxt[r];
-        }
+        for (int c = 0; c < 4; ++c)
+            if (in_range(kk[c], m)) atomicAdd(&s_cnt[bdiv((uint32_t)kk[c])], 1);
     }
+    __syncthreads();
+    for (int b = threadIdx.x; b <= B; b += kPartThreads)
+        counts[(int64_t)b * nchunks + blockIdx.x] = b < B ? s_cnt[b] : 0;
 }
 
 // 3. Counting sort of one chunk by bucket in shared memory, then contiguous
@@ -389,10 +378,11 @@ k_part_scatter(const int32_t *__restrict__ keys, const T *__restrict__ vals, con
 // whole chunk's keys and values arrive in shared memory by two bulk copies
 // issued one chunk ahead, so the DRAM reads of the next chunk overlap the
 // ranking, the bucket scan and the writes of this one.  The chunk is ranked
-// by bucket as above; a 16-bit permutation (bucket order -> element) takes
-// the place of the sorted payload copy, and the readout gathers key and value
-// from the staged chunk.  The ragged last chunk is loaded by plain loads.
+// by bucket as above; a permutation of (bucket, element) words in bucket
+// order takes the place of the sorted payload copy, and the readout gathers
+// key and value from the staged chunk.  The ragged last chunk is loaded by plain loads.
 constexpr int kScatThreads = 1024;
+static_assert(kPartChunk == (1 << 13), "the permutation word keeps the element in its low 13 bits");
 constexpr int kScatItems = kPartChunk / kScatThreads;  // 8 elements per thread
 
 template <int MODE>
@@ -405,10 +395,10 @@ k_part_scatter_tma(const int32_t *__restrict__ keys, const float *__restrict__ v
     constexpr int NW = kScatThreads / kWarp;
     constexpr int PER = kPartMaxBuckets / kScatThreads;  // buckets per thread in the local scan
     constexpr uint32_t kChunkBytes = kPartChunk * 4u;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];  // bulk copies need 16-byte alignment
     int32_t *const s_key0 = reinterpret_cast<int32_t *>(smem_raw);        // [2][kPartChunk] keys
     float *const s_val0 = reinterpret_cast<float *>(s_key0 + 2 * kPartChunk);  // [2][kPartChunk] values
-    uint16_t *const s_perm = reinterpret_cast<uint16_t *>(s_val0 + 2 * kPartChunk);  // [kPartChunk]
+    uint32_t *const s_perm = reinterpret_cast<uint32_t *>(s_val0 + 2 * kPartChunk);  // [kPartChunk] b << 13 | i
     int32_t *const s_loc = reinterpret_cast<int32_t *>(s_perm + kPartChunk);        // [B]
     int32_t *const s_dst = s_loc + B;                                                // [B]
     __shared__ __align__(8) unsigned long long s_bar[2];
@@ -528,23 +518,24 @@ k_part_scatter_tma(const int32_t *__restrict__ keys, const float *__restrict__ v
         }
         __syncthreads();
 
-        // the permutation: position in bucket order -> element of the chunk
+        // the permutation: position in bucket order -> (bucket, element of the chunk)
 #pragma unroll
         for (int r = 0; r < kScatItems; ++r) {
             if (bk[r] != 0xffffffffu) {
                 const uint32_t rank = (r & 1) ? (rk2[r >> 1] >> 16) : (rk2[r >> 1] & 0xffffu);
-                s_perm[s_loc[bk[r] >> 16] + (int)rank] = (uint16_t)(r * kScatThreads + tid);
+                const uint32_t b = bk[r] >> 16;
+                s_perm[s_loc[b] + (int)rank] = (b << 13) | (uint32_t)(r * kScatThreads + tid);
             }
         }
         __syncthreads();
 
         // contiguous runs out; the bucket counters are cleared for the next chunk
         for (int pos = tid; pos < total; pos += kScatThreads) {
-            const int i = s_perm[pos];
-            const uint32_t k = (uint32_t)sk[i];
-            const uint32_t b = bdiv(k);
-            const int64_t g = (int64_t)s_dst[b] + pos;
-            obin[g] = (uint16_t)(k - b * bdiv.W);
+            const uint32_t x = s_perm[pos];
+            const int i = (int)(x & (kPartChunk - 1));
+            const uint32_t b = x >> 13;
+            const int32_t g = s_dst[b] + pos;  // < n < 2^31
+            obin[g] = (uint16_t)((uint32_t)sk[i] - b * bdiv.W);
             oval[g] = Tr::enc(sv[i], e0 + i);
         }
         for (int b = tid; b < B; b += kScatThreads) s_loc[b] = 0;
@@ -682,17 +673,14 @@ static adc_status part_run(int64_t n, int64_t m, const int32_t *keys, const T *v
     const int64_t nc = P.nchunks;
 
     const BucketDiv bdiv{P.W, P.inv};
-    {
-        const int64_t grid = nc < num_sms() ? nc : num_sms();
-        k_part_count_p<<<(unsigned)grid, kCountThreads, (size_t)P.B * 4, s>>>(keys, n, m, bdiv, P.B, nc, counts);
-    }
+    k_part_count<<<(unsigned)nc, kPartThreads, (size_t)P.B * 4, s>>>(keys, n, m, bdiv, P.B, nc, counts);
     adc_status st = check_launch();
     if (st != ADC_OK) return st;
     st = excl_scan_i32(counts, offs, (int64_t)(P.B + 1) * nc, ws, kPartSlot, w + L.scanreg, s);
     if (st != ADC_OK) return st;
     if constexpr (sizeof(T) == 4) {
         // staged pipeline: 2 x (keys + values) + the permutation + the bucket arrays
-        const size_t sm_tma = (size_t)kPartChunk * (4 * 4 + 2) + (size_t)P.B * 8;
+        const size_t sm_tma = (size_t)kPartChunk * (4 * 4 + 4) + (size_t)P.B * 8;
         if (!smem_attr(k_part_scatter_tma<MODE>, sm_tma)) return ADC_ERR_CUDA;
         const int64_t grid = nc < num_sms() ? nc : num_sms();
         k_part_scatter_tma<MODE><<<(unsigned)grid, kScatThreads, sm_tma, s>>>(keys, vals, n, m, bdiv, P.B, nc, offs,
@@ -712,8 +700,8 @@ static adc_status part_run(int64_t n, int64_t m, const int32_t *keys, const T *v
 
 template <typename T>
 static adc_status part_fwd_t(int mode, int64_t n, int64_t m, const int32_t *keys, const T *vals, const T *h0, T *hist,
-                             int32_t *n0, T *p, unsigned long long *tab, void *ws, size_t ws_off, cudaStream_t s) {
-    const PartOut<T> out{hist, h0, n0, p, tab};
+                             int32_t *n0, T *p, int32_t *is, void *ws, size_t ws_off, cudaStream_t s) {
+    const PartOut<T> out{hist, h0, n0, p, is, vals, n};
     switch (mode) {
     case kPAdd: return part_run<T, kPAdd>(n, m, keys, vals, out, ws, ws_off, s);
     case kPMul: return part_run<T, kPMul>(n, m, keys, vals, out, ws, ws_off, s);
@@ -732,15 +720,15 @@ static adc_status part_fwd_t(int mode, int64_t n, int64_t m, const int32_t *keys
 }
 
 adc_status part_fwd(int mode, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
-                    const void *hist0, void *hist, int32_t *n0, void *p, unsigned long long *tab, void *ws,
-                    size_t ws_off, cudaStream_t s) {
+                    const void *hist0, void *hist, int32_t *n0, void *p, int32_t *is, void *ws, size_t ws_off,
+                    cudaStream_t s) {
     if (n <= 0) return ADC_ERR_INVALID_ARG;
     if (dt == ADC_F64)
         return part_fwd_t<double>(mode, n, m, keys, static_cast<const double *>(vals),
                                   static_cast<const double *>(hist0), static_cast<double *>(hist), n0,
-                                  static_cast<double *>(p), tab, ws, ws_off, s);
+                                  static_cast<double *>(p), is, ws, ws_off, s);
     return part_fwd_t<float>(mode, n, m, keys, static_cast<const float *>(vals), static_cast<const float *>(hist0),
-                             static_cast<float *>(hist), n0, static_cast<float *>(p), tab, ws, ws_off, s);
+                             static_cast<float *>(hist), n0, static_cast<float *>(p), is, ws, ws_off, s);
 }
 
 }  // namespace adc

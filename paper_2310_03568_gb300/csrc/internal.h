@@ -132,10 +132,11 @@ adc_status sop_hist_vjp(adc_dtype dt, int64_t n, int64_t m, const int32_t *keys,
 enum PartMode { kPAdd = 0, kPMul = 1, kPMin = 2, kPMax = 3, kPPrimMul = 4, kPPrimMin = 5, kPPrimMax = 6 };
 bool part_applicable(int mode, size_t s, int64_t m);
 size_t part_ws_bytes(int mode, size_t s, int64_t n, int64_t m);
-// Outputs: ADD and the primals write hist (hist0 folded in); MUL writes the
-// residuals n0, p; MIN/MAX write the packed key table `tab`.  n > 0.
+// Outputs: every mode writes hist (hist0 folded in); MUL also writes the
+// residuals n0, p; MIN/MAX (fp32) also the selected index per bin, `is` (n if
+// none, or if hist0 won).  n > 0.
 adc_status part_fwd(int mode, adc_dtype dt, int64_t n, int64_t m, const int32_t *keys, const void *vals,
-                    const void *hist0, void *hist, int32_t *n0, void *p, unsigned long long *tab, void *ws,
-                    size_t ws_off, cudaStream_t s);
+                    const void *hist0, void *hist, int32_t *n0, void *p, int32_t *is, void *ws, size_t ws_off,
+                    cudaStream_t s);
 
 }  // namespace adc
