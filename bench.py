@@ -47,13 +47,17 @@ TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.1, 120e6), ("fwd", "min", 10
 
 def launches(phase, op, m, n):
     """Our kernels launched by one call (csrc/hist.cu, hist_part.cu): the lifted
-    forward is init + table kernel + finaliser, or, partitioned by bin range
-    (m >= 2^18), count + count scan + scatter + per-bucket tables (which also
-    finalise);
+    forward is init + table kernel + finaliser (for * with per-thread or
+    per-warp tables: table kernel + cross-block reduce, which finalises), or,
+    partitioned by bin range (m >= 2^18), count + count scan + scatter +
+    per-bucket tables (which also finalise);
     the * vjp is coefficient tables + gather; the min/max vjp is a zero-fill +
     scatter, or one gather pass when bins are sparse (8m > n)."""
     if phase == "fwd":
-        return 4 if m >= (1 << 18) else 3
+        if m >= (1 << 18):
+            return 4
+        # * with per-thread or per-warp tables: table kernel + cross-block reduce
+        return 2 if op == "mul" and m * 8 * 8 <= 48 * 1024 else 3
     if op == "mul":
         return 2
     return 1 if m * 8 > n else 2

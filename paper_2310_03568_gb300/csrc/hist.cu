@@ -348,7 +348,7 @@ __global__ void k_mul_init(int32_t *__restrict__ n0, T *__restrict__ p, const in
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_hist_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
-                const int R, int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+                const int R, T *__restrict__ part_p, int32_t *__restrict__ part_z, unsigned *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sp = reinterpret_cast<T *>(smem_raw);
     int32_t *sz = reinterpret_cast<int32_t *>(sp + (int64_t)m * R);
@@ -364,6 +364,9 @@ k_hist_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, co
         else atomic_mul(sp + off + k, v, err);
     });
     __syncthreads();
+    // this block's partial table, combined across blocks by k_mul_reduce
+    T *P = part_p + (int64_t)blockIdx.x * m;
+    int32_t *Z = part_z + (int64_t)blockIdx.x * m;
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
         T prod = T(1);
         int32_t z = 0;
@@ -371,8 +374,8 @@ k_hist_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, co
             prod *= sp[(int64_t)r * m + j];
             z += sz[(int64_t)r * m + j];
         }
-        if (z) atomicAdd(n0 + j, z);
-        if (prod != T(1)) atomic_mul(p + j, prod, err);
+        P[j] = prod;
+        Z[j] = z;
     }
 }
 
@@ -393,11 +396,11 @@ __global__ void k_hist_mul_global(const int32_t *__restrict__ keys, const T *__r
 }
 
 // One block-wide shared table of products (up to ~200 KB); the rare zeros go
-// straight to the global zero counts.
+// straight to the global zero counts, the products to this block's partial row.
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_hist_mul_smem_prod(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
-                     int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+                     int32_t *__restrict__ n0, T *__restrict__ part_p, unsigned *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sp = reinterpret_cast<T *>(smem_raw);
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x) sp[j] = T(1);
@@ -408,8 +411,8 @@ k_hist_mul_smem_prod(const int32_t *__restrict__ keys, const T *__restrict__ val
         else atomic_mul(sp + k, v, err);
     });
     __syncthreads();
-    for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
-        if (sp[j] != T(1)) atomic_mul(p + j, sp[j], err);
+    T *P = part_p + (int64_t)blockIdx.x * m;  // combined across blocks by k_mul_reduce
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) P[j] = sp[j];
 }
 
 // ------------------------------------------------- per-thread private tables --
@@ -421,7 +424,7 @@ constexpr int kThrThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kThrThreads)
 k_hist_mul_thread(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
-                  int32_t *__restrict__ n0, T *__restrict__ p, unsigned *__restrict__ err) {
+                  T *__restrict__ part_p, int32_t *__restrict__ part_z, unsigned *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sp = reinterpret_cast<T *>(smem_raw);
     int32_t *sz = reinterpret_cast<int32_t *>(sp + m * kThrThreads);
@@ -452,8 +455,8 @@ k_hist_mul_thread(const int32_t *__restrict__ keys, const T *__restrict__ vals, 
             z += __shfl_xor_sync(0xffffffffu, z, o);
         }
         if (lane == 0) {
-            if (z) atomicAdd(n0 + j, z);
-            if (prod != T(1)) atomic_mul(p + j, prod, err);
+            part_p[(int64_t)blockIdx.x * m + j] = prod;
+            part_z[(int64_t)blockIdx.x * m + j] = z;
         }
     }
 }
@@ -522,6 +525,50 @@ __global__ void k_hist_mul_final(const int32_t *__restrict__ n0, const T *__rest
     }
 }
 
+// The per-block partial tables of the shared-memory * strategies, combined
+// per bin in block order (deterministic, no global compare-and-swap): P[g][j]
+// products and, for the lifted form, Z[g][j] zero counts (or, when Z is null,
+// the zero counts already accumulated in n0).  32 bins per block across the
+// lanes (coalesced rows), the G partials split over the 32 warps, then the
+// warps' results combined in warp order.  Writes n0, p and hist (lifted:
+// hist = hist0 * (n0 ? 0 : p)), or hist = hist0 * product (original primal,
+// n0 == p == null).
+template <typename T>
+__global__ void __launch_bounds__(1024)
+k_mul_reduce(const T *__restrict__ P, const int32_t *__restrict__ Z, const int G, const int64_t m,
+             int32_t *__restrict__ n0, T *__restrict__ p, const T *__restrict__ h0, T *__restrict__ hist) {
+    __shared__ T s_p[32][33];
+    __shared__ int32_t s_z[32][33];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    T prod = T(1);
+    int32_t z = 0;
+    if (j < m) {
+        for (int g = w; g < G; g += 32) {
+            prod *= P[(int64_t)g * m + j];
+            if (Z) z += Z[(int64_t)g * m + j];
+        }
+    }
+    s_p[w][lane] = prod;
+    s_z[w][lane] = z;
+    __syncthreads();
+    if (w == 0 && j < m) {
+        T q = T(1);
+        int32_t zz = (Z == nullptr && n0 != nullptr) ? n0[j] : 0;
+        for (int u = 0; u < 32; ++u) {
+            q *= s_p[u][lane];
+            zz += s_z[u][lane];
+        }
+        T xs = q;
+        if (p != nullptr) {
+            n0[j] = zz;
+            p[j] = q;
+            xs = zz > 0 ? T(0) : q;
+        }
+        hist[j] = h0 ? h0[j] * xs : xs;
+    }
+}
+
 // =================================================== original primals ==
 // The un-lifted primal of Sec. 4 (the program being differentiated): the
 // plain product per bin (zeros included) and the plain min/max value.  Used
@@ -529,7 +576,7 @@ __global__ void k_hist_mul_final(const int32_t *__restrict__ n0, const T *__rest
 template <typename T>
 __global__ void __launch_bounds__(1024)
 k_prim_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
-                const int R, T *__restrict__ hist, unsigned *__restrict__ err) {
+                const int R, T *__restrict__ part_p, unsigned *__restrict__ err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sp = reinterpret_cast<T *>(smem_raw);
     for (int64_t j = threadIdx.x; j < m * R; j += blockDim.x) sp[j] = T(1);
@@ -539,10 +586,11 @@ k_prim_mul_smem(const int32_t *__restrict__ keys, const T *__restrict__ vals, co
         if (in_range(k, m)) atomic_mul(mine + k, v, err);
     });
     __syncthreads();
+    T *P = part_p + (int64_t)blockIdx.x * m;  // combined across blocks by k_mul_reduce
     for (int64_t j = threadIdx.x; j < m; j += blockDim.x) {
         T prod = T(1);
         for (int r = 0; r < R; ++r) prod *= sp[(int64_t)r * m + j];
-        if (prod != T(1)) atomic_mul(hist + j, prod, err);
+        P[j] = prod;
     }
 }
 
@@ -865,12 +913,38 @@ template <typename K> static bool set_smem(K kernel, size_t smem) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess;
 }
 
+static HistStrategy pick_entry(adc_op op, size_t s, size_t e, int64_t m, int *R);
+
+// Partial tables of the shared-memory * strategies (one row of m products, and
+// for the lifted form m zero counts, per block), at the workspace's start: the
+// lifted forward's strategy and the original primal's, whichever is larger.
+static size_t mul_partial_p(size_t s, int64_t G, int64_t m) { return align_up((size_t)G * m * s, 256); }
+static size_t mul_partial_bytes(size_t s, int64_t m) {
+    size_t b = 0;
+    const HistStrategy st = pick(ADC_OP_MUL, s, m);
+    if (st == kSmemThread || st == kSmemWarp || st == kSmemBlock) {
+        const int64_t G = shape(ADC_OP_MUL, s, st, m, 0).grid;
+        b = mul_partial_p(s, G, m) + align_up((size_t)G * m * 4, 256);
+    }
+    int R;
+    const HistStrategy sp = pick_entry(ADC_OP_MUL, s, s, m, &R);
+    if (sp == kSmemWarp || sp == kSmemBlock) {
+        const size_t c = mul_partial_p(s, sp == kSmemWarp ? (int64_t)num_sms() * 4 : (int64_t)num_sms(), m);
+        b = c > b ? c : b;
+    }
+    return b;
+}
+
 // Workspace: the header, the operator's tables, then (where the partitioned
 // strategy can run) its scratch at part_off().
 static size_t base_ws(adc_op op, adc_dtype dt, int64_t m) {
     switch (op) {
     case ADC_OP_ADD: return kWsHeader;
-    case ADC_OP_MUL: return kWsHeader + 2 * align_up((size_t)m * 8, 256);
+    case ADC_OP_MUL: {
+        const size_t vjp_tables = 2 * align_up((size_t)m * 8, 256);
+        const size_t partials = mul_partial_bytes(dt == ADC_F64 ? 8 : 4, m);
+        return kWsHeader + (vjp_tables > partials ? vjp_tables : partials);
+    }
     case ADC_OP_MIN:
     case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
     default: return 0;
@@ -932,19 +1006,20 @@ static adc_status hist_primal_t(adc_op op, int64_t n, int64_t m, const int32_t *
         if (st == kPart && n > 0)
             return part_fwd(kPPrimMul, dt, n, m, keys, vals, h0, hist, nullptr, nullptr, nullptr, ws,
                             part_off(op, dt, m), s);
-        k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(1));
-        if (n > 0) {
-            if (st == kGlobal) {
-                k_prim_mul_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, hist, err);
-            } else {
-                const size_t smem = (size_t)m * sizeof(T) * R;
-                if (cudaFuncSetAttribute(k_prim_mul_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-                    cudaSuccess)
-                    return ADC_ERR_CUDA;
-                k_prim_mul_smem<T><<<st == kSmemWarp ? num_sms() * 4 : num_sms(), st == kSmemWarp ? 256 : 1024, smem,
-                                     s>>>(keys, vals, n, m, R, hist, err);
-            }
+        if (n == 0 || st == kGlobal) {
+            k_hist_init<T><<<gm, 256, 0, s>>>(hist, h0, m, T(1));
+            if (n > 0) k_prim_mul_global<T><<<gglob, 256, 0, s>>>(keys, vals, n, m, hist, err);
+            return check_launch();
         }
+        // shared-memory strategies: per-block partial rows, combined by k_mul_reduce
+        const size_t smem = (size_t)m * sizeof(T) * R;
+        if (cudaFuncSetAttribute(k_prim_mul_smem<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess)
+            return ADC_ERR_CUDA;
+        const int G = st == kSmemWarp ? num_sms() * 4 : num_sms();
+        T *P = reinterpret_cast<T *>(w + kWsHeader);
+        k_prim_mul_smem<T><<<G, st == kSmemWarp ? 256 : 1024, smem, s>>>(keys, vals, n, m, R, P, err);
+        k_mul_reduce<T><<<(unsigned)((m + 31) / 32), 1024, 0, s>>>(P, nullptr, G, m, nullptr, nullptr, h0, hist);
         return check_launch();
     }
     const bool mx = op == ADC_OP_MAX;
@@ -1020,24 +1095,31 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
             // the table blocks write n0, p and hist: no finaliser
             return part_fwd(kPMul, dt_of<T>(), n, m, keys, vals, h0, hist, n0, p, nullptr, ws,
                             part_off(op, dt_of<T>(), m), s);
-        } else {
-            k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
         }
-        if (n > 0 && st != kPart) {
+        // shared-memory strategies: per-block partial rows, combined by k_mul_reduce
+        const bool partial = n > 0 && (st == kSmemThread || st == kSmemWarp || st == kSmemBlock);
+        T *P = reinterpret_cast<T *>(w + kWsHeader);
+        int32_t *Z = reinterpret_cast<int32_t *>(w + kWsHeader + mul_partial_p(sizeof(T), L.grid, m));
+        if (!partial || st == kSmemBlock) k_mul_init<T><<<gm, 256, 0, s>>>(n0, p, m);
+        if (n > 0) {
             if (st == kGlobal) {
                 k_hist_mul_global<T><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, n0, p, err);
             } else if (st == kSmemThread) {
                 if (!set_smem(k_hist_mul_thread<T>, L.smem)) return ADC_ERR_CUDA;
-                k_hist_mul_thread<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, n0, p, err);
+                k_hist_mul_thread<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, P, Z, err);
             } else if (st == kSmemBlock) {
                 if (!set_smem(k_hist_mul_smem_prod<T>, L.smem)) return ADC_ERR_CUDA;
-                k_hist_mul_smem_prod<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, n0, p, err);
+                k_hist_mul_smem_prod<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, n0, P, err);
             } else {
                 if (!set_smem(k_hist_mul_smem<T>, L.smem)) return ADC_ERR_CUDA;
-                k_hist_mul_smem<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, 8, n0, p, err);
+                k_hist_mul_smem<T><<<L.grid, L.block, L.smem, s>>>(keys, vals, n, m, 8, P, Z, err);
             }
         }
-        k_hist_mul_final<T><<<gm, 256, 0, s>>>(n0, p, h0, m, hist);
+        if (partial)
+            k_mul_reduce<T><<<(unsigned)((m + 31) / 32), 1024, 0, s>>>(P, st == kSmemBlock ? nullptr : Z, (int)L.grid,
+                                                                       m, n0, p, h0, hist);
+        else
+            k_hist_mul_final<T><<<gm, 256, 0, s>>>(n0, p, h0, m, hist);
         return check_launch();
     }
     case ADC_OP_MIN:
