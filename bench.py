@@ -577,6 +577,13 @@ def run_kernels(args):
                 vb = torch.empty_like(v)
                 row(f"bench {op} m={m} fwd", NB, 8 * NB,
                     timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
+                if op != "mul" and 200 * 1024 < m * 8 <= 8 * 200 * 1024:
+                    for strat, label in [(2, "global"), (6, "cluster")]:
+                        adcomb.debug_force_hist_strategy(strat)
+                        ws.get(adcomb.workspace_bytes("hist", op, torch.float32, NB, m), dev)
+                        row(f"bench {op} m={m} fwd [{label}]", NB, 8 * NB,
+                            timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
+                    adcomb.debug_force_hist_strategy(-1)
                 forms = [(1, "gather"), (2, "scatter")] if op != "mul" else [(0, "")]
                 for f, label in forms:
                     adcomb.debug_set_sel_vjp_form(f)

@@ -28,7 +28,7 @@ _cache = None
 
 BATCHED_CHUNKS = (1 << 14, 1 << 16, 1 << 18)
 BATCHED_SMEM_BINS = (4096, 8192, 16384)
-HIST_STRATEGIES = (3, 0, 1, 2, 4, 5)  # per-thread, per-warp, per-block, global, partitioned, split tables
+HIST_STRATEGIES = (3, 0, 1, 2, 4, 5, 6)  # per-thread, per-warp, per-block, global, partitioned, split, cluster
 
 
 def cache_path():

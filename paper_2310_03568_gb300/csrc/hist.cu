@@ -9,6 +9,11 @@
 //   SPLIT     : lifted min/max tables of 2-4 block tables: S blocks read the
 //               same elements, each owns 1/S of the bins in its shared
 //               memory, then flushes them (filtered global atomics).
+//   CLUSTER   : lifted fp32 min/max tables of 2-8 block tables: the table is
+//               spread over the blocks of a thread-block cluster, each element
+//               is read once and updates its bin in the owning block's shared
+//               memory (local or distributed); each cluster's table is written
+//               as a partial row and the rows are reduced per bin.
 //   PART      : for tables beyond shared memory: the elements are first
 //               partitioned by bin range so that every range's bins fit one
 //               block's shared memory (hist_part.cu) -- no global atomics.
@@ -33,10 +38,11 @@
 #include "hist_common.cuh"
 #include "internal.h"
 #include "tile_io.cuh"
+#include "tma.cuh"
 
 namespace adc {
 
-enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4, kSplit = 5 };
+enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4, kSplit = 5, kCluster = 6 };
 
 // ------------------------------------------------------------ element loop --
 // Calls f(key, value, index) for every element, grid-stride over 4-element
@@ -213,6 +219,129 @@ __global__ void k_hist_sel_global(const int32_t *__restrict__ keys, const float 
             }
         }
     });
+}
+
+// CLUSTER: the table is spread over the CS blocks of a cluster, block r owning
+// bins [r*H, r*H + H); every element is read once (the grid strides over all
+// of them) and its packed key goes to the owning block's shared memory through
+// the cluster's shared window: a read of the current key, then, while it can
+// win, a compare-and-swap.
+// After a cluster barrier each block writes its bins to the cluster's partial
+// row; k_sel_reduce combines the rows.
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Address of the same shared-memory offset in block `rank` of the cluster.
+__device__ __forceinline__ uint32_t cluster_map(uint32_t local, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ unsigned long long cluster_ld_u64(uint32_t addr) {
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long cluster_cas_u64(uint32_t addr, unsigned long long expect,
+                                                          unsigned long long val) {
+    unsigned long long prev;
+    asm volatile("atom.shared::cluster.cas.b64 %0, [%1], %2, %3;" : "=l"(prev) : "r"(addr), "l"(expect), "l"(val)
+                 : "memory");
+    return prev;
+}
+// The lifted min/max update of a bin in a cluster block's table, as a
+// compare-and-swap loop from the key read just before (bounded; a give-up
+// sets the error word).  64-bit min/max atomics on distributed shared memory
+// were measured to lose updates on this part (min.u64 / max.u64 with red and
+// with atom), so the update is built on the compare-and-swap, which did not.
+template <bool MAX>
+__device__ __forceinline__ void cluster_update(uint32_t addr, unsigned long long k, unsigned long long cur,
+                                               unsigned *err) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        if (!Pack<MAX>::better(k, cur)) return;
+        const unsigned long long prev = cluster_cas_u64(addr, cur, k);
+        if (prev == cur) return;
+        cur = prev;
+    }
+    set_error(err, kErrCasLimit);
+}
+
+constexpr int kMaxClusterBlocks = 8;
+
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_hist_sel_cluster(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                   const int CS, const int64_t H, unsigned long long *__restrict__ rows, unsigned *__restrict__ err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long *sh = reinterpret_cast<unsigned long long *>(smem_raw);
+    const uint32_t rank = cluster_rank();
+    const int64_t lo = (int64_t)rank * H;
+    const int64_t w = (m - lo) < H ? (m - lo) : H;
+    for (int64_t j = threadIdx.x; j < H; j += blockDim.x) sh[j] = Pack<MAX>::kEmpty;
+    uint32_t base[kMaxClusterBlocks];
+    const uint32_t mine = smem_u32(sh);
+#pragma unroll
+    for (int q = 0; q < kMaxClusterBlocks; ++q) base[q] = q < CS ? cluster_map(mine, (uint32_t)q) : 0u;
+    cluster_barrier();  // every block's table is initialised before anyone writes into it
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
+        if (!in_range(k, m)) return;
+        const uint32_t owner = (uint32_t)((int64_t)k / H);
+        uint32_t b = base[0];
+#pragma unroll
+        for (int q = 1; q < kMaxClusterBlocks; ++q)
+            if ((uint32_t)q == owner) b = base[q];
+        const uint32_t addr = b + (uint32_t)(((int64_t)k - (int64_t)owner * H) * 8);
+        cluster_update<MAX>(addr, Pack<MAX>::key(v, i), cluster_ld_u64(addr), err);
+    });
+    cluster_barrier();  // all updates, local and remote, have landed
+    unsigned long long *row = rows + (int64_t)(blockIdx.x / CS) * m + lo;
+    for (int64_t j = threadIdx.x; j < w; j += blockDim.x) row[j] = sh[j];
+}
+
+// Per bin, the best key over the C partial rows (in row order), decoded with
+// hist0 folded in as in k_hist_sel_final: 32 bins per block across the lanes,
+// the rows split over the 32 warps.
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_sel_reduce(const unsigned long long *__restrict__ rows, const int C, const int64_t m,
+             const float *__restrict__ vals, const float *__restrict__ h0, const int64_t n,
+             float *__restrict__ hist, int32_t *__restrict__ is) {
+    __shared__ unsigned long long s_k[32][33];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    unsigned long long best = Pack<MAX>::kEmpty;
+    if (j < m)
+        for (int c = wp; c < C; c += 32) {
+            const unsigned long long k = rows[(int64_t)c * m + j];
+            if (Pack<MAX>::better(k, best)) best = k;
+        }
+    s_k[wp][lane] = best;
+    __syncthreads();
+    if (wp == 0 && j < m) {
+        for (int u = 1; u < 32; ++u)
+            if (Pack<MAX>::better(s_k[u][lane], best)) best = s_k[u][lane];
+        float v = MAX ? -Num<float>::inf() : Num<float>::inf();
+        int64_t idx = n;
+        if (best != Pack<MAX>::kEmpty) {
+            idx = Pack<MAX>::index(best);
+            v = from_ordered((uint32_t)(best >> 32));
+            if (v == 0.0f) v = vals[idx];  // the key folds -0.0 onto +0.0
+        }
+        if (h0) {
+            const float a = h0[j];
+            if (MAX ? (a >= v) : (a <= v)) {
+                v = a;
+                idx = n;
+            }
+        }
+        hist[j] = v;
+        is[j] = (int32_t)idx;
+    }
 }
 
 // SPLIT: blocks come in groups of S that read the same elements; block p of a
@@ -872,6 +1001,9 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
     case kSplit:
         return (op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 4 && (size_t)m * 8 > kBlockBudget &&
                (size_t)m * 8 <= 4 * kBlockBudget;
+    case kCluster:
+        return (op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 4 && (size_t)m * 8 > kBlockBudget &&
+               (size_t)m * 8 <= (size_t)kMaxClusterBlocks * kBlockBudget;
     default: return true;
     }
 }
@@ -880,14 +1012,15 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
 // always uses the two global phases.
 static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
-    if (g_force_strategy >= 0 && g_force_strategy <= 5 && fits(op, s, (HistStrategy)g_force_strategy, m))
+    if (g_force_strategy >= 0 && g_force_strategy <= 6 && fits(op, s, (HistStrategy)g_force_strategy, m))
         return (HistStrategy)g_force_strategy;
     // min/max updates are rare after the first few values of a bin (a read
     // filters them), so per-warp copies beat per-thread tables there: the
     // latter's larger footprint costs occupancy.
     const bool select = op == ADC_OP_MIN || op == ADC_OP_MAX;
-    // (SPLIT is not chosen automatically: at m = 50,000 it measured no faster
-    // than the filtered global atomics.)
+    // (SPLIT and CLUSTER are not chosen automatically: at m = 50,000 they
+    // measured no faster than the filtered global atomics -- 0.40 ms for
+    // CLUSTER against 0.28 ms.)
     for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
         if (!(select && st == kSmemThread) && fits(op, s, st, m)) return st;
     if (m >= kPartMinBins && fits(op, s, kPart, m)) return kPart;
@@ -914,6 +1047,11 @@ template <typename K> static bool set_smem(K kernel, size_t smem) {
 }
 
 static HistStrategy pick_entry(adc_op op, size_t s, size_t e, int64_t m, int *R);
+
+// CLUSTER: blocks per cluster, bins per block, and the partial rows (at most
+// one cluster per two SMs).
+static int cluster_blocks(int64_t m) { return (int)(((size_t)m * 8 + kBlockBudget - 1) / kBlockBudget); }
+static size_t cluster_rows_bytes(int64_t m) { return (size_t)(num_sms() / 2) * (size_t)m * 8; }
 
 // Partial tables of the shared-memory * strategies (one row of m products, and
 // for the lifted form m zero counts, per block), at the workspace's start: the
@@ -946,7 +1084,13 @@ static size_t base_ws(adc_op op, adc_dtype dt, int64_t m) {
         return kWsHeader + (vjp_tables > partials ? vjp_tables : partials);
     }
     case ADC_OP_MIN:
-    case ADC_OP_MAX: return kWsHeader + (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
+    case ADC_OP_MAX: {
+        const size_t tab = (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
+        // (CLUSTER is not chosen automatically: its rows only when it is forced)
+        const size_t rows =
+            dt == ADC_F32 && g_force_strategy == kCluster && fits(op, 4, kCluster, m) ? cluster_rows_bytes(m) : 0;
+        return kWsHeader + (tab > rows ? tab : rows);
+    }
     default: return 0;
     }
 }
@@ -1140,6 +1284,36 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
                 if (st == kGlobal) {
                     if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
                     else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
+                } else if (st == kCluster) {
+                    const int CS = cluster_blocks(m);
+                    const int64_t H = (m + CS - 1) / CS;
+                    const size_t smem = (size_t)H * 8;
+                    auto kern = mx ? k_hist_sel_cluster<true> : k_hist_sel_cluster<false>;
+                    if (!set_smem(kern, smem)) return ADC_ERR_CUDA;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeClusterDimension;
+                    attr[0].val.clusterDim.x = (unsigned)CS;
+                    attr[0].val.clusterDim.y = 1;
+                    attr[0].val.clusterDim.z = 1;
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.blockDim = dim3(1024);
+                    cfg.dynamicSmemBytes = smem;
+                    cfg.stream = s;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    cfg.gridDim = dim3((unsigned)((num_sms() / CS) * CS));
+                    // one wave of clusters: as many as can be resident at once
+                    int active = 0;
+                    if (cudaOccupancyMaxActiveClusters(&active, kern, &cfg) != cudaSuccess || active < 1)
+                        return ADC_ERR_CUDA;
+                    const int C = active < num_sms() / CS ? active : num_sms() / CS;
+                    cfg.gridDim = dim3((unsigned)(C * CS));
+                    unsigned long long *rows = tab;  // the rows take the packed table's place
+                    if (cudaLaunchKernelEx(&cfg, kern, keys, vals, n, m, CS, H, rows, err) != cudaSuccess)
+                        return ADC_ERR_CUDA;
+                    auto red = mx ? k_sel_reduce<true> : k_sel_reduce<false>;
+                    red<<<(unsigned)((m + 31) / 32), 1024, 0, s>>>(rows, C, m, vals, h0, n, hist, is);
+                    return check_launch();
                 } else if (st == kSplit) {
                     const int S = (int)(((size_t)m * 8 + kBlockBudget - 1) / kBlockBudget);
                     const int64_t W = (m + S - 1) / S;

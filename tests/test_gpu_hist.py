@@ -56,7 +56,7 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2, 3, 4, 5]  # auto, per-warp, per-block, global, per-thread, partitioned, split tables
+STRATS = [-1, 0, 1, 2, 3, 4, 5, 6]  # auto, per-warp, per-block, global, per-thread, partitioned, split, cluster
 
 
 def fits(op, dt, m, s):
@@ -69,6 +69,8 @@ def fits(op, dt, m, s):
         return True
     if s == 5:  # lifted fp32 min/max whose packed table needs 2-4 block tables
         return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 4 * 200 * 1024
+    if s == 6:  # the same spread over the blocks of a 2-8 block cluster
+        return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 8 * 200 * 1024
     e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
     if s == 3:
         return m * e * 256 <= 64 * 1024
@@ -362,3 +364,30 @@ def test_hist_sel_vjp_forms(op, dt):
                 assert np.array_equal(host(vb2), (old + ref.astype(dt)).astype(dt)), (n, m, form)
     finally:
         adcomb.debug_set_sel_vjp_form(0)
+
+
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_hist_sel_cluster_sizes(op):
+    """Lifted fp32 min/max with the table spread over clusters of 2 to 8 blocks
+    (distributed shared memory), forward and vjp bit-exact against the oracle,
+    with and without hist0, with exact ties everywhere (64 value levels)."""
+    g = np.random.default_rng(71)
+    try:
+        adcomb.debug_force_hist_strategy(6)
+        for n, m in [(1, 25_601), (200_003, 30_000), (500_001, 50_000), (400_003, 120_007), (300_001, 204_800)]:
+            k = keys_oor(g, n, m)
+            v = ((g.integers(0, 64, n) - 32) / 8.0).astype(np.float32)
+            h0 = ((g.integers(0, 64, m) - 40) / 8.0).astype(np.float32)
+            hb = synth.normal(g, m, np.float32)
+            for hist0 in (None, h0):
+                h, saved = adcomb.hist_fwd(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0))
+                ref, idx = oracle.hist_fwd(op, m, k, v, hist0)
+                assert np.array_equal(host(h), ref.astype(np.float32)), (n, m)
+                assert np.array_equal(host(saved.view(torch.int32))[:m], idx.astype(np.int32)), (n, m)
+                vb, h0b = adcomb.hist_vjp(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0), h, saved,
+                                          dev(hb), want_hist0bar=True)
+                vr, h0r = oracle.hist_vjp(op, m, k, v, hb, hist0)
+                assert np.array_equal(host(vb), vr.astype(np.float32)), (n, m)
+                assert np.array_equal(host(h0b), h0r.astype(np.float32)), (n, m)
+    finally:
+        adcomb.debug_force_hist_strategy(-1)
