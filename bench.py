@@ -48,7 +48,8 @@ TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.1, 120e6), ("fwd", "min", 10
 def launches(phase, op, m, n):
     """Our kernels launched by one call (csrc/hist.cu, hist_part.cu): the lifted
     forward is init + table kernel + finaliser (for * with per-thread or
-    per-warp tables: table kernel + cross-block reduce, which finalises), or,
+    per-warp tables: table kernel + cross-block reduce, which finalises; for
+    min/max in two passes: value rows + row reduce + index pass + decode), or,
     partitioned by bin range (m >= 2^18), count + count scan + scatter +
     per-bucket tables (which also finalise);
     the * vjp is coefficient tables + gather; the min/max vjp is a zero-fill +
@@ -57,7 +58,11 @@ def launches(phase, op, m, n):
         if m >= (1 << 18):
             return 4
         # * with per-thread or per-warp tables: table kernel + cross-block reduce
-        return 2 if op == "mul" and m * 8 * 8 <= 48 * 1024 else 3
+        if op == "mul":
+            return 2 if m * 8 * 8 <= 48 * 1024 else 3
+        # min/max whose packed table exceeds a block but whose values fit:
+        # value rows + row reduce + index pass + decode
+        return 4 if m * 8 > 200 * 1024 and m * 4 <= 200 * 1024 else 3
     if op == "mul":
         return 2
     return 1 if m * 8 > n else 2
@@ -578,7 +583,7 @@ def run_kernels(args):
                 row(f"bench {op} m={m} fwd", NB, 8 * NB,
                     timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
                 if op != "mul" and 200 * 1024 < m * 8 <= 8 * 200 * 1024:
-                    for strat, label in [(2, "global"), (6, "cluster")]:
+                    for strat, label in [(2, "global"), (6, "cluster"), (7, "two passes")]:
                         adcomb.debug_force_hist_strategy(strat)
                         ws.get(adcomb.workspace_bytes("hist", op, torch.float32, NB, m), dev)
                         row(f"bench {op} m={m} fwd [{label}]", NB, 8 * NB,

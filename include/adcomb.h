@@ -421,7 +421,8 @@ void adc_debug_set_scan_range_tiles(int tiles);
  * 2: global atomics, 3: per-thread shared-memory tables, 4: partition by bin
  * range into shared-memory-sized buckets, 5: lifted fp32 min/max split over
  * 2-4 block tables, 6: lifted fp32 min/max spread over the shared memory of a
- * 2-8 block cluster) where the histogram fits it; -1
+ * 2-8 block cluster, 7: lifted fp32 min/max by per-block value tables and an
+ * index pass) where the histogram fits it; -1
  * (default) chooses automatically from m and the operator.  The choice also
  * applies to the original primal (saved == NULL).
  */

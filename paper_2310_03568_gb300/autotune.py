@@ -28,7 +28,8 @@ _cache = None
 
 BATCHED_CHUNKS = (1 << 14, 1 << 16, 1 << 18)
 BATCHED_SMEM_BINS = (4096, 8192, 16384)
-HIST_STRATEGIES = (3, 0, 1, 2, 4, 5, 6)  # per-thread, per-warp, per-block, global, partitioned, split, cluster
+HIST_STRATEGIES = (3, 0, 1, 2, 4, 5, 6, 7)  # per-thread, per-warp, per-block, global, partitioned, split,
+                                          # cluster, two passes
 
 
 def cache_path():

@@ -14,6 +14,10 @@
 //               is read once and updates its bin in the owning block's shared
 //               memory (local or distributed); each cluster's table is written
 //               as a partial row and the rows are reduced per bin.
+//   TWOPASS   : lifted fp32 min/max whose packed table exceeds one block but
+//               whose 32-bit value table does not: per-block value tables
+//               written as partial rows and reduced per bin, then a second
+//               pass finds the lowest index holding each bin's value.
 //   PART      : for tables beyond shared memory: the elements are first
 //               partitioned by bin range so that every range's bins fit one
 //               block's shared memory (hist_part.cu) -- no global atomics.
@@ -42,7 +46,9 @@
 
 namespace adc {
 
-enum HistStrategy { kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4, kSplit = 5, kCluster = 6 };
+enum HistStrategy {
+    kSmemWarp = 0, kSmemBlock = 1, kGlobal = 2, kSmemThread = 3, kPart = 4, kSplit = 5, kCluster = 6, kTwoPass = 7
+};
 
 // ------------------------------------------------------------ element loop --
 // Calls f(key, value, index) for every element, grid-stride over 4-element
@@ -341,6 +347,93 @@ k_sel_reduce(const unsigned long long *__restrict__ rows, const int C, const int
         }
         hist[j] = v;
         is[j] = (int32_t)idx;
+    }
+}
+
+// TWOPASS, pass 1: each block (one per SM) keeps a table of the bins' best
+// order-preserving 32-bit value keys in shared memory and writes it as its
+// partial row; k_ord_rows_reduce takes the best over the rows per bin.
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_sel_val_rows(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+               uint32_t *__restrict__ rows) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) sh[j] = Ord32<MAX>::kEmpty;
+    __syncthreads();
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t) {
+        if (in_range(k, m)) Ord32<MAX>::update(sh + k, ordered_key(v), true);
+    });
+    __syncthreads();
+    uint32_t *row = rows + (int64_t)blockIdx.x * m;
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) row[j] = sh[j];
+}
+
+// Per bin, the best of the G rows' keys (32 bins across the lanes, the rows
+// over the 32 warps); idx gets its "none yet" sentinel for pass 2.
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_ord_rows_reduce(const uint32_t *__restrict__ rows, const int G, const int64_t m, uint32_t *__restrict__ best,
+                  uint32_t *__restrict__ idx) {
+    __shared__ uint32_t s_k[32][33];
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    const int64_t j = (int64_t)blockIdx.x * 32 + lane;
+    uint32_t b = Ord32<MAX>::kEmpty;
+    if (j < m)
+        for (int g = wp; g < G; g += 32) {
+            const uint32_t c = rows[(int64_t)g * m + j];
+            if (Ord32<MAX>::better(c, b)) b = c;
+        }
+    s_k[wp][lane] = b;
+    __syncthreads();
+    if (wp == 0 && j < m) {
+        for (int u = 1; u < 32; ++u)
+            if (Ord32<MAX>::better(s_k[u][lane], b)) b = s_k[u][lane];
+        best[j] = b;
+        idx[j] = 0xffffffffu;
+    }
+}
+
+// TWOPASS, pass 2: with the bins' best keys in shared memory, every element
+// holding its bin's best value offers its index; the lowest one stays (the
+// lifted operator's tie rule).  Few elements match, so the global atomics are
+// few.
+template <bool MAX>
+__global__ void __launch_bounds__(1024)
+k_sel_index_pass(const int32_t *__restrict__ keys, const float *__restrict__ vals, const int64_t n, const int64_t m,
+                 const uint32_t *__restrict__ best, uint32_t *__restrict__ idx) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sh = reinterpret_cast<uint32_t *>(smem_raw);
+    for (int64_t j = threadIdx.x; j < m; j += blockDim.x) sh[j] = best[j];
+    __syncthreads();
+    for_each_elem(keys, vals, n, [&](int32_t k, float v, int64_t i) {
+        if (in_range(k, m) && ordered_key(v) == sh[k]) atomicMin(idx + k, (uint32_t)i);
+    });
+}
+
+// Decode: the bin's value (a selected zero takes the stored element's sign),
+// its index (n if none), hist0 folded in as in k_hist_sel_final.
+template <bool MAX>
+__global__ void k_sel_twopass_final(const uint32_t *__restrict__ best, const uint32_t *__restrict__ idx,
+                                    const float *__restrict__ vals, const float *__restrict__ h0, const int64_t m,
+                                    const int64_t n, float *__restrict__ hist, int32_t *__restrict__ is) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m; j += (int64_t)gridDim.x * blockDim.x) {
+        float v = MAX ? -Num<float>::inf() : Num<float>::inf();
+        int64_t i = n;
+        if (best[j] != Ord32<MAX>::kEmpty) {
+            i = idx[j];
+            v = from_ordered(best[j]);
+            if (v == 0.0f) v = vals[i];
+        }
+        if (h0) {
+            const float a = h0[j];
+            if (MAX ? (a >= v) : (a <= v)) {
+                v = a;
+                i = n;
+            }
+        }
+        hist[j] = v;
+        is[j] = (int32_t)i;
     }
 }
 
@@ -1004,6 +1097,9 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
     case kCluster:
         return (op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 4 && (size_t)m * 8 > kBlockBudget &&
                (size_t)m * 8 <= (size_t)kMaxClusterBlocks * kBlockBudget;
+    case kTwoPass:
+        return (op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 4 && (size_t)m * 8 > kBlockBudget &&
+               (size_t)m * 4 <= kBlockBudget;
     default: return true;
     }
 }
@@ -1012,7 +1108,7 @@ static bool fits(adc_op op, size_t s, HistStrategy st, int64_t m) {
 // always uses the two global phases.
 static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && s == 8) return kGlobal;
-    if (g_force_strategy >= 0 && g_force_strategy <= 6 && fits(op, s, (HistStrategy)g_force_strategy, m))
+    if (g_force_strategy >= 0 && g_force_strategy <= 7 && fits(op, s, (HistStrategy)g_force_strategy, m))
         return (HistStrategy)g_force_strategy;
     // min/max updates are rare after the first few values of a bin (a read
     // filters them), so per-warp copies beat per-thread tables there: the
@@ -1023,6 +1119,9 @@ static HistStrategy pick(adc_op op, size_t s, int64_t m) {
     // CLUSTER against 0.28 ms.)
     for (HistStrategy st : {kSmemThread, kSmemWarp, kSmemBlock})
         if (!(select && st == kSmemThread) && fits(op, s, st, m)) return st;
+    // packed table beyond one block but values within: two passes (at m = 50,000
+    // 0.18 ms against 0.25 ms for the filtered global atomics)
+    if (fits(op, s, kTwoPass, m)) return kTwoPass;
     if (m >= kPartMinBins && fits(op, s, kPart, m)) return kPart;
     return kGlobal;
 }
@@ -1052,6 +1151,9 @@ static HistStrategy pick_entry(adc_op op, size_t s, size_t e, int64_t m, int *R)
 // one cluster per two SMs).
 static int cluster_blocks(int64_t m) { return (int)(((size_t)m * 8 + kBlockBudget - 1) / kBlockBudget); }
 static size_t cluster_rows_bytes(int64_t m) { return (size_t)(num_sms() / 2) * (size_t)m * 8; }
+// TWOPASS: rows [SMs][m] of 32-bit keys, then best[m] and idx[m].
+static size_t twopass_rows(int64_t m) { return align_up((size_t)num_sms() * (size_t)m * 4, 256); }
+static size_t twopass_bytes(int64_t m) { return twopass_rows(m) + 2 * align_up((size_t)m * 4, 256); }
 
 // Partial tables of the shared-memory * strategies (one row of m products, and
 // for the lifted form m zero counts, per block), at the workspace's start: the
@@ -1087,8 +1189,12 @@ static size_t base_ws(adc_op op, adc_dtype dt, int64_t m) {
     case ADC_OP_MAX: {
         const size_t tab = (size_t)m * 8 + (dt == ADC_F64 ? (size_t)m * 4 + 256 : 0);
         // (CLUSTER is not chosen automatically: its rows only when it is forced)
-        const size_t rows =
+        size_t rows =
             dt == ADC_F32 && g_force_strategy == kCluster && fits(op, 4, kCluster, m) ? cluster_rows_bytes(m) : 0;
+        if (dt == ADC_F32 && fits(op, 4, kTwoPass, m)) {
+            const size_t t = twopass_bytes(m);
+            rows = t > rows ? t : rows;
+        }
         return kWsHeader + (tab > rows ? tab : rows);
     }
     default: return 0;
@@ -1276,7 +1382,7 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
                 // the table blocks decode their bins into hist and is: no finaliser
                 return part_fwd(mx ? kPMax : kPMin, ADC_F32, n, m, keys, vals, h0, hist, nullptr, nullptr, is, ws,
                                 part_off(op, ADC_F32, m), s);
-            } else {
+            } else if (!(n > 0 && (st == kTwoPass || st == kCluster))) {  // those two build their own tables
                 if (mx) k_pack_init<true><<<gm, 256, 0, s>>>(tab, m);
                 else k_pack_init<false><<<gm, 256, 0, s>>>(tab, m);
             }
@@ -1284,6 +1390,22 @@ static adc_status hist_fwd_t(adc_op op, int64_t n, int64_t m, const int32_t *key
                 if (st == kGlobal) {
                     if (mx) k_hist_sel_global<true><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
                     else k_hist_sel_global<false><<<L.grid, L.block, 0, s>>>(keys, vals, n, m, tab, n >= 16 * m);
+                } else if (st == kTwoPass) {
+                    const int G = num_sms();
+                    uint32_t *rows = reinterpret_cast<uint32_t *>(tab);  // the rows take the packed table's place
+                    uint32_t *best = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(tab) + twopass_rows(m));
+                    uint32_t *idx = best + align_up((size_t)m * 4, 256) / 4;
+                    const size_t smem = (size_t)m * 4;
+                    auto p1 = mx ? k_sel_val_rows<true> : k_sel_val_rows<false>;
+                    auto p2 = mx ? k_sel_index_pass<true> : k_sel_index_pass<false>;
+                    if (!set_smem(p1, smem) || !set_smem(p2, smem)) return ADC_ERR_CUDA;
+                    p1<<<G, 1024, smem, s>>>(keys, vals, n, m, rows);
+                    if (mx) k_ord_rows_reduce<true><<<(unsigned)((m + 31) / 32), 1024, 0, s>>>(rows, G, m, best, idx);
+                    else k_ord_rows_reduce<false><<<(unsigned)((m + 31) / 32), 1024, 0, s>>>(rows, G, m, best, idx);
+                    p2<<<G, 1024, smem, s>>>(keys, vals, n, m, best, idx);
+                    if (mx) k_sel_twopass_final<true><<<gm, 256, 0, s>>>(best, idx, vals, h0, m, n, hist, is);
+                    else k_sel_twopass_final<false><<<gm, 256, 0, s>>>(best, idx, vals, h0, m, n, hist, is);
+                    return check_launch();
                 } else if (st == kCluster) {
                     const int CS = cluster_blocks(m);
                     const int64_t H = (m + CS - 1) / CS;

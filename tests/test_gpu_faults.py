@@ -76,7 +76,7 @@ def test_reverse_scan_stall_times_out():
 def test_host_side_errors_are_status_codes():
     x = dev(np.zeros(10, np.float32))
     with pytest.raises(adcomb.AdcError) as e:
-        adcomb.scan_fwd("sop", dev(np.zeros((10, 2), np.float32)))  # sumOfProd: reduce rules only
+        adcomb.vscan_fwd("lin", dev(np.zeros((10, 4), np.float32)))  # vectorised: scalar operators only
     assert e.value.code == 2
     small = adcomb.Workspace()
     small.buf = torch.empty(256, dtype=torch.uint8, device="cuda")

@@ -56,7 +56,8 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2, 3, 4, 5, 6]  # auto, per-warp, per-block, global, per-thread, partitioned, split, cluster
+STRATS = [-1, 0, 1, 2, 3, 4, 5, 6, 7]  # auto, per-warp, per-block, global, per-thread, partitioned, split,
+                                       # cluster, two passes
 
 
 def fits(op, dt, m, s):
@@ -71,6 +72,8 @@ def fits(op, dt, m, s):
         return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 4 * 200 * 1024
     if s == 6:  # the same spread over the blocks of a 2-8 block cluster
         return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 8 * 200 * 1024
+    if s == 7:  # value tables per block, then an index pass
+        return op in ("min", "max") and sz == 4 and m * 8 > 200 * 1024 and m * 4 <= 200 * 1024
     e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
     if s == 3:
         return m * e * 256 <= 64 * 1024
@@ -383,6 +386,33 @@ def test_hist_sel_cluster_sizes(op):
                 h, saved = adcomb.hist_fwd(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0))
                 ref, idx = oracle.hist_fwd(op, m, k, v, hist0)
                 assert np.array_equal(host(h), ref.astype(np.float32)), (n, m)
+                assert np.array_equal(host(saved.view(torch.int32))[:m], idx.astype(np.int32)), (n, m)
+                vb, h0b = adcomb.hist_vjp(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0), h, saved,
+                                          dev(hb), want_hist0bar=True)
+                vr, h0r = oracle.hist_vjp(op, m, k, v, hb, hist0)
+                assert np.array_equal(host(vb), vr.astype(np.float32)), (n, m)
+                assert np.array_equal(host(h0b), h0r.astype(np.float32)), (n, m)
+    finally:
+        adcomb.debug_force_hist_strategy(-1)
+
+
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_hist_sel_twopass(op):
+    """Lifted fp32 min/max by value tables per block plus an index pass, across
+    its range of m, forward and vjp bit-exact (ties everywhere, signed zeros)."""
+    g = np.random.default_rng(73)
+    try:
+        adcomb.debug_force_hist_strategy(7)
+        for n, m in [(1, 25_601), (7, 30_000), (200_003, 30_000), (500_001, 50_000), (400_003, 51_200)]:
+            k = keys_oor(g, n, m)
+            v = ((g.integers(0, 64, n) - 32) / 8.0).astype(np.float32)
+            v[g.random(n) < 0.05] = -0.0
+            h0 = ((g.integers(0, 64, m) - 40) / 8.0).astype(np.float32)
+            hb = synth.normal(g, m, np.float32)
+            for hist0 in (None, h0):
+                h, saved = adcomb.hist_fwd(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0))
+                ref, idx = oracle.hist_fwd(op, m, k, v, hist0)
+                assert np.array_equal(host(h).view(np.uint32), ref.astype(np.float32).view(np.uint32)), (n, m)
                 assert np.array_equal(host(saved.view(torch.int32))[:m], idx.astype(np.int32)), (n, m)
                 vb, h0b = adcomb.hist_vjp(op, m, dev(k), dev(v), None if hist0 is None else dev(hist0), h, saved,
                                           dev(hb), want_hist0bar=True)
