@@ -955,6 +955,7 @@ __global__ void k_hist_sel_vjp_gather(const int32_t *__restrict__ keys, const in
                                       const int accumulate) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t keep = l2_evict_last_policy();  // is and histbar stay in L2; keys and valsbar stream
     const int64_t nv = n / 4;
     for (int64_t v = g; v < nv; v += stride) {
         const int4 k = __ldcs(reinterpret_cast<const int4 *>(keys) + v);
@@ -963,8 +964,8 @@ __global__ void k_hist_sel_vjp_gather(const int32_t *__restrict__ keys, const in
         const int kk[4] = {k.x, k.y, k.z, k.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            const bool sel = in_range(kk[c], m) && __ldg(is + kk[c]) == (int32_t)(4 * v + c);
-            const T gv = sel ? __ldg(hb + kk[c]) : T(0);
+            const bool sel = in_range(kk[c], m) && ld_keep(is + kk[c], keep) == (int32_t)(4 * v + c);
+            const T gv = sel ? ld_keep(hb + kk[c], keep) : T(0);
             o[c] = accumulate ? o[c] + gv : gv;
         }
         store_chunk(vb, v * 4, n, o);
@@ -1008,9 +1009,10 @@ __global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__rest
                                const int64_t n, const int64_t m, const int accumulate) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t keep = l2_evict_last_policy();  // the coefficient tables stay in L2; keys and values stream
     auto grad = [&](int32_t k, T v) -> T {
         if (!in_range(k, m)) return T(0);
-        return v != T(0) ? __ldg(anz + k) / v : __ldg(az + k);
+        return v != T(0) ? ld_keep(anz + k, keep) / v : ld_keep(az + k, keep);
     };
     // two 4-element groups per thread and step: both groups' loads issued first
     const int64_t nv = n / 8;
@@ -1018,7 +1020,7 @@ __global__ void k_hist_mul_vjp(const int32_t *__restrict__ keys, const T *__rest
         const int4 k0 = __ldcs(reinterpret_cast<const int4 *>(keys) + 2 * v);
         const int4 k1 = __ldcs(reinterpret_cast<const int4 *>(keys) + 2 * v + 1);
         T a[8], o[8];
-        load_chunk(vals, v * 8, n, a, T(1));
+        load_chunk_cs(vals, v * 8, n, a, T(1));
         if (accumulate) load_chunk(vb, v * 8, n, o, T(0));
         const int kk[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
 #pragma unroll
