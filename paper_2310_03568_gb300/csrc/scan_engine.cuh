@@ -39,6 +39,21 @@ namespace adc {
 
 struct NoAux {};
 
+// An Op may ask (static constexpr bool members, detected here) to receive in
+// store() the EXCLUSIVE prefix of each item instead of the inclusive one
+// (kExclusiveStore: segment ops, whose item is a run of elements that store()
+// re-walks from its incoming value), and to be scanned by the per-tile engine
+// only (kPerTileOnly: ops whose build() is expensive, which the range engine
+// would run twice).
+template <class Op> constexpr bool exclusive_store(long) { return false; }
+template <class Op> constexpr auto exclusive_store(int) -> decltype(Op::kExclusiveStore, bool()) {
+    return Op::kExclusiveStore;
+}
+template <class Op> constexpr bool per_tile_only(long) { return false; }
+template <class Op> constexpr auto per_tile_only(int) -> decltype(Op::kPerTileOnly, bool()) {
+    return Op::kPerTileOnly;
+}
+
 // ---------------------------------------------------- tagged tile status --
 // A published tile state S is stored as K = sizeof(S)/4 64-bit words, each
 // (tag << 32 | one 32-bit word of S), in two arrays: aggregates (tag AGG) and
@@ -230,8 +245,9 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
 #pragma unroll
                 for (int k = 0; k < ITEMS; ++k) {
                     const int kk = REVERSE ? ITEMS - 1 - k : k;
+                    const S ex = run;
                     run = op.combine(run, st[kk]);
-                    st[kk] = run;
+                    st[kk] = exclusive_store<Op>(0) ? ex : run;
                 }
                 op.store(c0, n, st, aux);
             }
@@ -430,8 +446,9 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const int kk = REVERSE ? ITEMS - 1 - k : k;
+            const S exk = run;
             run = op.combine(run, st[kk]);
-            st[kk] = run;
+            st[kk] = exclusive_store<Op>(0) ? exk : run;
         }
         op.store(c0, n, st, aux);
     }
@@ -499,6 +516,12 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     char *w = static_cast<char *>(region);
     if (cudaMemsetAsync(w, 0, L.bytes, s) != cudaSuccess) return ADC_ERR_CUDA;
     const DevCtl ctl = make_ctl(ws, slot);
+    if constexpr (per_tile_only<Op>(0)) {
+        k_scan<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)T, kScanThreads, 0, s>>>(
+            op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
+            reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
+        return check_launch();
+    } else {
     const int64_t G = (int64_t)num_sms() * ranges_blocks_per_sm<Op, ITEMS, REVERSE>();
     // Ranges: one per resident block by default; a tuned count launches more,
     // smaller ranges (blocks claim them in start order, so the look-back only
@@ -519,6 +542,7 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
         op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
         reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
     return check_launch();
+    }
 }
 
 }  // namespace adc
