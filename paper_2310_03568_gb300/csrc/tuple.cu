@@ -22,63 +22,131 @@ struct TupleDesc {
     int k, D, Dp;                   // blocks, row width, shared-memory row stride (odd)
     int off[kMaxTupleBlocks];       // first column of block c in a row
     int w[kMaxTupleBlocks];         // arity of block c
+    float invw[kMaxTupleBlocks];    // 1 / w[c]
     int64_t plane[kMaxTupleBlocks]; // element offset of block c's plane in a plane set
 };
 
-// Rows [n][D] -> k planes [n][a_c].  A tile of R rows is read coalesced into
-// shared memory (row stride Dp odd: a column walk is conflict-free), then each
-// block's R x a_c run is written out contiguously.
+// q = f / d for f < 2^14 by a float reciprocal and one correction step (the
+// estimate is off by at most one there); an integer division per element
+// would dominate these copy kernels.
+struct SmallDiv {
+    uint32_t d;
+    float inv;
+    __device__ __forceinline__ uint32_t operator()(uint32_t f) const {
+        uint32_t q = __float2uint_rz(__uint2float_rz(f) * inv);
+        if (q * d > f) --q;
+        else if ((q + 1) * d <= f) ++q;
+        return q;
+    }
+};
+__device__ __forceinline__ SmallDiv small_div(int d) { return {(uint32_t)d, 1.0f / (float)d}; }
+
+// 16-byte words of T, for the vectorised halves of the copies.
+template <typename T> struct Vec16 {
+    static constexpr int V = 16 / (int)sizeof(T);
+    T v[V];
+};
+
+// Rows [n][D] -> k planes [n][a_c].  A tile of R rows (R a multiple of 4, so
+// every tile and every plane run starts on a 16-byte boundary) is read with
+// 16-byte loads into shared memory (row stride Dp odd: a column walk is
+// conflict-free), then each block's R x a_c run is written out with 16-byte
+// stores; the ragged ends element by element.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tuple_split(const T *__restrict__ x, T *__restrict__ planes,
                                                       const TupleDesc d, const int64_t n, const int R) {
+    constexpr int V = Vec16<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    const SmallDiv divD = small_div(d.D);
     const int64_t tiles = (n + R - 1) / R;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t r0 = t * R;
         const int rows = (int)((n - r0) < R ? (n - r0) : R);
+        const int total = rows * d.D;
         const T *src = x + r0 * d.D;
-        for (int f = threadIdx.x; f < rows * d.D; f += blockDim.x) {
-            const int r = f / d.D, c = f - r * d.D;
-            sm[r * d.Dp + c] = src[f];
+        for (int fv = threadIdx.x; fv < total / V; fv += blockDim.x) {
+            const Vec16<T> u = reinterpret_cast<const Vec16<T> *>(src)[fv];
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int f = fv * V + q, r = (int)divD((uint32_t)f);
+                sm[r * d.Dp + (f - r * d.D)] = u.v[q];
+            }
+        }
+        for (int f = (total / V) * V + threadIdx.x; f < total; f += blockDim.x) {
+            const int r = (int)divD((uint32_t)f);
+            sm[r * d.Dp + (f - r * d.D)] = src[f];
         }
         __syncthreads();
         for (int b = 0; b < d.k; ++b) {
-            const int w = d.w[b], o = d.off[b];
+            const int w = d.w[b], o = d.off[b], cnt = rows * w;
+            const SmallDiv divw{(uint32_t)w, d.invw[b]};
             T *dst = planes + d.plane[b] + r0 * w;
-            for (int j = threadIdx.x; j < rows * w; j += blockDim.x) {
-                const int r = j / w, q = j - r * w;
-                dst[j] = sm[r * d.Dp + o + q];
+            for (int jv = threadIdx.x; jv < cnt / V; jv += blockDim.x) {
+                Vec16<T> u;
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    const int j = jv * V + q, r = (int)divw((uint32_t)j);
+                    u.v[q] = sm[r * d.Dp + o + (j - r * w)];
+                }
+                reinterpret_cast<Vec16<T> *>(dst)[jv] = u;
+            }
+            for (int j = (cnt / V) * V + threadIdx.x; j < cnt; j += blockDim.x) {
+                const int r = (int)divw((uint32_t)j);
+                dst[j] = sm[r * d.Dp + o + (j - r * w)];
             }
         }
         __syncthreads();
     }
 }
 
-// k planes -> rows [n][D] (y = rows, or y += rows).
+// k planes -> rows [n][D] (y = rows, or y += rows), the same way round.
 template <typename T>
 __global__ void __launch_bounds__(256) k_tuple_merge(const T *__restrict__ planes, T *__restrict__ y,
                                                       const TupleDesc d, const int64_t n, const int R,
                                                       const int accumulate) {
+    constexpr int V = Vec16<T>::V;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *sm = reinterpret_cast<T *>(smem_raw);
+    const SmallDiv divD = small_div(d.D);
     const int64_t tiles = (n + R - 1) / R;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
         const int64_t r0 = t * R;
         const int rows = (int)((n - r0) < R ? (n - r0) : R);
+        const int total = rows * d.D;
         for (int b = 0; b < d.k; ++b) {
-            const int w = d.w[b], o = d.off[b];
+            const int w = d.w[b], o = d.off[b], cnt = rows * w;
+            const SmallDiv divw{(uint32_t)w, d.invw[b]};
             const T *src = planes + d.plane[b] + r0 * w;
-            for (int j = threadIdx.x; j < rows * w; j += blockDim.x) {
-                const int r = j / w, q = j - r * w;
-                sm[r * d.Dp + o + q] = src[j];
+            for (int jv = threadIdx.x; jv < cnt / V; jv += blockDim.x) {
+                const Vec16<T> u = reinterpret_cast<const Vec16<T> *>(src)[jv];
+#pragma unroll
+                for (int q = 0; q < V; ++q) {
+                    const int j = jv * V + q, r = (int)divw((uint32_t)j);
+                    sm[r * d.Dp + o + (j - r * w)] = u.v[q];
+                }
+            }
+            for (int j = (cnt / V) * V + threadIdx.x; j < cnt; j += blockDim.x) {
+                const int r = (int)divw((uint32_t)j);
+                sm[r * d.Dp + o + (j - r * w)] = src[j];
             }
         }
         __syncthreads();
         T *dst = y + r0 * d.D;
-        for (int f = threadIdx.x; f < rows * d.D; f += blockDim.x) {
-            const int r = f / d.D, c = f - r * d.D;
-            const T v = sm[r * d.Dp + c];
+        for (int fv = threadIdx.x; fv < total / V; fv += blockDim.x) {
+            Vec16<T> u;
+            if (accumulate) u = reinterpret_cast<const Vec16<T> *>(dst)[fv];
+#pragma unroll
+            for (int q = 0; q < V; ++q) {
+                const int f = fv * V + q, r = (int)divD((uint32_t)f);
+                const T v = sm[r * d.Dp + (f - r * d.D)];
+                u.v[q] = accumulate ? u.v[q] + v : v;
+            }
+            reinterpret_cast<Vec16<T> *>(dst)[fv] = u;
+        }
+        for (int f = (total / V) * V + threadIdx.x; f < total; f += blockDim.x) {
+            const int r = (int)divD((uint32_t)f);
+            const T v = sm[r * d.Dp + (f - r * d.D)];
             dst[f] = accumulate ? dst[f] + v : v;
         }
         __syncthreads();
@@ -190,6 +258,7 @@ static TupleDesc tdesc(int k, const adc_op *ops, const TLayout &L) {
     for (int c = 0; c < k; ++c) {
         d.off[c] = o;
         d.w[c] = arity(ops[c]);
+        d.invw[c] = 1.0f / (float)d.w[c];
         d.plane[c] = L.plane[c];
         o += d.w[c];
     }
@@ -198,8 +267,9 @@ static TupleDesc tdesc(int k, const adc_op *ops, const TLayout &L) {
     return d;
 }
 
-// Rows per tile: 16 KB of shared memory per block (Dp <= 65 scalars: R >= 31).
-static int tile_rows(const TupleDesc &d, size_t e) { return (int)(16384 / ((size_t)d.Dp * e)); }
+// Rows per tile: 16 KB of shared memory per block (Dp <= 65 scalars: R >= 28),
+// a multiple of 4 so that tiles and plane runs start on 16-byte boundaries.
+static int tile_rows(const TupleDesc &d, size_t e) { return (int)(16384 / ((size_t)d.Dp * e)) & ~3; }
 
 static unsigned tile_grid(int64_t n, int R) {
     const int64_t tiles = (n + R - 1) / R;
