@@ -508,6 +508,54 @@ def run_kernels(args):
         adcomb.debug_set_scan_engine(0)
         adcomb.debug_set_scan_range_tiles(0)
         del x, y, yb, xb
+    # min / max scans (the general arity-1 rule), values on 1024 levels
+    for op in ("min", "max"):
+        if not want(f"scan {op} float32"):
+            continue
+        n = 100_000_000
+        x = torch.from_numpy(((g.integers(0, 1024, n) - 512) / 64.0).astype(np.float32)).to(dev)
+        y = adcomb.scan_fwd(op, x, ws=ws)
+        yb = torch.randn_like(x)
+        xb = torch.empty_like(x)
+        row(f"scan {op} fwd float32", n, 8 * n, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
+        row(f"scan {op} vjp float32", n, 16 * n, timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        del x, y, yb, xb
+    # vectorised operators (Irwim / Iswim): the paper's [n][d] shapes, d = 16 (reduce, scan), 10 (hist)
+    for kind, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),
+                           ("vreduce", "add", 10_000_000, 16), ("vreduce", "min", 10_000_000, 16),
+                           ("vhist", "add", 10_000_000, 10), ("vhist", "max", 10_000_000, 10)]:
+        if not want(f"{kind} {op}"):
+            continue
+        if op == "mul":
+            x = (torch.rand(n, d, device=dev) * 0.2 + 0.9).contiguous()
+        elif op in ("min", "max"):
+            x = ((torch.randint(0, 1024, (n, d), device=dev) - 512) / 64.0).float().contiguous()
+        else:
+            x = (torch.rand(n, d, device=dev) * 2 - 1).contiguous()
+        s = n * d * 4
+        if kind == "vscan":
+            y = adcomb.vscan_fwd(op, x, ws=ws)
+            yb = torch.randn_like(x)
+            xb = torch.empty_like(x)
+            row(f"vscan {op} fwd d={d}", n, 2 * s, timeit(lambda: adcomb.vscan_fwd(op, x, y, ws=ws)))
+            row(f"vscan {op} vjp d={d}", n, (2 if op == "add" else 4) * s,
+                timeit(lambda: adcomb.vscan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        elif kind == "vreduce":
+            y, sv = adcomb.vreduce_fwd(op, x, ws=ws)
+            yb = torch.randn(d, device=dev)
+            xb = torch.empty_like(x)
+            row(f"vreduce {op} fwd d={d}", n, s, timeit(lambda: adcomb.vreduce_fwd(op, x, y, sv, ws=ws)))
+            row(f"vreduce {op} vjp d={d}", n, s, timeit(lambda: adcomb.vreduce_vjp(op, x, y, sv, yb, xbar=xb, ws=ws)))
+        else:
+            m = 1000
+            k = torch.randint(0, m, (n,), dtype=torch.int32, device=dev)
+            h, sv = adcomb.vhist_fwd(op, m, k, x, ws=ws)
+            hb = torch.randn(m, d, device=dev)
+            vb = torch.empty_like(x)
+            row(f"vhist {op} fwd d={d} m={m}", n, 4 * n + s, timeit(lambda: adcomb.vhist_fwd(op, m, k, x, None, h, sv, ws=ws)))
+            row(f"vhist {op} vjp d={d} m={m}", n, 4 * n + s,
+                timeit(lambda: adcomb.vhist_vjp(op, m, k, x, None, h, sv, hb, valsbar=vb, ws=ws)))
+        del x
     # tuple scans (block-diagonal Jacobians): rows [n][D] and one array per block
     for ops, n in [(("sop",) * 16, 10_000_000), (("add", "mul", "lin", "sop", "mm2", "min"), 20_000_000)]:
         name = f"{ops[0]}x{len(ops)}" if len(set(ops)) == 1 else "-".join(ops)

@@ -122,6 +122,8 @@ static VLayout vlayout(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_
 
 size_t vws_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
     if (scalar_ws(kind, op, dt, n, m) == 0) return 0;
+    if (kind == ADC_REDUCE)  // the direct form: one partial row of column states per block
+        return kWsHeader + align_up((size_t)num_sms() * 8 * (size_t)d * 16, 256);
     return vlayout(kind, op, dt, n, m, d).bytes;
 }
 size_t vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
@@ -148,51 +150,223 @@ static adc_status finish(char *ws, const VLayout &L, int64_t d, cudaStream_t s) 
 }
 
 // -------------------------------------------------------------- combinators --
+// ---------------------------------------------------- reduce, direct form --
+// The Irwim rule makes the vectorised reduce d independent column reductions.
+// Rather than transposing, the rows are read as they lie: the flat array of
+// n*d scalars is strided by S, a multiple of d threads, so each thread meets
+// a single column and folds it with that column's lifted operator (Fig. 3's
+// zero count and product for *, Fig. 5's lowest-index min/max); each block
+// then folds its threads column by column into one partial row, and one more
+// kernel folds the partial rows in block order.  Column c's residuals go to
+// saved + c * kVColSaved, laid out as the scalar reduce's.
+constexpr int kVRedThreads = 256;
+constexpr size_t kVColSaved = 256;  // bytes of residuals per column
+
+template <typename T> struct VAdd {
+    using State = T;
+    __device__ State identity() const { return T(0); }
+    __device__ State combine(State a, State b) const { return a + b; }
+    __device__ State lift(T x, int64_t) const { return x; }
+};
+template <typename T> struct VMulS { T p; int32_t z; int32_t pad; };
+template <typename T> struct VMul {
+    using State = VMulS<T>;
+    __device__ State identity() const { return {T(1), 0, 0}; }
+    __device__ State combine(const State &a, const State &b) const { return {a.p * b.p, a.z + b.z, 0}; }
+    __device__ State lift(T x, int64_t) const { return x == T(0) ? State{T(1), 1, 0} : State{x, 0, 0}; }
+};
+template <typename T> struct VSelS { T v; int32_t i; int32_t pad; };
+template <typename T, bool MAX> struct VSel {
+    using State = VSelS<T>;
+    int32_t none;  // the index of "no element" (n)
+    __device__ State identity() const { return {MAX ? -Num<T>::inf() : Num<T>::inf(), none, 0}; }
+    __device__ State combine(const State &a, const State &b) const {
+        if (MAX ? (a.v > b.v) : (a.v < b.v)) return a;
+        if (MAX ? (b.v > a.v) : (b.v < a.v)) return b;
+        return a.i <= b.i ? a : b;  // equal values: the smaller index
+    }
+    __device__ State lift(T x, int64_t i) const { return {x, (int32_t)i, 0}; }
+};
+
+// Active threads of the grid: the largest multiple of d.
+__device__ __forceinline__ int64_t vred_active(int64_t d) {
+    return ((int64_t)gridDim.x * blockDim.x / d) * d;
+}
+
+template <class Op, typename T>
+__global__ void __launch_bounds__(kVRedThreads)
+k_vred_rows(const Op op, const T *__restrict__ x, const int64_t n, const int64_t d,
+            typename Op::State *__restrict__ part) {
+    using S = typename Op::State;
+    __shared__ S s_st[kVRedThreads];
+    const int64_t S_ = vred_active(d);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    S a = op.identity();
+    if (gt < S_) {
+        // eight loads in flight per thread before they are folded in order
+        constexpr int U = 8;
+        const int64_t total = n * d, rstep = S_ / d;
+        int64_t row = gt / d, f = gt;
+        for (; f + (U - 1) * S_ < total; f += U * S_, row += U * rstep) {
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = __ldcs(x + f + u * S_);
+#pragma unroll
+            for (int u = 0; u < U; ++u) a = op.combine(a, op.lift(v[u], row + u * rstep));
+        }
+        for (; f < total; f += S_, row += rstep) a = op.combine(a, op.lift(__ldcs(x + f), row));
+    }
+    s_st[threadIdx.x] = a;
+    __syncthreads();
+    if (threadIdx.x < d) {
+        // this block's threads of column c = (base + t) mod d, in thread order
+        const int64_t base = (int64_t)blockIdx.x * blockDim.x;
+        const int64_t c = (base + threadIdx.x) % d;
+        S r = op.identity();
+        for (int t = threadIdx.x; t < kVRedThreads && base + t < S_; t += (int)d) r = op.combine(r, s_st[t]);
+        part[(int64_t)blockIdx.x * d + c] = r;
+    }
+}
+
+// Column c: fold the G partial rows in block order, write y[c] and the residuals.
+template <typename T> __device__ __forceinline__ void vred_out(const T &r, T *y, char *, int64_t c) { y[c] = r; }
+template <typename T> __device__ __forceinline__ void vred_out(const VMulS<T> &r, T *y, char *sv, int64_t c) {
+    y[c] = r.z > 0 ? T(0) : r.p;
+    *reinterpret_cast<int32_t *>(sv + c * kVColSaved) = r.z;
+    *reinterpret_cast<T *>(sv + c * kVColSaved + 8) = r.p;
+}
+template <typename T> __device__ __forceinline__ void vred_out(const VSelS<T> &r, T *y, char *sv, int64_t c) {
+    y[c] = r.v;
+    *reinterpret_cast<int32_t *>(sv + c * kVColSaved) = r.i;
+}
+
+template <class Op, typename T>
+__global__ void k_vred_final(const Op op, const typename Op::State *__restrict__ part, const int G, const int64_t d,
+                             T *__restrict__ y, char *__restrict__ saved) {
+    for (int64_t c = threadIdx.x; c < d; c += blockDim.x) {
+        typename Op::State r = op.identity();
+        for (int g = 0; g < G; ++g) r = op.combine(r, part[(int64_t)g * d + c]);
+        vred_out(r, y, saved, c);
+    }
+}
+
+// vjp, elementwise with the same fixed-column striding: xbar[i][c] (+)= the
+// scalar rule of column c (Sec. 3.2: broadcast for +; Fig. 3's three cases for
+// *; Fig. 5's selected index for min/max).
+template <typename T, int OPK>  // OPK: 0 add, 1 mul, 2 min/max
+__global__ void __launch_bounds__(kVRedThreads)
+k_vred_vjp(const T *__restrict__ x, const T *__restrict__ ybar, const char *__restrict__ saved, T *__restrict__ xbar,
+           const int64_t n, const int64_t d, const int accumulate) {
+    const int64_t S_ = vred_active(d);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= S_) return;
+    const int64_t c = gt % d, total = n * d, rstep = S_ / d;
+    const T yb = ybar[c];
+    int32_t k = 0;
+    T p = T(0);
+    if (OPK == 1) {
+        k = *reinterpret_cast<const int32_t *>(saved + c * kVColSaved);
+        p = *reinterpret_cast<const T *>(saved + c * kVColSaved + 8);
+    } else if (OPK == 2) {
+        k = *reinterpret_cast<const int32_t *>(saved + c * kVColSaved);
+    }
+    auto grad = [&](T a, int64_t row) -> T {
+        if (OPK == 0) return yb;
+        if (OPK == 1) return k == 0 ? (p / a) * yb : ((k == 1 && a == T(0)) ? p * yb : T(0));
+        return row == k ? yb : T(0);
+    };
+    // eight elements per thread and step, their loads issued first
+    constexpr int U = 8;
+    int64_t row = gt / d, f = gt;
+    for (; f + (U - 1) * S_ < total; f += U * S_, row += U * rstep) {
+        T a[U], o[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            a[u] = OPK == 1 ? __ldcs(x + f + u * S_) : T(0);
+            o[u] = accumulate ? xbar[f + u * S_] : T(0);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const T g = grad(a[u], row + u * rstep);
+            __stcs(xbar + f + u * S_, accumulate ? o[u] + g : g);
+        }
+    }
+    for (; f < total; f += S_, row += rstep) {
+        const T g = grad(OPK == 1 ? __ldcs(x + f) : T(0), row);
+        xbar[f] = accumulate ? xbar[f] + g : g;
+    }
+}
+
+static int vred_grid() { return num_sms() * 8; }
+
+template <typename T>
+static adc_status vred_fwd_t(adc_op op, int64_t n, int64_t d, const T *x, T *y, char *saved, char *ws,
+                             cudaStream_t s) {
+    const int G = vred_grid();
+    void *part = ws + kWsHeader;
+    switch (op) {
+    case ADC_OP_ADD: {
+        VAdd<T> o;
+        k_vred_rows<<<G, kVRedThreads, 0, s>>>(o, x, n, d, static_cast<T *>(part));
+        k_vred_final<<<1, 64, 0, s>>>(o, static_cast<const T *>(part), G, d, y, saved);
+        break;
+    }
+    case ADC_OP_MUL: {
+        VMul<T> o;
+        k_vred_rows<<<G, kVRedThreads, 0, s>>>(o, x, n, d, static_cast<VMulS<T> *>(part));
+        k_vred_final<<<1, 64, 0, s>>>(o, static_cast<const VMulS<T> *>(part), G, d, y, saved);
+        break;
+    }
+    case ADC_OP_MIN: {
+        VSel<T, false> o{(int32_t)n};
+        k_vred_rows<<<G, kVRedThreads, 0, s>>>(o, x, n, d, static_cast<VSelS<T> *>(part));
+        k_vred_final<<<1, 64, 0, s>>>(o, static_cast<const VSelS<T> *>(part), G, d, y, saved);
+        break;
+    }
+    case ADC_OP_MAX: {
+        VSel<T, true> o{(int32_t)n};
+        k_vred_rows<<<G, kVRedThreads, 0, s>>>(o, x, n, d, static_cast<VSelS<T> *>(part));
+        k_vred_final<<<1, 64, 0, s>>>(o, static_cast<const VSelS<T> *>(part), G, d, y, saved);
+        break;
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+    return check_launch();
+}
+
 adc_status vreduce_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *saved, void *ws,
                        cudaStream_t s) {
-    const VLayout L = vlayout(ADC_REDUCE, op, dt, n, 0, d);
-    const size_t e = dt == ADC_F64 ? 8 : 4;
-    char *w = static_cast<char *>(ws);
-    char *xt = w + L.nplane[0];
-    adc_status st = to_plane(dt, n, d, x, xt, s);
-    if (st != ADC_OK) return st;
-    const size_t sv = align_up(scalar_saved(ADC_REDUCE, op, dt, n, 0), 256);
-    const Cols cols{w + L.col, L.col_stride};
-    for (int64_t c = 0; c < d; ++c) {
-        bool ok;
-        char *cw = cols.ws(c, s, &ok);
-        if (!ok) return ADC_ERR_CUDA;
-        // y is the row of d results; column c's residuals follow column c-1's
-        if ((st = reduce_fwd(op, dt, n, xt + (size_t)c * plane_ld(n) * e, static_cast<char *>(y) + c * e,
-                             saved ? static_cast<char *>(saved) + c * sv : nullptr, cw, s)) != ADC_OK)
-            return st;
+    char *sv = static_cast<char *>(saved), *w = static_cast<char *>(ws);
+    if (dt == ADC_F64)
+        return vred_fwd_t<double>(op, n, d, static_cast<const double *>(x), static_cast<double *>(y), sv, w, s);
+    return vred_fwd_t<float>(op, n, d, static_cast<const float *>(x), static_cast<float *>(y), sv, w, s);
+}
+
+template <typename T>
+static adc_status vred_vjp_t(adc_op op, int64_t n, int64_t d, const T *x, const char *saved, const T *ybar, T *xbar,
+                             int acc, cudaStream_t s) {
+    if (n == 0) return ADC_OK;
+    const int G = vred_grid();
+    switch (op) {
+    case ADC_OP_ADD: k_vred_vjp<T, 0><<<G, kVRedThreads, 0, s>>>(x, ybar, saved, xbar, n, d, acc); break;
+    case ADC_OP_MUL: k_vred_vjp<T, 1><<<G, kVRedThreads, 0, s>>>(x, ybar, saved, xbar, n, d, acc); break;
+    case ADC_OP_MIN:
+    case ADC_OP_MAX: k_vred_vjp<T, 2><<<G, kVRedThreads, 0, s>>>(x, ybar, saved, xbar, n, d, acc); break;
+    default: return ADC_ERR_UNSUPPORTED;
     }
-    return finish(w, L, d, s);
+    return check_launch();
 }
 
 adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *saved,
                        const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s) {
-    const VLayout L = vlayout(ADC_REDUCE, op, dt, n, 0, d);
-    const size_t e = dt == ADC_F64 ? 8 : 4;
-    char *w = static_cast<char *>(ws);
-    char *xt = w + L.nplane[0], *xbt = w + L.nplane[1];
-    adc_status st;
-    if (x && (st = to_plane(dt, n, d, x, xt, s)) != ADC_OK) return st;
-    if (accumulate && (st = to_plane(dt, n, d, xbar, xbt, s)) != ADC_OK) return st;
-    const size_t sv = align_up(scalar_saved(ADC_REDUCE, op, dt, n, 0), 256);
-    const Cols cols{w + L.col, L.col_stride};
-    for (int64_t c = 0; c < d; ++c) {
-        bool ok;
-        char *cw = cols.ws(c, s, &ok);
-        if (!ok) return ADC_ERR_CUDA;
-        if ((st = reduce_vjp(op, dt, n, x ? xt + (size_t)c * plane_ld(n) * e : nullptr, static_cast<const char *>(y) + c * e,
-                             saved ? static_cast<const char *>(saved) + c * sv : nullptr,
-                             static_cast<const char *>(ybar) + c * e, xbt + (size_t)c * plane_ld(n) * e, accumulate, cw, s)) !=
-            ADC_OK)
-            return st;
-    }
-    if ((st = from_plane(dt, n, d, xbt, xbar, s)) != ADC_OK) return st;
-    return finish(w, L, d, s);
+    (void)y;
+    (void)ws;
+    const char *sv = static_cast<const char *>(saved);
+    if (dt == ADC_F64)
+        return vred_vjp_t<double>(op, n, d, static_cast<const double *>(x), sv, static_cast<const double *>(ybar),
+                                  static_cast<double *>(xbar), accumulate, s);
+    return vred_vjp_t<float>(op, n, d, static_cast<const float *>(x), sv, static_cast<const float *>(ybar),
+                             static_cast<float *>(xbar), accumulate, s);
 }
 
 adc_status vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s) {
