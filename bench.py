@@ -521,10 +521,10 @@ def run_kernels(args):
         row(f"scan {op} vjp float32", n, 16 * n, timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
         del x, y, yb, xb
     # vectorised operators (Irwim / Iswim): the paper's [n][d] shapes, d = 16 (reduce, scan), 10 (hist)
-    for kind, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),
-                           ("vreduce", "add", 10_000_000, 16), ("vreduce", "min", 10_000_000, 16),
-                           ("vhist", "add", 10_000_000, 10), ("vhist", "max", 10_000_000, 10)]:
-        if not want(f"{kind} {op}"):
+    for fam, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),
+                          ("vreduce", "add", 10_000_000, 16), ("vreduce", "min", 10_000_000, 16),
+                          ("vhist", "add", 10_000_000, 10), ("vhist", "max", 10_000_000, 10)]:
+        if not want(f"{fam} {op}"):
             continue
         if op == "mul":
             x = (torch.rand(n, d, device=dev) * 0.2 + 0.9).contiguous()
@@ -533,14 +533,14 @@ def run_kernels(args):
         else:
             x = (torch.rand(n, d, device=dev) * 2 - 1).contiguous()
         s = n * d * 4
-        if kind == "vscan":
+        if fam == "vscan":
             y = adcomb.vscan_fwd(op, x, ws=ws)
             yb = torch.randn_like(x)
             xb = torch.empty_like(x)
             row(f"vscan {op} fwd d={d}", n, 2 * s, timeit(lambda: adcomb.vscan_fwd(op, x, y, ws=ws)))
             row(f"vscan {op} vjp d={d}", n, (2 if op == "add" else 4) * s,
                 timeit(lambda: adcomb.vscan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
-        elif kind == "vreduce":
+        elif fam == "vreduce":
             y, sv = adcomb.vreduce_fwd(op, x, ws=ws)
             yb = torch.randn(d, device=dev)
             xb = torch.empty_like(x)

@@ -11,6 +11,7 @@
 // calls of the scalar kernels on contiguous rows, and a transpose back of the
 // [n][d] / [m][d] results.  Operators: ADD, MUL, MIN, MAX (scalar elements).
 #include "common.cuh"
+#include "hist_common.cuh"
 #include "internal.h"
 
 namespace adc {
@@ -120,10 +121,25 @@ static VLayout vlayout(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_
     return L;
 }
 
+// The direct reduce_by_index (below) applies to + and the lifted fp32 min/max
+// when one block's shared memory holds the whole [m][d] table; its workspace
+// holds one partial table per block.
+constexpr size_t kVHBudget = 200 * 1024;
+static bool vhist_direct(adc_op op, adc_dtype dt, int64_t m, int64_t d) {
+    const size_t cells = (size_t)m * (size_t)d;
+    if (op == ADC_OP_ADD) return cells * (dt == ADC_F64 ? 8 : 4) <= kVHBudget;
+    if (op == ADC_OP_MIN || op == ADC_OP_MAX) return dt == ADC_F32 && cells * 8 <= kVHBudget;
+    return false;
+}
+static size_t vhist_direct_ws(int64_t m, int64_t d) {
+    return kWsHeader + align_up((size_t)num_sms() * (size_t)m * (size_t)d * 8, 256);
+}
+
 size_t vws_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
     if (scalar_ws(kind, op, dt, n, m) == 0) return 0;
     if (kind == ADC_REDUCE)  // the direct form: one partial row of column states per block
         return kWsHeader + align_up((size_t)num_sms() * 8 * (size_t)d * 16, 256);
+    if (kind == ADC_HIST && vhist_direct(op, dt, m, d)) return vhist_direct_ws(m, d);
     return vlayout(kind, op, dt, n, m, d).bytes;
 }
 size_t vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
@@ -412,8 +428,180 @@ adc_status vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *
     return finish(w, L, d, s);
 }
 
+// -------------------------------------------- reduce_by_index, direct form --
+// For + (fp32, fp64) and the lifted fp32 min/max, when one block's shared
+// memory holds the whole [m][d] table: the same fixed-column striding over the
+// row-major values (each thread meets one column c and reads its row's key),
+// the element goes to table[key][c] (a float add, or Fig. 5's packed
+// value/index key), each block writes its table as a partial row, and a final
+// kernel folds the rows in block order per (bin, column) -- decoding min/max,
+// folding hist0 in and writing column c's selected indices where the scalar
+// entry point keeps them (saved + c * sv).  Other cases take the transposed
+// path above.
+constexpr int kVHThreads = 1024;
+
+
+// MODE 0: +, entries T; MODE 1 / 2: min / max, entries packed 64-bit keys.
+template <typename T, int MODE> struct VHE { using type = T; };
+template <typename T> struct VHE<T, 1> { using type = unsigned long long; };
+template <typename T> struct VHE<T, 2> { using type = unsigned long long; };
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kVHThreads)
+k_vhist_rows(const int32_t *__restrict__ keys, const T *__restrict__ vals, const int64_t n, const int64_t m,
+             const int64_t d, typename VHE<T, MODE>::type *__restrict__ part) {
+    using E = typename VHE<T, MODE>::type;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    E *tab = reinterpret_cast<E *>(smem_raw);
+    const int64_t cells = m * d;
+    for (int64_t j = threadIdx.x; j < cells; j += blockDim.x)
+        tab[j] = MODE == 0 ? E(0) : (MODE == 2 ? Pack<true>::kEmpty : Pack<false>::kEmpty);
+    __syncthreads();
+    const int64_t S_ = vred_active(d);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt < S_) {
+        const int64_t total = n * d, rstep = S_ / d, c = gt % d;
+        auto upd = [&](int32_t k, T v, int64_t row) {
+            if (!in_range(k, m)) return;
+            E *cell = tab + (int64_t)k * d + c;
+            if constexpr (MODE == 0) atomicAdd(cell, v);
+            else if constexpr (MODE == 1) Pack<false>::update_smem(cell, Pack<false>::key((float)v, row));
+            else Pack<true>::update_smem(cell, Pack<true>::key((float)v, row));
+        };
+        constexpr int U = 4;  // four rows' loads in flight per thread
+        int64_t row = gt / d, f = gt;
+        for (; f + (U - 1) * S_ < total; f += U * S_, row += U * rstep) {
+            int32_t k[U];
+            T v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                k[u] = __ldg(keys + row + u * rstep);
+                v[u] = __ldcs(vals + f + u * S_);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) upd(k[u], v[u], row + u * rstep);
+        }
+        for (; f < total; f += S_, row += rstep) upd(__ldg(keys + row), __ldcs(vals + f), row);
+    }
+    __syncthreads();
+    E *dst = part + (int64_t)blockIdx.x * cells;
+    for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) dst[j] = tab[j];
+}
+
+template <typename T, int MODE>
+__global__ void k_vhist_final(const typename VHE<T, MODE>::type *__restrict__ part, const int G, const int64_t m,
+                              const int64_t d, const T *__restrict__ vals, const T *__restrict__ h0, const int64_t n,
+                              T *__restrict__ hist, char *__restrict__ saved, const size_t sv) {
+    using E = typename VHE<T, MODE>::type;
+    const int64_t cells = m * d;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cells; j += (int64_t)gridDim.x * blockDim.x) {
+        if constexpr (MODE == 0) {
+            T a = T(0);
+            for (int g = 0; g < G; ++g) a += part[(int64_t)g * cells + j];
+            hist[j] = h0 ? h0[j] + a : a;
+        } else {
+            constexpr bool MAX = MODE == 2;
+            E best = Pack<MAX>::kEmpty;
+            for (int g = 0; g < G; ++g) {
+                const E k = part[(int64_t)g * cells + j];
+                if (Pack<MAX>::better(k, best)) best = k;
+            }
+            const int64_t c = j % d, bin = j / d;
+            float v = MAX ? -Num<float>::inf() : Num<float>::inf();
+            int64_t idx = n;
+            if (best != Pack<MAX>::kEmpty) {
+                idx = Pack<MAX>::index(best);
+                v = from_ordered((uint32_t)(best >> 32));
+                if (v == 0.0f) v = (float)vals[idx * d + c];  // the key folds -0.0 onto +0.0
+            }
+            if (h0) {
+                const float a = (float)h0[j];
+                if (MAX ? (a >= v) : (a <= v)) {
+                    v = a;
+                    idx = n;
+                }
+            }
+            hist[j] = (T)v;
+            if (saved) reinterpret_cast<int32_t *>(saved + c * sv)[bin] = (int32_t)idx;
+        }
+    }
+}
+
+template <typename T, int MODE>
+__global__ void __launch_bounds__(256)
+k_vhist_vjp(const int32_t *__restrict__ keys, const char *__restrict__ saved, const size_t sv,
+            const T *__restrict__ hb, T *__restrict__ vb, const int64_t n, const int64_t m, const int64_t d,
+            const int accumulate) {
+    const int64_t S_ = vred_active(d);
+    const int64_t gt = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gt >= S_) return;
+    const int64_t total = n * d, rstep = S_ / d, c = gt % d;
+    const int32_t *is = MODE == 0 ? nullptr : reinterpret_cast<const int32_t *>(saved + c * sv);
+    int64_t row = gt / d;
+    for (int64_t f = gt; f < total; f += S_, row += rstep) {
+        const int32_t k = __ldg(keys + row);
+        T g = T(0);
+        if (in_range(k, m) && (MODE == 0 || __ldg(is + k) == (int32_t)row)) g = __ldg(hb + (int64_t)k * d + c);
+        vb[f] = accumulate ? vb[f] + g : g;
+    }
+}
+
+template <typename T, int MODE>
+__global__ void k_vhist_h0bar(const char *__restrict__ saved, const size_t sv, const T *__restrict__ hb,
+                              T *__restrict__ h0b, const int64_t m, const int64_t d, const int64_t n,
+                              const int accumulate) {
+    const int64_t cells = m * d;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < cells; j += (int64_t)gridDim.x * blockDim.x) {
+        T g = hb[j];
+        if (MODE != 0 && reinterpret_cast<const int32_t *>(saved + (j % d) * sv)[j / d] < n) g = T(0);
+        h0b[j] = accumulate ? h0b[j] + g : g;
+    }
+}
+
+template <typename T, int MODE>
+static adc_status vhist_direct_fwd(int64_t n, int64_t m, int64_t d, const int32_t *keys, const T *vals, const T *h0,
+                                   T *hist, char *saved, size_t sv, char *ws, cudaStream_t s) {
+    using E = typename VHE<T, MODE>::type;
+    const int G = num_sms();
+    E *part = reinterpret_cast<E *>(ws + kWsHeader);
+    const size_t smem = (size_t)m * (size_t)d * sizeof(E);
+    if (cudaFuncSetAttribute(k_vhist_rows<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return ADC_ERR_CUDA;
+    k_vhist_rows<T, MODE><<<G, kVHThreads, smem, s>>>(keys, vals, n, m, d, part);
+    const int64_t cells = m * d;
+    const unsigned gb = (unsigned)((cells + 255) / 256 < 4096 ? (cells + 255) / 256 : 4096);
+    k_vhist_final<T, MODE><<<gb, 256, 0, s>>>(part, G, m, d, vals, h0, n, hist, saved, sv);
+    return check_launch();
+}
+
+template <typename T, int MODE>
+static adc_status vhist_direct_vjp(int64_t n, int64_t m, int64_t d, const int32_t *keys, const char *saved, size_t sv,
+                                   const T *hb, T *vb, T *h0b, int acc, cudaStream_t s) {
+    if (n > 0) k_vhist_vjp<T, MODE><<<num_sms() * 8, 256, 0, s>>>(keys, saved, sv, hb, vb, n, m, d, acc);
+    if (h0b) {
+        const int64_t cells = m * d;
+        const unsigned gb = (unsigned)((cells + 255) / 256 < 4096 ? (cells + 255) / 256 : 4096);
+        k_vhist_h0bar<T, MODE><<<gb, 256, 0, s>>>(saved, sv, hb, h0b, m, d, n, acc);
+    }
+    return check_launch();
+}
+
 adc_status vhist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys, const void *vals,
                      const void *hist0, void *hist, void *saved, void *ws, cudaStream_t s) {
+    if (vhist_direct(op, dt, m, d)) {
+        const size_t svb = align_up(scalar_saved(ADC_HIST, op, dt, n, m), 256);
+        char *sv = static_cast<char *>(saved), *w = static_cast<char *>(ws);
+        if (dt == ADC_F64)
+            return vhist_direct_fwd<double, 0>(n, m, d, keys, static_cast<const double *>(vals),
+                                               static_cast<const double *>(hist0), static_cast<double *>(hist), sv,
+                                               svb, w, s);
+        const float *v = static_cast<const float *>(vals), *h0 = static_cast<const float *>(hist0);
+        float *h = static_cast<float *>(hist);
+        if (op == ADC_OP_ADD) return vhist_direct_fwd<float, 0>(n, m, d, keys, v, h0, h, sv, svb, w, s);
+        if (op == ADC_OP_MIN) return vhist_direct_fwd<float, 1>(n, m, d, keys, v, h0, h, sv, svb, w, s);
+        return vhist_direct_fwd<float, 2>(n, m, d, keys, v, h0, h, sv, svb, w, s);
+    }
     const VLayout L = vlayout(ADC_HIST, op, dt, n, m, d);
     const size_t e = dt == ADC_F64 ? 8 : 4;
     char *w = static_cast<char *>(ws);
@@ -440,6 +628,19 @@ adc_status vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, c
                      const void *hist0, const void *hist, const void *saved, const void *histbar, void *valsbar,
                      void *hist0bar, int accumulate, void *ws, cudaStream_t s) {
     (void)hist;
+    if (vhist_direct(op, dt, m, d)) {
+        const size_t svb = align_up(scalar_saved(ADC_HIST, op, dt, n, m), 256);
+        const char *sv = static_cast<const char *>(saved);
+        if (dt == ADC_F64)
+            return vhist_direct_vjp<double, 0>(n, m, d, keys, sv, svb, static_cast<const double *>(histbar),
+                                               static_cast<double *>(valsbar), static_cast<double *>(hist0bar),
+                                               accumulate, s);
+        const float *hb = static_cast<const float *>(histbar);
+        float *vb = static_cast<float *>(valsbar), *h0b = static_cast<float *>(hist0bar);
+        if (op == ADC_OP_ADD) return vhist_direct_vjp<float, 0>(n, m, d, keys, sv, svb, hb, vb, h0b, accumulate, s);
+        if (op == ADC_OP_MIN) return vhist_direct_vjp<float, 1>(n, m, d, keys, sv, svb, hb, vb, h0b, accumulate, s);
+        return vhist_direct_vjp<float, 2>(n, m, d, keys, sv, svb, hb, vb, h0b, accumulate, s);
+    }
     const VLayout L = vlayout(ADC_HIST, op, dt, n, m, d);
     const size_t e = dt == ADC_F64 ? 8 : 4;
     char *w = static_cast<char *>(ws);
