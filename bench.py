@@ -522,6 +522,7 @@ def run_kernels(args):
         del x, y, yb, xb
     # vectorised operators (Irwim / Iswim): the paper's [n][d] shapes, d = 16 (reduce, scan), 10 (hist)
     for fam, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),
+                          ("vscan", "max", 10_000_000, 16),
                           ("vreduce", "add", 10_000_000, 16), ("vreduce", "min", 10_000_000, 16),
                           ("vhist", "add", 10_000_000, 10), ("vhist", "max", 10_000_000, 10)]:
         if not want(f"{fam} {op}"):

@@ -6,10 +6,13 @@
 //   reduce (map2 .) (replicate d e) x  ==  map (reduce . e) (transpose x)
 //   scan   (map2 .) (replicate d e) x  ==  transpose (map (scan . e) (transpose x))
 // and the vjp is taken of the right-hand side: d scalar combinators whose
-// specialised rules (Sec. 3-5) apply column by column.  Here: tiled
-// shared-memory transposes of the [n][d] (or [m][d]) operands to [d][n], d
-// calls of the scalar kernels on contiguous rows, and a transpose back of the
-// [n][d] / [m][d] results.  Operators: ADD, MUL, MIN, MAX (scalar elements).
+// specialised rules (Sec. 3-5) apply column by column.  Reduce, scan and (for
+// + and the fp32 min/max while the [m][d] table fits one block's shared
+// memory) reduce_by_index run these column rules in direct form, on the rows
+// where they lie; the other reduce_by_index cases transpose the [n][d] and
+// [m][d] operands to [d][n] through shared-memory tiles, call the scalar
+// kernels on the d contiguous columns and transpose the results back.
+// Operators: ADD, MUL, MIN, MAX (scalar elements).
 #include "common.cuh"
 #include "hist_common.cuh"
 #include "internal.h"
@@ -79,12 +82,11 @@ __global__ void k_gather_errors(unsigned *err, const char *cols, const int64_t d
 }
 
 // ------------------------------------------------------------- workspace --
-// [header][n-planes: [d][n] each][m-planes: [d][m] each][per-column scalar
-// workspaces, each with its own header].  Planes per kind: reduce 2 (x^T,
-// xbar^T); scan 4 (x^T, y^T, ybar^T, xbar^T); reduce_by_index 2 n-planes
-// (vals^T, valsbar^T) and 3 m-planes (hist0^T / histbar^T, hist^T, hist0bar^T).
+// The transposed reduce_by_index: [header][2 n-planes [d][n]: vals^T,
+// valsbar^T][3 m-planes [d][m]: hist0^T / histbar^T, hist^T, hist0bar^T]
+// [d per-column scalar workspaces, each with its own header].
 struct VLayout {
-    size_t nplane[4], mplane[3], col, col_stride, bytes;
+    size_t nplane[2], mplane[3], col, col_stride, bytes;
 };
 
 static size_t scalar_ws(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m) {
@@ -102,21 +104,20 @@ static size_t scalar_saved(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, in
     }
 }
 
-static VLayout vlayout(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
+static VLayout vlayout(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
     VLayout L{};
     const size_t e = dt == ADC_F64 ? 8 : 4;
-    const int np = kind == ADC_SCAN ? 4 : 2, mp = kind == ADC_HIST ? 3 : 0;
     size_t o = kWsHeader;
-    for (int i = 0; i < np; ++i) {
+    for (int i = 0; i < 2; ++i) {
         L.nplane[i] = o;
         o = align_up(o + (size_t)d * plane_ld(n) * e, 256);
     }
-    for (int i = 0; i < mp; ++i) {
+    for (int i = 0; i < 3; ++i) {
         L.mplane[i] = o;
         o = align_up(o + (size_t)d * plane_ld(m) * e, 256);
     }
     L.col = o;
-    L.col_stride = align_up(scalar_ws(kind, op, dt, n, m), 256);
+    L.col_stride = align_up(scalar_ws(ADC_HIST, op, dt, n, m), 256);
     L.bytes = o + (size_t)d * L.col_stride;
     return L;
 }
@@ -135,12 +136,21 @@ static size_t vhist_direct_ws(int64_t m, int64_t d) {
     return kWsHeader + align_up((size_t)num_sms() * (size_t)m * (size_t)d * 8, 256);
 }
 
+// The direct scan (below) keeps two rows of column states (at most 16 bytes
+// each) per block: the block folds and their exclusive prefixes.
+constexpr int kVScanMaxBlocksPerSM = 8;
+static size_t vscan_states_bytes(int64_t d) {
+    return align_up((size_t)num_sms() * kVScanMaxBlocksPerSM * (size_t)d * 16, 256);
+}
+static size_t vscan_direct_ws(int64_t d) { return kWsHeader + 2 * vscan_states_bytes(d); }
+
 size_t vws_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
     if (scalar_ws(kind, op, dt, n, m) == 0) return 0;
     if (kind == ADC_REDUCE)  // the direct form: one partial row of column states per block
         return kWsHeader + align_up((size_t)num_sms() * 8 * (size_t)d * 16, 256);
     if (kind == ADC_HIST && vhist_direct(op, dt, m, d)) return vhist_direct_ws(m, d);
-    return vlayout(kind, op, dt, n, m, d).bytes;
+    if (kind == ADC_SCAN) return d == 1 ? scan_ws_bytes(op, dt, n) : vscan_direct_ws(d);
+    return vlayout(op, dt, n, m, d).bytes;
 }
 size_t vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d) {
     if (kind == ADC_SCAN) return 16;
@@ -385,47 +395,288 @@ adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void
                              static_cast<float *>(xbar), accumulate, s);
 }
 
-adc_status vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s) {
-    const VLayout L = vlayout(ADC_SCAN, op, dt, n, 0, d);
-    const size_t e = dt == ADC_F64 ? 8 : 4;
-    char *w = static_cast<char *>(ws);
-    char *xt = w + L.nplane[0], *yt = w + L.nplane[1];
-    adc_status st = to_plane(dt, n, d, x, xt, s);
-    if (st != ADC_OK) return st;
-    const Cols cols{w + L.col, L.col_stride};
-    for (int64_t c = 0; c < d; ++c) {
-        bool ok;
-        char *cw = cols.ws(c, s, &ok);
-        if (!ok) return ADC_ERR_CUDA;
-        if ((st = scan_fwd(op, dt, n, xt + (size_t)c * plane_ld(n) * e, yt + (size_t)c * plane_ld(n) * e, cw, s)) != ADC_OK) return st;
+// ------------------------------------------------------ scan, direct form --
+// The Iswim rule makes the vectorised scan d independent column scans (and
+// its vjp d column vjps).  Rather than transposing, the rows are scanned where
+// they lie, in three launches with no inter-block waits:
+//   1. block b folds its contiguous range of rows into one state per column;
+//   2. one warp per column turns the G block states into exclusive prefixes;
+//   3. block b rescans its range from its prefixes, tile by tile.
+// Threads t < P*d (P = floor(256 / d) parts) own column c = t mod d and part
+// p = t / d; a tile is P*RP consecutive rows, part p its RP rows from
+// p*RP on, held in registers.  A warp's load then covers whole row segments
+// (32 / d parts of d columns), and consecutive rows follow in its next load.
+// The tile's part states are combined across parts by a Hillis-Steele scan in
+// shared memory.  Reverse scans (the vjps, Sec. 5) run in logical order
+// L = n-1-i.  Traffic: the inputs twice, the outputs once.
+constexpr int kVScanThreads = 256;
+
+template <typename T> struct VAff { T v, c; };  // lambda -> v + c * lambda
+
+template <typename T, int K> struct VScanFwd {  // K: 0 add, 1 mul, 2 min, 3 max
+    using S = T;
+    struct Aux {};
+    static constexpr bool kRev = false;
+    const T *__restrict__ x;
+    T *__restrict__ y;
+    int64_t d;
+    __device__ S identity() const {
+        return K == 0 ? T(0) : K == 1 ? T(1) : K == 2 ? Num<T>::inf() : -Num<T>::inf();
     }
-    if ((st = from_plane(dt, n, d, yt, y, s)) != ADC_OK) return st;
-    return finish(w, L, d, s);
+    __device__ S combine(const S &a, const S &b) const {
+        if (K == 0) return a + b;
+        if (K == 1) return a * b;
+        return (K == 3 ? (b > a) : (b < a)) ? b : a;  // the earlier value wins ties
+    }
+    __device__ S state(int64_t i, int64_t c, Aux &) const { return __ldg(x + i * d + c); }
+    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &) const { y[i * d + c] = inc; }
+};
+
+// + scan vjp: xbar_i = sum_{j >= i} ybar_j (a reverse + scan).
+template <typename T> struct VScanVjpAdd {
+    using S = T;
+    struct Aux { T old; };
+    static constexpr bool kRev = true;
+    const T *__restrict__ ybar;
+    T *__restrict__ xbar;
+    int64_t d;
+    int accumulate;
+    __device__ S identity() const { return T(0); }
+    __device__ S combine(const S &a, const S &b) const { return a + b; }
+    __device__ S state(int64_t i, int64_t c, Aux &a) const {
+        a.old = accumulate ? xbar[i * d + c] : T(0);
+        return __ldg(ybar + i * d + c);
+    }
+    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &a) const {
+        xbar[i * d + c] = accumulate ? a.old + inc : inc;
+    }
+};
+
+// * and min / max scan vjps: the recurrence lambda_i = ybar_i + J_{i+1}
+// lambda_{i+1} as a reverse scan of affine maps (Sec. 5.1), with
+// J_{i+1} = x_{i+1} for * and the 0/1 "y_i selected" for min / max; then
+// xbar_i = y_{i-1} lambda_i (*) or [x_i selected at step i] lambda_i.
+template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
+    using S = VAff<T>;
+    struct Aux { T g, old; };
+    static constexpr bool kRev = true;
+    const T *__restrict__ x, *__restrict__ y, *__restrict__ ybar;
+    T *__restrict__ xbar;
+    int64_t n, d;
+    int accumulate;
+    static __device__ __forceinline__ bool beats(T a, T b) { return K == 3 ? (a > b) : (a < b); }
+    __device__ S identity() const { return {T(0), T(1)}; }
+    __device__ S combine(const S &acc, const S &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
+    __device__ S state(int64_t i, int64_t c, Aux &a) const {
+        const int64_t f = i * d + c;
+        a.old = accumulate ? xbar[f] : T(0);
+        const T xn = i + 1 < n ? __ldg(x + f + d) : T(1);
+        if (K == 1) {
+            a.g = i > 0 ? __ldg(y + f - d) : T(1);
+            return {__ldg(ybar + f), xn};
+        }
+        const T yi = __ldg(y + f);
+        a.g = (i == 0 || beats(__ldg(x + f), __ldg(y + f - d))) ? T(1) : T(0);
+        return {__ldg(ybar + f), (i + 1 < n && beats(xn, yi)) ? T(0) : T(1)};
+    }
+    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &a) const {
+        const T g = a.g * inc.v;
+        xbar[i * d + c] = accumulate ? a.old + g : g;
+    }
+};
+
+// Block b's logical rows [l0, l1): the G blocks split n as evenly as possible.
+__device__ __forceinline__ void vscan_range(int64_t n, int64_t b, int64_t G, int64_t *l0, int64_t *l1) {
+    const int64_t per = n / G, extra = n % G;
+    *l0 = b * per + (b < extra ? b : extra);
+    *l1 = *l0 + per + (b < extra ? 1 : 0);
+}
+
+template <class Op> __device__ __forceinline__ int64_t vscan_phys(int64_t L, int64_t n) {
+    return Op::kRev ? n - 1 - L : L;
+}
+
+template <class Op, int RP>
+__global__ void __launch_bounds__(kVScanThreads)
+k_vscan_fold(const Op op, const int64_t n, const int64_t d, typename Op::S *__restrict__ agg) {
+    using S = typename Op::S;
+    __shared__ S s_part[kVScanThreads];
+    const int t = threadIdx.x;
+    const int P = kVScanThreads / (int)d;
+    const bool active = t < P * (int)d;
+    const int64_t c = t % d, p = t / d;
+    int64_t l0, l1;
+    vscan_range(n, blockIdx.x, gridDim.x, &l0, &l1);
+    S a = op.identity();
+    if (active) {
+        // part p folds a contiguous piece of the range, RP loads in flight
+        const int64_t per = (l1 - l0 + P - 1) / P;
+        const int64_t lo = l0 + p * per, hi = lo + per < l1 ? lo + per : l1;
+        int64_t L = lo;
+        for (; L + RP <= hi; L += RP) {
+            S v[RP];
+            typename Op::Aux aux;
+#pragma unroll
+            for (int k = 0; k < RP; ++k) v[k] = op.state(vscan_phys<Op>(L + k, n), c, aux);
+#pragma unroll
+            for (int k = 0; k < RP; ++k) a = op.combine(a, v[k]);
+        }
+        for (; L < hi; ++L) {
+            typename Op::Aux aux;
+            a = op.combine(a, op.state(vscan_phys<Op>(L, n), c, aux));
+        }
+    }
+    s_part[t] = a;
+    __syncthreads();
+    if (t < d) {
+        S r = op.identity();
+        for (int q = 0; q < P; ++q) r = op.combine(r, s_part[q * d + t]);
+        agg[(int64_t)blockIdx.x * d + t] = r;
+    }
+}
+
+// One warp per column: the exclusive prefixes of the G block states, in order.
+template <class Op>
+__global__ void k_vscan_prefix(const Op op, const typename Op::S *__restrict__ agg, const int G, const int64_t d,
+                               typename Op::S *__restrict__ pre) {
+    using S = typename Op::S;
+    const int lane = threadIdx.x;
+    const int64_t c = blockIdx.x;
+    const int per = (G + kWarp - 1) / kWarp;
+    const int g0 = lane * per, g1 = g0 + per < G ? g0 + per : G;
+    S v = op.identity();
+    for (int g = g0; g < g1; ++g) v = op.combine(v, agg[(int64_t)g * d + c]);
+    const S inc = warp_inclusive_scan(op, v);
+    S run = shfl_up(inc, 1);
+    if (lane == 0) run = op.identity();
+    for (int g = g0; g < g1; ++g) {
+        pre[(int64_t)g * d + c] = run;
+        run = op.combine(run, agg[(int64_t)g * d + c]);
+    }
+}
+
+template <class Op, int RP>
+__global__ void __launch_bounds__(kVScanThreads)
+k_vscan_apply(const Op op, const int64_t n, const int64_t d, const typename Op::S *__restrict__ pre) {
+    using S = typename Op::S;
+    __shared__ S s_part[kVScanThreads];
+    const int t = threadIdx.x;
+    const int P = kVScanThreads / (int)d;
+    const bool active = t < P * (int)d;
+    const int64_t c = t % d, p = t / d;
+    int64_t l0, l1;
+    vscan_range(n, blockIdx.x, gridDim.x, &l0, &l1);
+    S carry = active ? pre[(int64_t)blockIdx.x * d + c] : op.identity();
+    for (int64_t lt = l0; lt < l1; lt += (int64_t)P * RP) {
+        const int64_t lp = lt + p * RP;
+        S st[RP];
+        typename Op::Aux aux[RP];
+#pragma unroll
+        for (int k = 0; k < RP; ++k)
+            st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+        S a = op.identity();
+#pragma unroll
+        for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
+        s_part[t] = a;
+        __syncthreads();
+        // inclusive scan over the parts of each column (Hillis-Steele)
+        for (int sh = 1; sh < P; sh <<= 1) {
+            const bool h = active && p >= sh;
+            S o = op.identity();
+            if (h) o = s_part[t - sh * d];
+            __syncthreads();
+            if (h) {
+                a = op.combine(o, a);
+                s_part[t] = a;
+            }
+            __syncthreads();
+        }
+        S r = (active && p > 0) ? op.combine(carry, s_part[t - d]) : carry;
+        const S tile = active ? s_part[(P - 1) * d + c] : op.identity();
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            if (active && lp + k < l1) {
+                r = op.combine(r, st[k]);
+                op.store(vscan_phys<Op>(lp + k, n), c, r, aux[k]);
+            }
+        }
+        carry = op.combine(carry, tile);
+        __syncthreads();  // s_part is rewritten by the next tile
+    }
+}
+
+// One wave of the rescan kernel: its resident blocks on every SM (cached per
+// device), fewer for short inputs (at least 64 rows a block).
+template <class Op, int RP> static int vscan_grid(int64_t n) {
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
+    if (cache[dev] == 0) {
+        int b = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vscan_apply<Op, RP>, kVScanThreads, 0) !=
+                cudaSuccess ||
+            b < 1)
+            b = 1;
+        cache[dev] = b < kVScanMaxBlocksPerSM ? b : kVScanMaxBlocksPerSM;
+    }
+    const int64_t want = (n + 63) / 64;
+    const int64_t cap = (int64_t)num_sms() * cache[dev];
+    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+}
+
+template <class Op, int RP> static adc_status vscan_run(const Op &op, int64_t n, int64_t d, char *ws, cudaStream_t s) {
+    using S = typename Op::S;
+    if (n == 0) return ADC_OK;
+    const int G = vscan_grid<Op, RP>(n);
+    S *agg = reinterpret_cast<S *>(ws + kWsHeader);
+    S *pre = reinterpret_cast<S *>(ws + kWsHeader + vscan_states_bytes(d));
+    k_vscan_fold<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, agg);
+    k_vscan_prefix<Op><<<(unsigned)d, kWarp, 0, s>>>(op, agg, G, d, pre);
+    k_vscan_apply<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, pre);
+    return check_launch();
+}
+
+template <typename T>
+static adc_status vscan_fwd_t(adc_op op, int64_t n, int64_t d, const T *x, T *y, char *ws, cudaStream_t s) {
+    switch (op) {
+    case ADC_OP_ADD: return vscan_run<VScanFwd<T, 0>, 16>({x, y, d}, n, d, ws, s);
+    case ADC_OP_MUL: return vscan_run<VScanFwd<T, 1>, 16>({x, y, d}, n, d, ws, s);
+    case ADC_OP_MIN: return vscan_run<VScanFwd<T, 2>, 16>({x, y, d}, n, d, ws, s);
+    case ADC_OP_MAX: return vscan_run<VScanFwd<T, 3>, 16>({x, y, d}, n, d, ws, s);
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename T>
+static adc_status vscan_vjp_t(adc_op op, int64_t n, int64_t d, const T *x, const T *y, const T *ybar, T *xbar,
+                              int acc, char *ws, cudaStream_t s) {
+    switch (op) {
+    case ADC_OP_ADD: return vscan_run<VScanVjpAdd<T>, 16>({ybar, xbar, d, acc}, n, d, ws, s);
+    case ADC_OP_MUL: return vscan_run<VScanVjpAff<T, 1>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
+    case ADC_OP_MIN: return vscan_run<VScanVjpAff<T, 2>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
+    case ADC_OP_MAX: return vscan_run<VScanVjpAff<T, 3>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+// d = 1 is the scalar scan itself; wider rows take the direct form above.
+adc_status vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s) {
+    if (d == 1) return scan_fwd(op, dt, n, x, y, ws, s);
+    char *w = static_cast<char *>(ws);
+    if (dt == ADC_F64)
+        return vscan_fwd_t<double>(op, n, d, static_cast<const double *>(x), static_cast<double *>(y), w, s);
+    return vscan_fwd_t<float>(op, n, d, static_cast<const float *>(x), static_cast<float *>(y), w, s);
 }
 
 adc_status vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
                      void *xbar, int accumulate, void *ws, cudaStream_t s) {
-    const VLayout L = vlayout(ADC_SCAN, op, dt, n, 0, d);
-    const size_t e = dt == ADC_F64 ? 8 : 4;
+    if (d == 1) return scan_vjp(op, dt, n, x, y, ybar, xbar, accumulate, ws, s);
     char *w = static_cast<char *>(ws);
-    char *xt = w + L.nplane[0], *yt = w + L.nplane[1], *ybt = w + L.nplane[2], *xbt = w + L.nplane[3];
-    adc_status st;
-    if (op != ADC_OP_ADD) {
-        if ((st = to_plane(dt, n, d, x, xt, s)) != ADC_OK) return st;
-        if ((st = to_plane(dt, n, d, y, yt, s)) != ADC_OK) return st;
-    }
-    if ((st = to_plane(dt, n, d, ybar, ybt, s)) != ADC_OK) return st;
-    if (accumulate && (st = to_plane(dt, n, d, xbar, xbt, s)) != ADC_OK) return st;
-    const Cols cols{w + L.col, L.col_stride};
-    for (int64_t c = 0; c < d; ++c) {
-        bool ok;
-        char *cw = cols.ws(c, s, &ok);
-        if (!ok) return ADC_ERR_CUDA;
-        const size_t off = (size_t)c * plane_ld(n) * e;
-        if ((st = scan_vjp(op, dt, n, xt + off, yt + off, ybt + off, xbt + off, accumulate, cw, s)) != ADC_OK) return st;
-    }
-    if ((st = from_plane(dt, n, d, xbt, xbar, s)) != ADC_OK) return st;
-    return finish(w, L, d, s);
+    if (dt == ADC_F64)
+        return vscan_vjp_t<double>(op, n, d, static_cast<const double *>(x), static_cast<const double *>(y),
+                                   static_cast<const double *>(ybar), static_cast<double *>(xbar), accumulate, w, s);
+    return vscan_vjp_t<float>(op, n, d, static_cast<const float *>(x), static_cast<const float *>(y),
+                              static_cast<const float *>(ybar), static_cast<float *>(xbar), accumulate, w, s);
 }
 
 // -------------------------------------------- reduce_by_index, direct form --
@@ -602,7 +853,7 @@ adc_status vhist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, c
         if (op == ADC_OP_MIN) return vhist_direct_fwd<float, 1>(n, m, d, keys, v, h0, h, sv, svb, w, s);
         return vhist_direct_fwd<float, 2>(n, m, d, keys, v, h0, h, sv, svb, w, s);
     }
-    const VLayout L = vlayout(ADC_HIST, op, dt, n, m, d);
+    const VLayout L = vlayout(op, dt, n, m, d);
     const size_t e = dt == ADC_F64 ? 8 : 4;
     char *w = static_cast<char *>(ws);
     char *vt = w + L.nplane[0], *h0t = w + L.mplane[0], *ht = w + L.mplane[1];
@@ -641,7 +892,7 @@ adc_status vhist_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, c
         if (op == ADC_OP_MIN) return vhist_direct_vjp<float, 1>(n, m, d, keys, sv, svb, hb, vb, h0b, accumulate, s);
         return vhist_direct_vjp<float, 2>(n, m, d, keys, sv, svb, hb, vb, h0b, accumulate, s);
     }
-    const VLayout L = vlayout(ADC_HIST, op, dt, n, m, d);
+    const VLayout L = vlayout(op, dt, n, m, d);
     const size_t e = dt == ADC_F64 ? 8 : 4;
     char *w = static_cast<char *>(ws);
     char *vt = w + L.nplane[0], *vbt = w + L.nplane[1];

@@ -68,28 +68,43 @@ def test_vreduce(op, d, dt):
             col_tol("vreduce * vjp", host(xb).reshape(n, d), xr.reshape(n, d), n, M, rtol)
 
 
+def check_vscan(g, op, n, d, dt):
+    rtol = rtol_for(dt)
+    x = values(g, op, n, d, dt)
+    y = adcomb.vscan_fwd(op, dev(x))
+    ref = oracle.vscan_fwd(op, x)
+    if op in ("min", "max"):
+        assert np.array_equal(host(y), ref.astype(dt))
+    else:
+        col_tol("vscan fwd", host(y).reshape(n, d), ref.reshape(n, d), np.arange(1, n + 1), colscale(x, op), rtol)
+    yb = synth.normal(g, (n, d), dt)
+    for acc in (False, True):
+        old = synth.normal(g, (n, d), dt)
+        xb = adcomb.vscan_vjp(op, dev(x), y, dev(yb), xbar=dev(old) if acc else None, accumulate=acc)
+        xr = oracle.vscan_vjp(op, x, yb) + (old if acc else 0)
+        M = (np.abs(yb).max(0) if n else 0) * (colscale(x, op) if op == "mul" else 1.0) * 4 + \
+            (np.abs(old) if acc else 0)
+        col_tol(f"vscan {op} vjp", host(xb).reshape(n, d), xr.reshape(n, d), np.arange(n, 0, -1), M, rtol)
+
+
+# d = 1 is the scalar scan; d = 2, 3, 10, 16, 33, 64 give 128, 85, 25, 16, 7
+# and 4 parts per block in the direct form (33: 25 idle threads), and n spans
+# one partial tile (1000) to several blocks of one tile each (100_003)
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("d", [1, 3, 16])
+@pytest.mark.parametrize("d", [1, 2, 3, 10, 16, 33, 64])
 @pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
 def test_vscan(op, d, dt):
     g = np.random.default_rng(61 + d)
-    rtol = rtol_for(dt)
     for n in [0, 1, 1000, 100_003]:
-        x = values(g, op, n, d, dt)
-        y = adcomb.vscan_fwd(op, dev(x))
-        ref = oracle.vscan_fwd(op, x)
-        if op in ("min", "max"):
-            assert np.array_equal(host(y), ref.astype(dt))
-        else:
-            col_tol("vscan fwd", host(y).reshape(n, d), ref.reshape(n, d), np.arange(1, n + 1), colscale(x, op), rtol)
-        yb = synth.normal(g, (n, d), dt)
-        for acc in (False, True):
-            old = synth.normal(g, (n, d), dt)
-            xb = adcomb.vscan_vjp(op, dev(x), y, dev(yb), xbar=dev(old) if acc else None, accumulate=acc)
-            xr = oracle.vscan_vjp(op, x, yb) + (old if acc else 0)
-            M = (np.abs(yb).max(0) if n else 0) * (colscale(x, op) if op == "mul" else 1.0) * 4 + \
-                (np.abs(old) if acc else 0)
-            col_tol(f"vscan {op} vjp", host(xb).reshape(n, d), xr.reshape(n, d), np.arange(n, 0, -1), M, rtol)
+        check_vscan(g, op, n, d, dt)
+
+
+@pytest.mark.parametrize("d", [3, 16])
+@pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
+def test_vscan_many_tiles_per_block(op, d):
+    """Enough rows that every block of the direct form rescans several tiles,
+    carrying each column's prefix from tile to tile."""
+    check_vscan(np.random.default_rng(90 + d), op, 2_000_003, d, np.float32)
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
