@@ -137,10 +137,11 @@ static size_t vhist_direct_ws(int64_t m, int64_t d) {
 }
 
 // The direct scan (below) keeps two rows of column states (at most 16 bytes
-// each) per block: the block folds and their exclusive prefixes.
+// each) per unit (a warp, or a block when d > 32): the unit folds and their
+// exclusive prefixes.
 constexpr int kVScanMaxBlocksPerSM = 8;
 static size_t vscan_states_bytes(int64_t d) {
-    return align_up((size_t)num_sms() * kVScanMaxBlocksPerSM * (size_t)d * 16, 256);
+    return align_up((size_t)num_sms() * kVScanMaxBlocksPerSM * 8 * (size_t)d * 16, 256);
 }
 static size_t vscan_direct_ws(int64_t d) { return kWsHeader + 2 * vscan_states_bytes(d); }
 
@@ -398,17 +399,19 @@ adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void
 // ------------------------------------------------------ scan, direct form --
 // The Iswim rule makes the vectorised scan d independent column scans (and
 // its vjp d column vjps).  Rather than transposing, the rows are scanned where
-// they lie, in three launches with no inter-block waits:
-//   1. block b folds its contiguous range of rows into one state per column;
-//   2. one warp per column turns the G block states into exclusive prefixes;
-//   3. block b rescans its range from its prefixes, tile by tile.
-// Threads t < P*d (P = floor(256 / d) parts) own column c = t mod d and part
-// p = t / d; a tile is P*RP consecutive rows, part p its RP rows from
-// p*RP on, held in registers.  A warp's load then covers whole row segments
+// they lie, in three launches with no inter-unit waits:
+//   1. unit u folds its contiguous range of rows into one state per column;
+//   2. per column, the U unit states become exclusive prefixes;
+//   3. unit u rescans its range from its prefixes, tile by tile.
+// A unit is a warp when d <= 32, else a block of 256 threads.  Its threads
+// t < P*d (P = floor(threads / d) parts) own column c = t mod d and part
+// p = t / d; a tile is P*RP consecutive rows, part p its RP rows from p*RP
+// on, held in registers.  A warp's load then covers whole row segments
 // (32 / d parts of d columns), and consecutive rows follow in its next load.
-// The tile's part states are combined across parts by a Hillis-Steele scan in
-// shared memory.  Reverse scans (the vjps, Sec. 5) run in logical order
-// L = n-1-i.  Traffic: the inputs twice, the outputs once.
+// The tile's part states are combined across parts by shuffles (warp units)
+// or a Hillis-Steele scan in shared memory (block units).  Reverse scans
+// (the vjps, Sec. 5) run in logical order L = n-1-i.  Traffic: the inputs
+// twice, the outputs once.
 constexpr int kVScanThreads = 256;
 
 template <typename T> struct VAff { T v, c; };  // lambda -> v + c * lambda
@@ -605,34 +608,161 @@ k_vscan_apply(const Op op, const int64_t n, const int64_t d, const typename Op::
     }
 }
 
-// One wave of the rescan kernel: its resident blocks on every SM (cached per
-// device), fewer for short inputs (at least 64 rows a block).
-template <class Op, int RP> static int vscan_grid(int64_t n) {
+// ---- warp form, d <= 32: every warp is a unit of its own, with a range of
+// rows, its parts (P = floor(32 / d)) and their cross-part scan in one warp
+// (shuffles by d, 2d, 4d, ...), so no block barrier is ever waited on.
+constexpr int kVScanWarps = kVScanThreads / kWarp;
+static_assert(kVScanWarps <= 8, "the workspace holds 8 units per resident block");
+
+// Column c's inclusive scan over the warp's parts: lane p*d + c combines the
+// states of lanes c, d + c, ..., p*d + c in order (lanes >= P*d never feed
+// an active lane: shuffles only read lower lanes).
+template <class Op>
+__device__ __forceinline__ typename Op::S warp_parts_scan(const Op &op, typename Op::S a, int d, int P) {
+    const int lane = threadIdx.x & 31;
+    for (int sh = d; sh < P * d; sh <<= 1) {
+        const typename Op::S o = shfl_up(a, sh);
+        if (lane >= sh) a = op.combine(o, a);
+    }
+    return a;
+}
+
+template <class Op, int RP>
+__global__ void __launch_bounds__(kVScanThreads)
+k_vscan_wfold(const Op op, const int64_t n, const int64_t d, const int64_t U, typename Op::S *__restrict__ agg) {
+    using S = typename Op::S;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = (int64_t)blockIdx.x * kVScanWarps + (threadIdx.x >> 5);
+    if (u >= U) return;  // whole warps
+    const int P = kWarp / (int)d;
+    const bool active = lane < P * (int)d;
+    const int64_t c = lane % d, p = lane / d;
+    int64_t l0, l1;
+    vscan_range(n, u, U, &l0, &l1);
+    S a = op.identity();
+    if (active) {
+        // part p folds a contiguous piece of the unit, RP loads in flight
+        const int64_t per = (l1 - l0 + P - 1) / P;
+        const int64_t lo = l0 + p * per, hi = lo + per < l1 ? lo + per : l1;
+        int64_t L = lo;
+        for (; L + RP <= hi; L += RP) {
+            S v[RP];
+            typename Op::Aux aux;
+#pragma unroll
+            for (int k = 0; k < RP; ++k) v[k] = op.state(vscan_phys<Op>(L + k, n), c, aux);
+#pragma unroll
+            for (int k = 0; k < RP; ++k) a = op.combine(a, v[k]);
+        }
+        for (; L < hi; ++L) {
+            typename Op::Aux aux;
+            a = op.combine(a, op.state(vscan_phys<Op>(L, n), c, aux));
+        }
+    }
+    a = warp_parts_scan(op, a, (int)d, P);
+    if (active && p == P - 1) agg[u * d + c] = a;
+}
+
+// One block per column: the exclusive prefixes of the U unit states, in order.
+constexpr int kVPrefixThreads = 1024;
+template <class Op>
+__global__ void __launch_bounds__(kVPrefixThreads)
+k_vscan_wprefix(const Op op, const typename Op::S *__restrict__ agg, const int64_t U, const int64_t d,
+                typename Op::S *__restrict__ pre) {
+    using S = typename Op::S;
+    __shared__ S s_w[kVPrefixThreads / kWarp];
+    const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+    const int64_t c = blockIdx.x;
+    const int64_t per = (U + kVPrefixThreads - 1) / kVPrefixThreads;
+    const int64_t g0 = t * per, g1 = g0 + per < U ? g0 + per : U;
+    S v = op.identity();
+    for (int64_t g = g0; g < g1; ++g) v = op.combine(v, agg[g * d + c]);
+    const S inc = warp_inclusive_scan(op, v);
+    if (lane == kWarp - 1) s_w[w] = inc;
+    __syncthreads();
+    S run = op.identity();
+    for (int j = 0; j < w; ++j) run = op.combine(run, s_w[j]);
+    S ex = shfl_up(inc, 1);
+    if (lane > 0) run = op.combine(run, ex);
+    for (int64_t g = g0; g < g1; ++g) {
+        pre[g * d + c] = run;
+        run = op.combine(run, agg[g * d + c]);
+    }
+}
+
+template <class Op, int RP>
+__global__ void __launch_bounds__(kVScanThreads)
+k_vscan_wapply(const Op op, const int64_t n, const int64_t d, const int64_t U, const typename Op::S *__restrict__ pre) {
+    using S = typename Op::S;
+    const int lane = threadIdx.x & 31;
+    const int64_t u = (int64_t)blockIdx.x * kVScanWarps + (threadIdx.x >> 5);
+    if (u >= U) return;  // whole warps
+    const int P = kWarp / (int)d;
+    const bool active = lane < P * (int)d;
+    const int64_t c = lane % d, p = lane / d;
+    const int last = (P - 1) * (int)d + (int)c;  // the lane with column c's tile total
+    int64_t l0, l1;
+    vscan_range(n, u, U, &l0, &l1);
+    S carry = active ? pre[u * d + c] : op.identity();
+    for (int64_t lt = l0; lt < l1; lt += (int64_t)P * RP) {
+        const int64_t lp = lt + p * RP;
+        S st[RP];
+        typename Op::Aux aux[RP];
+#pragma unroll
+        for (int k = 0; k < RP; ++k)
+            st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+        S a = op.identity();
+#pragma unroll
+        for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
+        a = warp_parts_scan(op, a, (int)d, P);
+        const S ex = P > 1 ? shfl_up(a, (int)d) : a;  // P is warp-uniform; read for p > 0 only
+        const S tile = shfl_idx(a, last);
+        S r = p > 0 ? op.combine(carry, ex) : carry;
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            if (active && lp + k < l1) {
+                r = op.combine(r, st[k]);
+                op.store(vscan_phys<Op>(lp + k, n), c, r, aux[k]);
+            }
+        }
+        carry = op.combine(carry, tile);
+    }
+}
+
+// Units of one wave of the rescan kernel: its resident blocks on every SM
+// (cached per device) times the units a block holds, fewer for short inputs
+// (at least 64 rows a unit).
+template <class Op, int RP, bool WARP> static int64_t vscan_units(int64_t n) {
     static int cache[64] = {0};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
     if (cache[dev] == 0) {
         int b = 0;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_vscan_apply<Op, RP>, kVScanThreads, 0) !=
-                cudaSuccess ||
-            b < 1)
-            b = 1;
+        const void *k = WARP ? (const void *)k_vscan_wapply<Op, RP> : (const void *)k_vscan_apply<Op, RP>;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kVScanThreads, 0) != cudaSuccess || b < 1) b = 1;
         cache[dev] = b < kVScanMaxBlocksPerSM ? b : kVScanMaxBlocksPerSM;
     }
     const int64_t want = (n + 63) / 64;
-    const int64_t cap = (int64_t)num_sms() * cache[dev];
-    return (int)(want < 1 ? 1 : want < cap ? want : cap);
+    const int64_t cap = (int64_t)num_sms() * cache[dev] * (WARP ? kVScanWarps : 1);
+    return want < 1 ? 1 : want < cap ? want : cap;
 }
 
 template <class Op, int RP> static adc_status vscan_run(const Op &op, int64_t n, int64_t d, char *ws, cudaStream_t s) {
     using S = typename Op::S;
     if (n == 0) return ADC_OK;
-    const int G = vscan_grid<Op, RP>(n);
     S *agg = reinterpret_cast<S *>(ws + kWsHeader);
     S *pre = reinterpret_cast<S *>(ws + kWsHeader + vscan_states_bytes(d));
-    k_vscan_fold<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, agg);
-    k_vscan_prefix<Op><<<(unsigned)d, kWarp, 0, s>>>(op, agg, G, d, pre);
-    k_vscan_apply<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, pre);
+    if (d <= kWarp) {
+        const int64_t U = vscan_units<Op, RP, true>(n);
+        const unsigned blocks = (unsigned)((U + kVScanWarps - 1) / kVScanWarps);
+        k_vscan_wfold<Op, RP><<<blocks, kVScanThreads, 0, s>>>(op, n, d, U, agg);
+        k_vscan_wprefix<Op><<<(unsigned)d, kVPrefixThreads, 0, s>>>(op, agg, U, d, pre);
+        k_vscan_wapply<Op, RP><<<blocks, kVScanThreads, 0, s>>>(op, n, d, U, pre);
+    } else {
+        const int G = (int)vscan_units<Op, RP, false>(n);
+        k_vscan_fold<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, agg);
+        k_vscan_prefix<Op><<<(unsigned)d, kWarp, 0, s>>>(op, agg, G, d, pre);
+        k_vscan_apply<Op, RP><<<G, kVScanThreads, 0, s>>>(op, n, d, pre);
+    }
     return check_launch();
 }
 

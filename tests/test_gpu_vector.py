@@ -87,11 +87,12 @@ def check_vscan(g, op, n, d, dt):
         col_tol(f"vscan {op} vjp", host(xb).reshape(n, d), xr.reshape(n, d), np.arange(n, 0, -1), M, rtol)
 
 
-# d = 1 is the scalar scan; d = 2, 3, 10, 16, 33, 64 give 128, 85, 25, 16, 7
-# and 4 parts per block in the direct form (33: 25 idle threads), and n spans
-# one partial tile (1000) to several blocks of one tile each (100_003)
+# d = 1 is the scalar scan; in the direct form d = 2, 3, 10, 16, 32 run warp
+# units of 16, 10, 3, 2 and 1 parts (10: 2 idle lanes), d = 33 and 64 block
+# units of 7 and 4 parts (33: 25 idle threads); n spans one partial tile
+# (1000) to many units of one tile or less (100_003)
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
-@pytest.mark.parametrize("d", [1, 2, 3, 10, 16, 33, 64])
+@pytest.mark.parametrize("d", [1, 2, 3, 10, 16, 32, 33, 64])
 @pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
 def test_vscan(op, d, dt):
     g = np.random.default_rng(61 + d)
@@ -99,11 +100,12 @@ def test_vscan(op, d, dt):
         check_vscan(g, op, n, d, dt)
 
 
-@pytest.mark.parametrize("d", [3, 16])
+@pytest.mark.parametrize("d", [3, 16, 48])
 @pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
-def test_vscan_many_tiles_per_block(op, d):
-    """Enough rows that every block of the direct form rescans several tiles,
-    carrying each column's prefix from tile to tile."""
+def test_vscan_many_tiles_per_unit(op, d):
+    """Enough rows that every unit of the direct form (warps for d = 3, 16,
+    blocks for 48) rescans several tiles, carrying each column's prefix from
+    tile to tile."""
     check_vscan(np.random.default_rng(90 + d), op, 2_000_003, d, np.float32)
 
 
