@@ -419,7 +419,7 @@ template <typename T> struct VAff { T v, c; };  // lambda -> v + c * lambda
 template <typename T, int K> struct VScanFwd {  // K: 0 add, 1 mul, 2 min, 3 max
     using S = T;
     struct Aux {};
-    static constexpr bool kRev = false;
+    static constexpr bool kRev = false, kHaloChunk = false;
     const T *__restrict__ x;
     T *__restrict__ y;
     int64_t d;
@@ -439,7 +439,7 @@ template <typename T, int K> struct VScanFwd {  // K: 0 add, 1 mul, 2 min, 3 max
 template <typename T> struct VScanVjpAdd {
     using S = T;
     struct Aux { T old; };
-    static constexpr bool kRev = true;
+    static constexpr bool kRev = true, kHaloChunk = false;
     const T *__restrict__ ybar;
     T *__restrict__ xbar;
     int64_t d;
@@ -463,6 +463,9 @@ template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
     using S = VAff<T>;
     struct Aux { T g, old; };
     static constexpr bool kRev = true;
+    // fp32 min / max: the rescan loads through vscan_chunk (fp64 would hold
+    // too many registers for it)
+    static constexpr bool kHaloChunk = K != 1 && sizeof(T) == 4;
     const T *__restrict__ x, *__restrict__ y, *__restrict__ ybar;
     T *__restrict__ xbar;
     int64_t n, d;
@@ -497,6 +500,45 @@ __device__ __forceinline__ void vscan_range(int64_t n, int64_t b, int64_t G, int
 
 template <class Op> __device__ __forceinline__ int64_t vscan_phys(int64_t L, int64_t n) {
     return Op::kRev ? n - 1 - L : L;
+}
+
+// The rescan of the min / max scan vjps: they read x and y at the element
+// and at its neighbours (x_{i+1} and y_{i-1}); here each of x and y is loaded
+// once per row of the chunk (logical rows lp .. lp+RP-1, none at or beyond
+// hi) plus one halo row, and the neighbours are taken from registers.
+template <typename T, int K, int RP>
+__device__ __forceinline__ void vscan_chunk(const VScanVjpAff<T, K> &op, int64_t lp, int64_t hi, int64_t n, int64_t c,
+                                            bool active, VAff<T> (&st)[RP],
+                                            typename VScanVjpAff<T, K>::Aux (&aux)[RP]) {
+    static_assert(K == 2 || K == 3, "min / max only");
+    const int64_t d = op.d;
+    int64_t cnt = hi - lp < RP ? hi - lp : RP;
+    if (!active || cnt < 0) cnt = 0;  // nothing is loaded then, not even a halo
+    const int64_t i0 = n - 1 - lp;   // physical rows i0, i0-1, ..., i0-cnt+1 (all >= 0)
+    // X[k] = x[i0 + 1 - k] (X[0]: the halo x_{i0+1}); Y[k] = y[i0 - k] (Y[cnt]: the halo y_{i0-cnt})
+    T X[RP + 1], Y[RP + 1], yb[RP], old[RP];
+#pragma unroll
+    for (int k = 0; k <= RP; ++k) {
+        const int64_t ix = i0 + 1 - k, iy = i0 - k;
+        X[k] = (cnt > 0 && k <= cnt && ix < n) ? __ldg(op.x + ix * d + c) : T(0);
+        Y[k] = (cnt > 0 && k <= cnt && iy >= 0) ? __ldg(op.y + iy * d + c) : T(0);
+        if (k < RP) {
+            yb[k] = k < cnt ? __ldg(op.ybar + iy * d + c) : T(0);
+            old[k] = (k < cnt && op.accumulate) ? op.xbar[iy * d + c] : T(0);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int64_t i = i0 - k;
+        aux[k].old = old[k];
+        if (k >= cnt) {
+            st[k] = op.identity();
+            aux[k].g = T(0);
+        } else {
+            aux[k].g = (i == 0 || op.beats(X[k + 1], Y[k + 1])) ? T(1) : T(0);
+            st[k] = {yb[k], (i + 1 < n && op.beats(X[k], Y[k])) ? T(0) : T(1)};
+        }
+    }
 }
 
 template <class Op, int RP>
@@ -574,9 +616,13 @@ k_vscan_apply(const Op op, const int64_t n, const int64_t d, const typename Op::
         const int64_t lp = lt + p * RP;
         S st[RP];
         typename Op::Aux aux[RP];
+        if constexpr (Op::kHaloChunk) {
+            vscan_chunk(op, lp, l1, n, c, active, st, aux);
+        } else {
 #pragma unroll
-        for (int k = 0; k < RP; ++k)
-            st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+            for (int k = 0; k < RP; ++k)
+                st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+        }
         S a = op.identity();
 #pragma unroll
         for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
@@ -707,9 +753,13 @@ k_vscan_wapply(const Op op, const int64_t n, const int64_t d, const int64_t U, c
         const int64_t lp = lt + p * RP;
         S st[RP];
         typename Op::Aux aux[RP];
+        if constexpr (Op::kHaloChunk) {
+            vscan_chunk(op, lp, l1, n, c, active, st, aux);
+        } else {
 #pragma unroll
-        for (int k = 0; k < RP; ++k)
-            st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+            for (int k = 0; k < RP; ++k)
+                st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
+        }
         S a = op.identity();
 #pragma unroll
         for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
