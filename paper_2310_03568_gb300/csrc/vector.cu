@@ -412,6 +412,9 @@ adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void
 // or a Hillis-Steele scan in shared memory (block units).  Reverse scans
 // (the vjps, Sec. 5) run in logical order L = n-1-i.  Traffic: the inputs
 // twice, the outputs once.
+// An op gives identity(), combine(earlier, later), state(i, f, aux) -- the
+// element state of row i at flat offset f = i*d + c, with what its store
+// needs in aux -- and store(f, inclusive, aux).
 constexpr int kVScanThreads = 256;
 
 template <typename T> struct VAff { T v, c; };  // lambda -> v + c * lambda
@@ -431,8 +434,8 @@ template <typename T, int K> struct VScanFwd {  // K: 0 add, 1 mul, 2 min, 3 max
         if (K == 1) return a * b;
         return (K == 3 ? (b > a) : (b < a)) ? b : a;  // the earlier value wins ties
     }
-    __device__ S state(int64_t i, int64_t c, Aux &) const { return __ldg(x + i * d + c); }
-    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &) const { y[i * d + c] = inc; }
+    __device__ S state(int64_t, int64_t f, Aux &) const { return __ldg(x + f); }
+    __device__ void store(int64_t f, const S &inc, const Aux &) const { y[f] = inc; }
 };
 
 // + scan vjp: xbar_i = sum_{j >= i} ybar_j (a reverse + scan).
@@ -446,13 +449,11 @@ template <typename T> struct VScanVjpAdd {
     int accumulate;
     __device__ S identity() const { return T(0); }
     __device__ S combine(const S &a, const S &b) const { return a + b; }
-    __device__ S state(int64_t i, int64_t c, Aux &a) const {
-        a.old = accumulate ? xbar[i * d + c] : T(0);
-        return __ldg(ybar + i * d + c);
+    __device__ S state(int64_t, int64_t f, Aux &a) const {
+        a.old = accumulate ? xbar[f] : T(0);
+        return __ldg(ybar + f);
     }
-    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &a) const {
-        xbar[i * d + c] = accumulate ? a.old + inc : inc;
-    }
+    __device__ void store(int64_t f, const S &inc, const Aux &a) const { xbar[f] = accumulate ? a.old + inc : inc; }
 };
 
 // * and min / max scan vjps: the recurrence lambda_i = ybar_i + J_{i+1}
@@ -473,8 +474,7 @@ template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
     static __device__ __forceinline__ bool beats(T a, T b) { return K == 3 ? (a > b) : (a < b); }
     __device__ S identity() const { return {T(0), T(1)}; }
     __device__ S combine(const S &acc, const S &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
-    __device__ S state(int64_t i, int64_t c, Aux &a) const {
-        const int64_t f = i * d + c;
+    __device__ S state(int64_t i, int64_t f, Aux &a) const {
         a.old = accumulate ? xbar[f] : T(0);
         const T xn = i + 1 < n ? __ldg(x + f + d) : T(1);
         if (K == 1) {
@@ -485,9 +485,9 @@ template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
         a.g = (i == 0 || beats(__ldg(x + f), __ldg(y + f - d))) ? T(1) : T(0);
         return {__ldg(ybar + f), (i + 1 < n && beats(xn, yi)) ? T(0) : T(1)};
     }
-    __device__ void store(int64_t i, int64_t c, const S &inc, const Aux &a) const {
+    __device__ void store(int64_t f, const S &inc, const Aux &a) const {
         const T g = a.g * inc.v;
-        xbar[i * d + c] = accumulate ? a.old + g : g;
+        xbar[f] = accumulate ? a.old + g : g;
     }
 };
 
@@ -500,6 +500,46 @@ __device__ __forceinline__ void vscan_range(int64_t n, int64_t b, int64_t G, int
 
 template <class Op> __device__ __forceinline__ int64_t vscan_phys(int64_t L, int64_t n) {
     return Op::kRev ? n - 1 - L : L;
+}
+
+// A rescan chunk: column c at logical rows lp .. lp+RP-1, none at or beyond
+// hi.  Offsets step by -d / +d from the chunk's first row; whole chunks (the
+// common case) run without per-element bounds tests.
+template <class Op, int RP>
+__device__ __forceinline__ void vscan_load(const Op &op, int64_t lp, int64_t hi, int64_t n, int64_t d, int64_t c,
+                                           bool active, typename Op::S (&st)[RP], typename Op::Aux (&aux)[RP]) {
+    const int64_t i0 = vscan_phys<Op>(lp, n), f0 = i0 * d + c, step = Op::kRev ? -d : d;
+    if (active && lp + RP <= hi) {
+#pragma unroll
+        for (int k = 0; k < RP; ++k) st[k] = op.state(Op::kRev ? i0 - k : i0 + k, f0 + k * step, aux[k]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < RP; ++k)
+            st[k] = (active && lp + k < hi) ? op.state(Op::kRev ? i0 - k : i0 + k, f0 + k * step, aux[k])
+                                            : op.identity();
+    }
+}
+// ... and its stores of the inclusive values, r the chunk's incoming prefix.
+template <class Op, int RP>
+__device__ __forceinline__ void vscan_store(const Op &op, int64_t lp, int64_t hi, int64_t n, int64_t d, int64_t c,
+                                            bool active, typename Op::S r, const typename Op::S (&st)[RP],
+                                            const typename Op::Aux (&aux)[RP]) {
+    const int64_t f0 = vscan_phys<Op>(lp, n) * d + c, step = Op::kRev ? -d : d;
+    if (active && lp + RP <= hi) {
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            r = op.combine(r, st[k]);
+            op.store(f0 + k * step, r, aux[k]);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < RP; ++k) {
+            if (active && lp + k < hi) {
+                r = op.combine(r, st[k]);
+                op.store(f0 + k * step, r, aux[k]);
+            }
+        }
+    }
 }
 
 // The rescan of the min / max scan vjps: they read x and y at the element
@@ -557,18 +597,21 @@ k_vscan_fold(const Op op, const int64_t n, const int64_t d, typename Op::S *__re
         // part p folds a contiguous piece of the range, RP loads in flight
         const int64_t per = (l1 - l0 + P - 1) / P;
         const int64_t lo = l0 + p * per, hi = lo + per < l1 ? lo + per : l1;
+        const int64_t step = Op::kRev ? -d : d;
         int64_t L = lo;
         for (; L + RP <= hi; L += RP) {
+            const int64_t i0 = vscan_phys<Op>(L, n), f0 = i0 * d + c;
             S v[RP];
             typename Op::Aux aux;
 #pragma unroll
-            for (int k = 0; k < RP; ++k) v[k] = op.state(vscan_phys<Op>(L + k, n), c, aux);
+            for (int k = 0; k < RP; ++k) v[k] = op.state(Op::kRev ? i0 - k : i0 + k, f0 + k * step, aux);
 #pragma unroll
             for (int k = 0; k < RP; ++k) a = op.combine(a, v[k]);
         }
         for (; L < hi; ++L) {
             typename Op::Aux aux;
-            a = op.combine(a, op.state(vscan_phys<Op>(L, n), c, aux));
+            const int64_t i = vscan_phys<Op>(L, n);
+            a = op.combine(a, op.state(i, i * d + c, aux));
         }
     }
     s_part[t] = a;
@@ -616,13 +659,10 @@ k_vscan_apply(const Op op, const int64_t n, const int64_t d, const typename Op::
         const int64_t lp = lt + p * RP;
         S st[RP];
         typename Op::Aux aux[RP];
-        if constexpr (Op::kHaloChunk) {
+        if constexpr (Op::kHaloChunk)
             vscan_chunk(op, lp, l1, n, c, active, st, aux);
-        } else {
-#pragma unroll
-            for (int k = 0; k < RP; ++k)
-                st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
-        }
+        else
+            vscan_load(op, lp, l1, n, d, c, active, st, aux);
         S a = op.identity();
 #pragma unroll
         for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
@@ -642,13 +682,7 @@ k_vscan_apply(const Op op, const int64_t n, const int64_t d, const typename Op::
         }
         S r = (active && p > 0) ? op.combine(carry, s_part[t - d]) : carry;
         const S tile = active ? s_part[(P - 1) * d + c] : op.identity();
-#pragma unroll
-        for (int k = 0; k < RP; ++k) {
-            if (active && lp + k < l1) {
-                r = op.combine(r, st[k]);
-                op.store(vscan_phys<Op>(lp + k, n), c, r, aux[k]);
-            }
-        }
+        vscan_store(op, lp, l1, n, d, c, active, r, st, aux);
         carry = op.combine(carry, tile);
         __syncthreads();  // s_part is rewritten by the next tile
     }
@@ -690,18 +724,21 @@ k_vscan_wfold(const Op op, const int64_t n, const int64_t d, const int64_t U, ty
         // part p folds a contiguous piece of the unit, RP loads in flight
         const int64_t per = (l1 - l0 + P - 1) / P;
         const int64_t lo = l0 + p * per, hi = lo + per < l1 ? lo + per : l1;
+        const int64_t step = Op::kRev ? -d : d;
         int64_t L = lo;
         for (; L + RP <= hi; L += RP) {
+            const int64_t i0 = vscan_phys<Op>(L, n), f0 = i0 * d + c;
             S v[RP];
             typename Op::Aux aux;
 #pragma unroll
-            for (int k = 0; k < RP; ++k) v[k] = op.state(vscan_phys<Op>(L + k, n), c, aux);
+            for (int k = 0; k < RP; ++k) v[k] = op.state(Op::kRev ? i0 - k : i0 + k, f0 + k * step, aux);
 #pragma unroll
             for (int k = 0; k < RP; ++k) a = op.combine(a, v[k]);
         }
         for (; L < hi; ++L) {
             typename Op::Aux aux;
-            a = op.combine(a, op.state(vscan_phys<Op>(L, n), c, aux));
+            const int64_t i = vscan_phys<Op>(L, n);
+            a = op.combine(a, op.state(i, i * d + c, aux));
         }
     }
     a = warp_parts_scan(op, a, (int)d, P);
@@ -753,13 +790,10 @@ k_vscan_wapply(const Op op, const int64_t n, const int64_t d, const int64_t U, c
         const int64_t lp = lt + p * RP;
         S st[RP];
         typename Op::Aux aux[RP];
-        if constexpr (Op::kHaloChunk) {
+        if constexpr (Op::kHaloChunk)
             vscan_chunk(op, lp, l1, n, c, active, st, aux);
-        } else {
-#pragma unroll
-            for (int k = 0; k < RP; ++k)
-                st[k] = (active && lp + k < l1) ? op.state(vscan_phys<Op>(lp + k, n), c, aux[k]) : op.identity();
-        }
+        else
+            vscan_load(op, lp, l1, n, d, c, active, st, aux);
         S a = op.identity();
 #pragma unroll
         for (int k = 0; k < RP; ++k) a = op.combine(a, st[k]);
@@ -767,13 +801,7 @@ k_vscan_wapply(const Op op, const int64_t n, const int64_t d, const int64_t U, c
         const S ex = P > 1 ? shfl_up(a, (int)d) : a;  // P is warp-uniform; read for p > 0 only
         const S tile = shfl_idx(a, last);
         S r = p > 0 ? op.combine(carry, ex) : carry;
-#pragma unroll
-        for (int k = 0; k < RP; ++k) {
-            if (active && lp + k < l1) {
-                r = op.combine(r, st[k]);
-                op.store(vscan_phys<Op>(lp + k, n), c, r, aux[k]);
-            }
-        }
+        vscan_store(op, lp, l1, n, d, c, active, r, st, aux);
         carry = op.combine(carry, tile);
     }
 }
@@ -831,7 +859,7 @@ template <typename T>
 static adc_status vscan_vjp_t(adc_op op, int64_t n, int64_t d, const T *x, const T *y, const T *ybar, T *xbar,
                               int acc, char *ws, cudaStream_t s) {
     switch (op) {
-    case ADC_OP_ADD: return vscan_run<VScanVjpAdd<T>, 16>({ybar, xbar, d, acc}, n, d, ws, s);
+    case ADC_OP_ADD: return vscan_run<VScanVjpAdd<T>, 8>({ybar, xbar, d, acc}, n, d, ws, s);
     case ADC_OP_MUL: return vscan_run<VScanVjpAff<T, 1>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
     case ADC_OP_MIN: return vscan_run<VScanVjpAff<T, 2>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
     case ADC_OP_MAX: return vscan_run<VScanVjpAff<T, 3>, 8>({x, y, ybar, xbar, n, d, acc}, n, d, ws, s);
