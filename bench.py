@@ -518,7 +518,8 @@ def run_kernels(args):
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
         row(f"scan {op} fwd float32", n, 8 * n, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
-        row(f"scan {op} vjp float32", n, 16 * n, timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        # the vjp reads y and ybar (the selections come from y), writes xbar
+        row(f"scan {op} vjp float32", n, 12 * n, timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
         del x, y, yb, xb
     # vectorised operators (Irwim / Iswim): the paper's [n][d] shapes, d = 16 (reduce, scan), 10 (hist)
     for fam, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),
@@ -539,7 +540,8 @@ def run_kernels(args):
             yb = torch.randn_like(x)
             xb = torch.empty_like(x)
             row(f"vscan {op} fwd d={d}", n, 2 * s, timeit(lambda: adcomb.vscan_fwd(op, x, y, ws=ws)))
-            row(f"vscan {op} vjp d={d}", n, (2 if op == "add" else 4) * s,
+            # vjp reads: ybar (+), x, y, ybar (*), y, ybar (min / max); writes xbar
+            row(f"vscan {op} vjp d={d}", n, (2 if op == "add" else 3 if op in ("min", "max") else 4) * s,
                 timeit(lambda: adcomb.vscan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
         elif fam == "vreduce":
             y, sv = adcomb.vreduce_fwd(op, x, ws=ws)

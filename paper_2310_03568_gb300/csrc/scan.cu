@@ -51,6 +51,25 @@ __device__ __forceinline__ void fetch_prev_sm(const E *sm, int64_t lo, int64_t c
     load_chunk_sm(sm + lo, c0, n, r.v, e);
     r.halo = (c0 > 0 && c0 - 1 < n) ? sm[lo - 1] : e;
 }
+// One chunk with one element on each side: v[k] = y[c0 + k], prev = y[c0 - 1],
+// next = y[c0 + ITEMS] (fill outside [0, n)).
+template <typename E, int ITEMS> struct Halo2Chunk {
+    E v[ITEMS];
+    E prev, next;
+};
+template <typename E, int ITEMS>
+__device__ __forceinline__ void fetch_both(const E *y, int64_t c0, int64_t n, Halo2Chunk<E, ITEMS> &r, E fill) {
+    load_chunk(y, c0, n, r.v, fill);
+    r.prev = (c0 > 0 && c0 - 1 < n) ? y[c0 - 1] : fill;
+    r.next = (c0 + ITEMS < n) ? y[c0 + ITEMS] : fill;
+}
+template <typename E, int ITEMS>
+__device__ __forceinline__ void fetch_both_sm(const E *sm, int64_t lo, int64_t c0, int64_t n, Halo2Chunk<E, ITEMS> &r,
+                                              E fill) {
+    load_chunk_sm(sm + lo, c0, n, r.v, fill);
+    r.prev = (c0 > 0 && c0 - 1 < n) ? sm[lo - 1] : fill;
+    r.next = (c0 + ITEMS < n) ? sm[lo + ITEMS] : fill;
+}
 // xs[k] = x[c0 + k + 1]  and  ys[k] = y[c0 + k - 1]
 template <typename E, int ITEMS> __device__ __forceinline__ E next_of(const HaloChunk<E, ITEMS> &r, int k) {
     return (k + 1 < ITEMS) ? r.v[k + 1] : r.halo;
@@ -211,38 +230,44 @@ template <typename T, int ITEMS> struct VjpMul {
 // min / max scan (the general rule of Fig. 7 with a scalar Jacobian): the step
 // y_{i+1} = y_i . x_{i+1} has d/dy_i = c_{i+1} = [y_i selected] and
 // d/dx_{i+1} = 1 - c_{i+1}, so lambda_i = ybar_i + c_{i+1} lambda_{i+1} and
-// xbar_i = [x_i selected at step i] lambda_i (x_0 always is).
+// xbar_i = [x_i selected at step i] lambda_i (x_0 always is).  Both
+// selections are read off y alone: x_i wins step i exactly when y_i differs
+// from y_{i-1} (a strict win changes the value, a loss or a tie keeps it; two
+// NaNs count as equal, as a NaN y_{i-1} is never beaten), so x is not read.
+template <typename T> __device__ __forceinline__ bool same_value(T a, T b) { return a == b || (a != a && b != b); }
+
 template <typename T, int ITEMS, bool MAX> struct VjpSel {
     using State = AffS<T>;
-    using Raw = VjpRaw<T, ITEMS>;
+    struct Raw {
+        Chunk<T, ITEMS> yb;
+        Halo2Chunk<T, ITEMS> y;
+    };
     struct Aux { T sel[ITEMS]; };
     const T *x, *y, *ybar;
     T *xbar;
     int accumulate;
-    static __device__ __forceinline__ bool beats(T a, T b) { return MAX ? (a > b) : (a < b); }
     __device__ State identity() const { return {T(0), T(1)}; }
     __device__ State combine(const State &acc, const State &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
     __device__ void fetch(int64_t c0, int64_t n, Raw &r) const {
         load_chunk(ybar, c0, n, r.yb.v, T(0));
-        fetch_next(x, c0, n, r.x, T(0));
-        fetch_prev(y, c0, n, r.y, T(0));
+        fetch_both(y, c0, n, r.y, T(0));
     }
-    static constexpr int kStreams = 3;
+    static constexpr int kStreams = 2;
     using Elem = T;
-    __device__ const T *stream(int s) const { return s == 0 ? ybar : (s == 1 ? x : y); }
-    __device__ void fetch_staged(const T *const (&sm)[3], int64_t lo, int64_t c0, int64_t n, Raw &r) const {
+    __device__ const T *stream(int s) const { return s == 0 ? ybar : y; }
+    __device__ void fetch_staged(const T *const (&sm)[2], int64_t lo, int64_t c0, int64_t n, Raw &r) const {
         load_chunk_sm(sm[0] + lo, c0, n, r.yb.v, T(0));
-        fetch_next_sm(sm[1], lo, c0, n, r.x, T(0));
-        fetch_prev_sm(sm[2], lo, c0, n, r.y, T(0));
+        fetch_both_sm(sm[1], lo, c0, n, r.y, T(0));
     }
     __device__ void build(int64_t c0, int64_t n, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
 #pragma unroll
         for (int k = 0; k < ITEMS; ++k) {
             const int64_t i = c0 + k;
-            // y_i is this element's own scan value: the y chunk is the y array at c0
             const T yi = r.y.v[k];
-            aux.sel[k] = (i == 0 || beats(r.x.v[k], prev_of(r.y, k))) ? T(1) : T(0);
-            const T c = (i + 1 < n && beats(next_of(r.x, k), yi)) ? T(0) : T(1);
+            const T yp = k > 0 ? r.y.v[k - 1] : r.y.prev;
+            const T yn = k + 1 < ITEMS ? r.y.v[k + 1] : r.y.next;
+            aux.sel[k] = (i == 0 || !same_value(yi, yp)) ? T(1) : T(0);
+            const T c = (i + 1 < n && !same_value(yn, yi)) ? T(0) : T(1);
             st[k] = (i < n) ? State{r.yb.v[k], c} : identity();
         }
     }

@@ -459,7 +459,12 @@ template <typename T> struct VScanVjpAdd {
 // * and min / max scan vjps: the recurrence lambda_i = ybar_i + J_{i+1}
 // lambda_{i+1} as a reverse scan of affine maps (Sec. 5.1), with
 // J_{i+1} = x_{i+1} for * and the 0/1 "y_i selected" for min / max; then
-// xbar_i = y_{i-1} lambda_i (*) or [x_i selected at step i] lambda_i.
+// xbar_i = y_{i-1} lambda_i (*) or [x_i selected at step i] lambda_i.  The
+// min / max selections are read off y alone: x_i wins step i exactly when
+// y_i differs from y_{i-1} (a strict win changes the value, a loss or a tie
+// keeps it; two NaNs count as equal), so x is not read.
+template <typename T> __device__ __forceinline__ bool vsame(T a, T b) { return a == b || (a != a && b != b); }
+
 template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
     using S = VAff<T>;
     struct Aux { T g, old; };
@@ -471,19 +476,17 @@ template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
     T *__restrict__ xbar;
     int64_t n, d;
     int accumulate;
-    static __device__ __forceinline__ bool beats(T a, T b) { return K == 3 ? (a > b) : (a < b); }
     __device__ S identity() const { return {T(0), T(1)}; }
     __device__ S combine(const S &acc, const S &e) const { return {e.v + e.c * acc.v, e.c * acc.c}; }
     __device__ S state(int64_t i, int64_t f, Aux &a) const {
         a.old = accumulate ? xbar[f] : T(0);
-        const T xn = i + 1 < n ? __ldg(x + f + d) : T(1);
         if (K == 1) {
             a.g = i > 0 ? __ldg(y + f - d) : T(1);
-            return {__ldg(ybar + f), xn};
+            return {__ldg(ybar + f), i + 1 < n ? __ldg(x + f + d) : T(1)};
         }
         const T yi = __ldg(y + f);
-        a.g = (i == 0 || beats(__ldg(x + f), __ldg(y + f - d))) ? T(1) : T(0);
-        return {__ldg(ybar + f), (i + 1 < n && beats(xn, yi)) ? T(0) : T(1)};
+        a.g = (i == 0 || !vsame(yi, __ldg(y + f - d))) ? T(1) : T(0);
+        return {__ldg(ybar + f), (i + 1 < n && !vsame(__ldg(y + f + d), yi)) ? T(0) : T(1)};
     }
     __device__ void store(int64_t f, const S &inc, const Aux &a) const {
         const T g = a.g * inc.v;
@@ -542,10 +545,10 @@ __device__ __forceinline__ void vscan_store(const Op &op, int64_t lp, int64_t hi
     }
 }
 
-// The rescan of the min / max scan vjps: they read x and y at the element
-// and at its neighbours (x_{i+1} and y_{i-1}); here each of x and y is loaded
-// once per row of the chunk (logical rows lp .. lp+RP-1, none at or beyond
-// hi) plus one halo row, and the neighbours are taken from registers.
+// The rescan of the min / max scan vjps: they read y at the element and at
+// both neighbours; here y is loaded once per row of the chunk (logical rows
+// lp .. lp+RP-1, none at or beyond hi) plus a halo row on each side, and the
+// neighbours are taken from registers.
 template <typename T, int K, int RP>
 __device__ __forceinline__ void vscan_chunk(const VScanVjpAff<T, K> &op, int64_t lp, int64_t hi, int64_t n, int64_t c,
                                             bool active, VAff<T> (&st)[RP],
@@ -555,28 +558,28 @@ __device__ __forceinline__ void vscan_chunk(const VScanVjpAff<T, K> &op, int64_t
     int64_t cnt = hi - lp < RP ? hi - lp : RP;
     if (!active || cnt < 0) cnt = 0;  // nothing is loaded then, not even a halo
     const int64_t i0 = n - 1 - lp;   // physical rows i0, i0-1, ..., i0-cnt+1 (all >= 0)
-    // X[k] = x[i0 + 1 - k] (X[0]: the halo x_{i0+1}); Y[k] = y[i0 - k] (Y[cnt]: the halo y_{i0-cnt})
-    T X[RP + 1], Y[RP + 1], yb[RP], old[RP];
+    // Y[j] = y[i0 + 1 - j]: Y[0] the halo y_{i0+1}, Y[cnt+1] the halo y_{i0-cnt}
+    T Y[RP + 2], yb[RP], old[RP];
 #pragma unroll
-    for (int k = 0; k <= RP; ++k) {
-        const int64_t ix = i0 + 1 - k, iy = i0 - k;
-        X[k] = (cnt > 0 && k <= cnt && ix < n) ? __ldg(op.x + ix * d + c) : T(0);
-        Y[k] = (cnt > 0 && k <= cnt && iy >= 0) ? __ldg(op.y + iy * d + c) : T(0);
-        if (k < RP) {
-            yb[k] = k < cnt ? __ldg(op.ybar + iy * d + c) : T(0);
-            old[k] = (k < cnt && op.accumulate) ? op.xbar[iy * d + c] : T(0);
-        }
+    for (int j = 0; j < RP + 2; ++j) {
+        const int64_t iy = i0 + 1 - j;
+        Y[j] = (cnt > 0 && j <= cnt + 1 && iy >= 0 && iy < n) ? __ldg(op.y + iy * d + c) : T(0);
     }
 #pragma unroll
     for (int k = 0; k < RP; ++k) {
-        const int64_t i = i0 - k;
+        yb[k] = k < cnt ? __ldg(op.ybar + (i0 - k) * d + c) : T(0);
+        old[k] = (k < cnt && op.accumulate) ? op.xbar[(i0 - k) * d + c] : T(0);
+    }
+#pragma unroll
+    for (int k = 0; k < RP; ++k) {
+        const int64_t i = i0 - k;  // y_{i+1} = Y[k], y_i = Y[k+1], y_{i-1} = Y[k+2]
         aux[k].old = old[k];
         if (k >= cnt) {
             st[k] = op.identity();
             aux[k].g = T(0);
         } else {
-            aux[k].g = (i == 0 || op.beats(X[k + 1], Y[k + 1])) ? T(1) : T(0);
-            st[k] = {yb[k], (i + 1 < n && op.beats(X[k], Y[k])) ? T(0) : T(1)};
+            aux[k].g = (i == 0 || !vsame(Y[k + 1], Y[k + 2])) ? T(1) : T(0);
+            st[k] = {yb[k], (i + 1 < n && !vsame(Y[k], Y[k + 1])) ? T(0) : T(1)};
         }
     }
 }

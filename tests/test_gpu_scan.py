@@ -218,3 +218,30 @@ def test_minmax_scan(op, dt, engine_id):
                            suffix_max(yb) + (np.abs(old) if acc else 0), rtol)
     finally:
         adcomb.debug_set_scan_engine(0)
+
+
+@pytest.mark.parametrize("engine_id", [1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_scan_nan_and_integer_adjoints(op, engine_id):
+    """NaN never wins a comparison, so a NaN x_i (i > 0) is never selected and
+    leaves y unchanged.  The kernels read the selections off y (x_i wins step
+    i exactly when y_i differs from y_{i-1}); with integer ybar every adjoint
+    is an exact sum, so the vjp must equal the oracle's, which compares x with
+    y.  (A NaN x_0 is left out: the identity (+-inf) combined with NaN gives
+    the identity, so the kernels' y_0 is +-inf where the sequential definition
+    y_0 = x_0 gives NaN.)"""
+    g = np.random.default_rng(43)
+    try:
+        adcomb.debug_set_scan_engine(engine_id)
+        for n in [1000, 100_003]:
+            x = ((g.integers(0, 64, n) - 32) / 8.0).astype(np.float32)
+            x[g.random(n) < 0.05] = np.nan
+            x[0] = 1.0
+            yb = g.integers(-3, 4, n).astype(np.float32)
+            xd = dev(x)
+            y = adcomb.scan_fwd(op, xd)
+            assert np.array_equal(host(y), oracle.scan_fwd(op, x).astype(np.float32), equal_nan=True)
+            xb = adcomb.scan_vjp(op, xd, y, dev(yb))
+            assert np.array_equal(host(xb), oracle.scan_vjp(op, x, yb).astype(np.float32))
+    finally:
+        adcomb.debug_set_scan_engine(0)

@@ -110,6 +110,27 @@ def test_vscan_many_tiles_per_unit(op, d):
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("d", [3, 16, 48])
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_vscan_minmax_nan_and_integer_adjoints(op, d, dt):
+    """The min / max vjps read the selections off y (x_i wins step i exactly
+    when y_i differs from y_{i-1}): with NaNs in x (never selected) after row
+    0 and integer ybar, every adjoint is an exact sum and equals the
+    oracle's, which compares x with y."""
+    g = np.random.default_rng(95 + d)
+    n = 100_003
+    x = ((g.integers(0, 64, (n, d)) - 32) / 8.0).astype(dt)
+    x[g.random((n, d)) < 0.05] = np.nan
+    x[0] = 1.0
+    yb = g.integers(-3, 4, (n, d)).astype(dt)
+    xd = dev(x)
+    y = adcomb.vscan_fwd(op, xd)
+    assert np.array_equal(host(y), oracle.vscan_fwd(op, x).astype(dt), equal_nan=True)
+    xb = adcomb.vscan_vjp(op, xd, y, dev(yb))
+    assert np.array_equal(host(xb), oracle.vscan_vjp(op, x, yb).astype(dt))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("d", [1, 4])
 @pytest.mark.parametrize("op", ["add", "mul", "min", "max"])
 def test_vhist(op, d, dt):
