@@ -142,7 +142,9 @@ adc_status adc_scan_fwd(adc_op op, adc_dtype dtype, int64_t n, const void *x, vo
  * (y_{-1} = e).  The Jacobians are block-diagonal with equal blocks (RBDS,
  * Sec. 5.3.4): a scalar c for ADD/MUL/LIN, M_{i+1}^T for MM2/MM3/MM5; for
  * MIN/MAX the scalar c_{i+1} = [y_i selected] is 0 or 1 and
- * xbar_i = [x_i selected] lambda_i (the general arity-1 rule).  SOP takes the
+ * xbar_i = [x_i selected] lambda_i (the general arity-1 rule); both are read
+ * off y (x_i is selected exactly when y_i differs from y_{i-1}), so MIN/MAX
+ * do not read x, although it must be passed.  SOP takes the
  * general arity-2 rule: c_{i+1} = [[1, s(x_{i+1})], [0, 1]] (not block-redundant),
  * composed as the single corner entry because unit upper-triangular matrices
  * multiply by adding it; xbar_i = (lambda.p, s(y_{i-1}) lambda.p + lambda.s).
@@ -301,19 +303,24 @@ adc_status adc_batched_hist_scan_vjp(const adc_instance *desc, int32_t count, co
  * reduce, scan and reduce_by_index whose operator is map2 (.) over rows of d
  * elements, (.) in ADD, MUL, MIN, MAX (Sec. 3.2 "Vectorized Operators": the
  * Irwim rule; Sec. 5.3: the Iswim rule; the same interchange for
- * reduce_by_index).  Computed as the rules rewrite them: the [n][d] operands
- * are transposed to [d][n], each column runs through the scalar entry point's
- * kernels (so each column follows that operator's specialised rule: zero
- * counting, lowest-index argmin, ...), and [n][d] / [m][d] results are
- * transposed back.  Arrays are row-major and 16-byte aligned; 1 <= d <= 64.
+ * reduce_by_index).  Computed as the rules rewrite them: d column
+ * combinators, each following its operator's specialised scalar rule (zero
+ * counting, lowest-index argmin, ...).  reduce, scan, and reduce_by_index
+ * with ADD (and fp32 MIN / MAX) while the [m][d] table fits one block's
+ * shared memory run on the row-major rows where they lie; the other
+ * reduce_by_index cases transpose the operands to [d][n] / [d][m], run the
+ * scalar entry point's kernels per column and transpose the results back.
+ * Arrays are row-major and 16-byte aligned; 1 <= d <= 64.
  *   vreduce : x [n][d] -> y [d]; saved = d column residuals (adc_vsaved_bytes)
- *   vscan   : x [n][d] -> y [n][d]; vjp reads x, y (not for ADD) and ybar [n][d]
+ *   vscan   : x [n][d] -> y [n][d]; the vjp reads ybar [n][d] and, except for
+ *             ADD, y (the MIN / MAX selections come from y alone) and x (MUL);
+ *             x and y must still be passed for every operator but ADD
  *   vhist   : keys [n], vals [n][d], hist0 [m][d] or NULL -> hist [m][d];
  *             saved == NULL computes the original primal (MUL, MIN, MAX)
- * The workspace holds the transposed planes and one scalar workspace per
- * column (adc_vworkspace_bytes); a timeout in any column is reported by
- * adc_check_device_error on this workspace.  Other operators:
- * ADC_ERR_UNSUPPORTED.
+ * The workspace (adc_vworkspace_bytes) holds per-block partial states, or
+ * for the transposed cases the planes and one scalar workspace per column;
+ * a timeout in any column is reported by adc_check_device_error on this
+ * workspace.  Other operators: ADC_ERR_UNSUPPORTED.
  */
 size_t adc_vworkspace_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d);
 size_t adc_vsaved_bytes(adc_kind kind, adc_op op, adc_dtype dtype, int64_t n, int64_t m, int64_t d);
