@@ -185,6 +185,30 @@ def test_minmax_scan_is_the_running_extremum_with_one_hot_adjoints(op):
     assert_close(oracle.scan_vjp(op, x, yb), expect, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("op", ["min", "max"])
+def test_minmax_selections_can_be_read_off_y(op):
+    # The reading the kernels use: x_i wins step i exactly when y_i differs
+    # from y_{i-1} (a strict win changes the running extremum, a tie or a
+    # loss keeps it), NaNs after position 0 never winning.  The adjoint built
+    # from y alone -- lambda_i = ybar_i + [y_{i+1} == y_i] lambda_{i+1},
+    # xbar_i = [i == 0 or y_i != y_{i-1}] lambda_i -- must equal the oracle's,
+    # which compares x with y; integer ybar makes both sums exact.
+    n = 2000
+    x = (RNG.integers(0, 20, n) - 10) / 4.0
+    x[RNG.random(n) < 0.05] = np.nan
+    x[0] = 0.5
+    y = oracle.scan_fwd(op, x)
+    assert not np.isnan(y).any()
+    yb = RNG.integers(-3, 4, n).astype(np.float64)
+    lam = np.zeros(n)
+    lam[n - 1] = yb[n - 1]
+    for i in range(n - 2, -1, -1):
+        lam[i] = yb[i] + (lam[i + 1] if y[i + 1] == y[i] else 0.0)
+    sel = np.ones(n, bool)
+    sel[1:] = y[1:] != y[:-1]
+    assert np.array_equal(oracle.scan_vjp(op, x, yb), np.where(sel, lam, 0.0))
+
+
 def test_sop_scan_closed_form():
     # sumOfProd (Fig. 8): scanning (p_i, s_i) gives S_k = sum_{j<=k} s_j and
     # P_k = sum_{j<=k} p_j + sum_{j<l<=k} s_j s_l = cumsum(p) + (S_k^2 - cumsum(s^2)) / 2.
