@@ -12,7 +12,9 @@
 // paper's compiler uses: k scans on the caller's arrays, nothing copied.  Rows
 // [n][D] with the blocks side by side: the rows are split into per-block
 // planes through shared-memory tiles, each plane is scanned, and the results
-// are merged back into rows.
+// are merged back into rows -- except when every block is the same scalar
+// operator (+, *, min, max), where the rows are the vectorised scan of width k
+// and its direct form scans them in place.
 #include "common.cuh"
 #include "internal.h"
 
@@ -195,8 +197,19 @@ static TLayout tlayout(int k, const adc_op *ops, adc_dtype dt, int64_t n, bool r
     return L;
 }
 
+// Rows whose k blocks are all the same scalar operator (+, *, min or max) are
+// the vectorised scan of width k: its direct form scans them in place.
+static bool uniform_scalar(int k, const adc_op *ops) {
+    const adc_op op = ops[0];
+    if (op != ADC_OP_ADD && op != ADC_OP_MUL && op != ADC_OP_MIN && op != ADC_OP_MAX) return false;
+    for (int c = 1; c < k; ++c)
+        if (ops[c] != op) return false;
+    return true;
+}
+
 size_t tscan_ws_bytes(int k, const adc_op *ops, adc_dtype dt, int64_t n, bool rows) {
     if (rows && k == 1) return scan_ws_bytes(ops[0], dt, n);
+    if (rows && uniform_scalar(k, ops)) return vws_bytes(ADC_SCAN, ops[0], dt, n, 0, k);
     return tlayout(k, ops, dt, n, rows).bytes;
 }
 
@@ -311,6 +324,7 @@ static char *plane_ptr(char *set, const TLayout &L, int c, adc_dtype dt) {
 adc_status tscan_fwd_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *x, void *y, void *ws,
                           cudaStream_t s) {
     if (k == 1) return scan_fwd(ops[0], dt, n, x, y, ws, s);  // one block: the rows are its elements
+    if (uniform_scalar(k, ops)) return vscan_fwd(ops[0], dt, n, k, x, y, ws, s);
     char *w = static_cast<char *>(ws);
     const TLayout L = tlayout(k, ops, dt, n, true);
     const TupleDesc d = tdesc(k, ops, L);
@@ -330,6 +344,7 @@ adc_status tscan_fwd_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, con
 adc_status tscan_vjp_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, const void *x, const void *y,
                           const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s) {
     if (k == 1) return scan_vjp(ops[0], dt, n, x, y, ybar, xbar, accumulate, ws, s);
+    if (uniform_scalar(k, ops)) return vscan_vjp(ops[0], dt, n, k, x, y, ybar, xbar, accumulate, ws, s);
     char *w = static_cast<char *>(ws);
     const TLayout L = tlayout(k, ops, dt, n, true);
     const TupleDesc d = tdesc(k, ops, L);

@@ -12,8 +12,10 @@ from tests.test_gpu_scan import IDENT, make_x
 
 pytestmark = pytest.mark.gpu
 
+# uniform scalar rows (("add", "add"), ("add",) * 64, ("max",) * 5, ("mul",) * 3)
+# take the vectorised scan's direct form; the others split into planes
 MIXES = [("add", "mul", "lin", "sop", "mm2", "min"), ("sop", "sop", "sop"), ("mm3", "max", "lin"), ("lin",),
-         ("add", "add"), ("sop",) * 16, ("add",) * 64, ("mm5", "mm5"), ("mul", "mm3")]
+         ("add", "add"), ("sop",) * 16, ("add",) * 64, ("mm5", "mm5"), ("mul", "mm3"), ("max",) * 5, ("mul",) * 3]
 SIZES = [0, 1, 2, 33, 1025, 4097, 100_003]
 
 
