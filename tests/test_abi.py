@@ -71,6 +71,11 @@ def test_tuple_size_queries(L):
     assert L.adc_tscan_workspace_bytes(0, codes(0), f32, 10, 1) == 0                  # no blocks
     assert L.adc_tscan_workspace_bytes(2, codes(0, 9), f32, 10, 1) == 0               # no operator 9
     assert L.adc_tscan_workspace_bytes(2, None, f32, 10, 1) == 0
+    # rows of one scalar operator repeated k times are the vectorised scan of width k
+    for op in (0, 1, 2, 3):
+        for k in (2, 16, 64):
+            assert L.adc_tscan_workspace_bytes(k, codes(*[op] * k), f32, 1000, 1) == \
+                L.adc_vworkspace_bytes(1, op, f32, 1000, 0, k) > 0
 
 
 def test_tuple_host_validation(L):
