@@ -414,7 +414,8 @@ adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void
 // twice, the outputs once.
 // An op gives identity(), combine(earlier, later), state(i, f, aux) -- the
 // element state of row i at flat offset f = i*d + c, with what its store
-// needs in aux -- and store(f, inclusive, aux).
+// needs in aux -- store(f, inclusive, aux), kRev (a reverse scan) and
+// kHaloChunk (its rescan loads a whole chunk through its own vscan_chunk).
 constexpr int kVScanThreads = 256;
 
 template <typename T> struct VAff { T v, c; };  // lambda -> v + c * lambda
