@@ -38,9 +38,9 @@ METRIC = "vjp elements/s & % HBM roofline; AD overhead = vjp time / primal time"
 WORKLOAD = ("reduce_by_index specialisations fp32: n=50M uniform int32 bins, m in {31,401,50000,10M}, "
             "ops * (1% zeros), min, max (1024 levels); lifted forward + vjp per (op, m)")
 # DRAM bytes (read + write) per call measured by ncu on n = 20M, m = 10M and
-# scaled to n by the parts that grow with n, plus the m-sized outputs
-# (profiles/hist_partition_kernels_n20M_m10M.md): the roofline's `traffic`
-# for the dominant call, when it is one of these.
+# scaled to n by the parts that grow with n, plus the m-sized outputs (the
+# partitioned-histogram kernels' capture): the roofline's `traffic` for the
+# dominant call, when it is one of these.
 TRAFFIC_PER_ELEM = {("fwd", "mul", 10_000_000): (22.1, 120e6), ("fwd", "min", 10_000_000): (29.7, 80e6),
                     ("fwd", "max", 10_000_000): (29.7, 80e6)}
 
@@ -78,6 +78,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-batched", action="store_true")
+    p.add_argument("--no-families", action="store_true")
     p.add_argument("--kernels", action="store_true",
                    help="instead of the bench line: per-kernel achieved bandwidth at full sizes (markdown)")
     p.add_argument("--only", default=None,
@@ -289,9 +290,12 @@ def run_ours(args, world, rank, local):
 
     del keys, vals, vbar
     torch.cuda.empty_cache()
+    families = None
+    if not args.no_families:
+        families = run_families(dev, peak)
     batched = None
     if not args.no_batched:
-        batched = run_batched(dev)
+        batched = run_batched(dev, peak)
 
     if rank == 0:
         line = {
@@ -309,7 +313,7 @@ def run_ours(args, world, rank, local):
             "per_call_ms": {f"{op}/{m}/{ph}": round(v, 4) for (op, m, ph), v in call_ms.items()},
             "primal_ms": {f"{op}/{m}": round(statistics.mean(v), 4) for (op, m, _), v in prim_ms.items()},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": n_launch, "clocks": clk,
-            "batched": batched,
+            "batched": batched, "families": families,
         }
         print(json.dumps(line))
     if world > 1:
@@ -406,18 +410,24 @@ def run_e2e(args, n, keys_h, vals_h, hbar_h, hist, saved, ws, dev, world):
             "overlap": "H2D on 2 and D2H on 3 streams of their own, ordered by events against the compute stream"}
 
 
-def run_batched(dev, seed=4):
+def run_batched(dev, peak, seed=4):
     """4096 hist -> +-scan -> sum instances (n_i, m_i log-uniform): forward + vjp
-    as two replayed CUDA graphs of the batched entry points, against the same
-    work through the single-instance entry points (several launches per
-    instance).  Reported beside the bench line; not part of its step."""
+    as two replayed CUDA graphs of the batched entry points (work-item size and
+    table size chosen by the autotuner), against the same work through the
+    single-instance entry points (several launches per instance), both as one
+    replayed CUDA graph of all instances (every buffer allocated before capture)
+    and as eager launches from Python.  Reported beside the bench line; not
+    part of its step."""
     import torch
 
+    from paper_2310_03568_gb300 import autotune
     from paper_2310_03568_gb300 import batched as B
     from paper_2310_03568_gb300 import synth
     w = synth.batched(seed=seed)
     desc, keys, vals = B.layout(w)
     p = B.BatchedHistScan(desc, keys, vals, device=dev)
+    tuned = autotune.tune_batched(p)
+    p.graphs = None
     for _ in range(3):
         p.replay_forward()
         p.replay_backward()
@@ -432,6 +442,18 @@ def run_batched(dev, seed=4):
     torch.cuda.synchronize()
     ms_batched = a.elapsed_time(b) / reps
     vb = p.valsbar.clone()
+    # per-instance launches captured in one graph: the launches alone
+    pig = B.PerInstanceGraph(desc, p.keys, p.vals, device=dev)
+    pig.replay()
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(3):
+        pig.replay()
+    b.record()
+    torch.cuda.synchronize()
+    ms_graph = a.elapsed_time(b) / 3
+    same_graph = bool(torch.equal(vb, pig.valsbar))
+    # per-instance launches from Python (dispatch included)
     B.per_instance_loss(desc, p.keys, p.vals)  # warm-up
     torch.cuda.synchronize()
     a.record()
@@ -441,10 +463,209 @@ def run_batched(dev, seed=4):
     ms_pi = a.elapsed_time(b)
     same = bool(torch.equal(vb, vb_pi))
     total = int(desc["n"].sum())
-    return {"instances": int(len(desc)), "values": total, "bins": int(desc["m"].sum()),
-            "batched_graph_ms": ms_batched, "per_instance_ms": ms_pi, "speedup": ms_pi / ms_batched,
-            "batched_values_per_s": total / (ms_batched * 1e-3), "gradients_bit_identical": same,
-            "loss_batched": float(p.loss.item()), "loss_per_instance": float(loss_pi.item())}
+    bins = int(desc["m"].sum())
+    add = desc["op"] == B.OPCODE["add"]
+    # forward: keys + values in, hist / scan / index words out; vjp: keys in (+ only), valsbar out
+    alg = int(8 * total + (8 * desc["n"][add].sum() + 4 * desc["n"][~add].sum()) + 16 * bins)
+    gbs = alg / (ms_batched * 1e-3) / 1e9
+    return {"instances": int(len(desc)), "values": total, "bins": bins,
+            "batched_graph_ms": ms_batched, "per_instance_graph_ms": ms_graph, "per_instance_ms": ms_pi,
+            "speedup_vs_graph": ms_graph / ms_batched, "speedup": ms_pi / ms_batched,
+            "batched_values_per_s": total / (ms_batched * 1e-3),
+            "algorithmic_bytes": alg, "achieved_gbs": gbs, "frac": gbs / peak,
+            "tuned": {"chunk": tuned["chunk"], "smem_bins": tuned["smem_bins"]},
+            "gradients_bit_identical": same and same_graph,
+            "loss_batched": float(p.loss.item()), "loss_per_instance": float(loss_pi.item()),
+            "loss_per_instance_graph": float(pig.loss.item())}
+
+
+# ------------------------------------------------------- other workloads ----
+# Algorithmic bytes per element of each call (minimal reads + writes, fp32
+# unless named): the roofline numerators of the families below.
+SCAN_BYTES = {"add": (2, 2), "mul": (2, 4), "lin": (4, 8), "mm2": (8, 16)}  # scalars per element: fwd, vjp
+REDUCE_BYTES = {"add": (1, 1), "mul": (1, 2), "min": (1, 1), "mm2": (4, 8), "lin": (2, 4)}
+
+
+def cpu_info():
+    """Host core count and CPU model (x86 'model name', else lscpu, else the Arm part ids)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            txt = f.read()
+        for line in txt.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+        if model is None:
+            r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+            for line in r.stdout.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        if model is None:
+            ids = [ln.split(":", 1)[1].strip() for ln in txt.splitlines()
+                   if ln.startswith(("CPU implementer", "CPU part"))][:2]
+            model = "implementer/part " + "/".join(ids) if ids else None
+    except Exception:
+        pass
+    return {"host_cpus": os.cpu_count(), "cpu_model": model}
+
+
+class L2Flush:
+    """Writes a buffer larger than L2 (256 MB) before each timed call."""
+
+    def __init__(self, dev):
+        import torch
+        self.buf = torch.empty(64 << 20, dtype=torch.float32, device=dev)
+
+    def __call__(self):
+        self.buf.zero_()
+
+
+def time_calls(fn, flush, reps=10, warm=3):
+    """Mean device time of fn() in ms: CUDA events on the launching stream
+    around each call, an L2 flush before each (outside the events)."""
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        flush()
+        fn()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+    for a, b in ev:
+        flush()
+        a.record(s)
+        fn()
+        b.record(s)
+    torch.cuda.synchronize()
+    return statistics.mean(a.elapsed_time(b) for a, b in ev)
+
+
+def family_entry(n, fwd_ms, vjp_ms, fwd_bytes, vjp_bytes, paper_bytes, peak, primal_ms=None):
+    """One workload's numbers: device times, algorithmic GB/s and fraction of
+    the measured copy bandwidth per call, AD overhead (fwd + vjp) / primal, and
+    the paper's normalised GB/s (its Nbytes of the primal / primal time)."""
+    primal_ms = fwd_ms if primal_ms is None else primal_ms
+    gbs = lambda b, ms: b / (ms * 1e-3) / 1e9  # noqa: E731
+    return {"n": n, "fwd_ms": round(fwd_ms, 5), "vjp_ms": round(vjp_ms, 5),
+            "fwd_gbs": round(gbs(fwd_bytes, fwd_ms), 1), "vjp_gbs": round(gbs(vjp_bytes, vjp_ms), 1),
+            "fwd_frac": round(gbs(fwd_bytes, fwd_ms) / peak, 3), "vjp_frac": round(gbs(vjp_bytes, vjp_ms) / peak, 3),
+            "fwd_bytes": fwd_bytes, "vjp_bytes": vjp_bytes,
+            "vjp_elements_per_s": n / (vjp_ms * 1e-3),
+            "ad_overhead": round((fwd_ms + vjp_ms) / primal_ms, 2),
+            "paper_gbs": round(gbs(paper_bytes, primal_ms), 1)}
+
+
+def run_families(dev, peak):
+    """The workloads beside the headline, each timed on its own at full size:
+    the small reduce-by-index workload (n = 1e5), the scans (n = 1e8 fp32,
+    1e7 fp64), the specialised reduces at 1e8, the 2x2 matrix scan and
+    reduce at 1e7, and linFnComp reduce-by-index at 1e7 / m = 1000.  Inputs are
+    seeded and drawn on the device with the workloads' distributions."""
+    import torch
+
+    from paper_2310_03568_gb300 import adcomb
+    flush = L2Flush(dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(2)
+    ws = adcomb.Workspace()
+    out = {}
+
+    def U(shape, lo, hi, dtype=torch.float32):
+        return torch.rand(shape, generator=gen, device=dev, dtype=dtype) * (hi - lo) + lo
+
+    def Nrm(shape, dtype=torch.float32):
+        return torch.randn(shape, generator=gen, device=dev, dtype=dtype)
+
+    def scan_x(op, n, dtype):
+        if op == "add":
+            return U(n, -1, 1, dtype)
+        if op == "mul":
+            x = U(n, 0.9, 1.1, dtype)
+            x[torch.rand(n, generator=gen, device=dev) < 0.001] = 0
+            return x
+        if op == "lin":
+            return torch.stack([Nrm(n, dtype), U(n, 0.95, 1.05, dtype)], 1).contiguous()
+        return (U((n, 4), -1, 1, dtype) / np.sqrt(2.0)).contiguous()
+
+    # small reduce-by-index workload: n = 1e5, m = 1000, hist0; + reduce and + scan of the same values
+    n, m = 100_000, 1000
+    k = torch.randint(0, m, (n,), generator=gen, device=dev, dtype=torch.int32)
+    v, h0, hb = U(n, -1, 1), U(m, -1, 1), Nrm(m)
+    h, sv = adcomb.hist_fwd("add", m, k, v, h0, ws=ws)
+    vb, h0b = torch.empty_like(v), torch.empty_like(h0)
+    f = time_calls(lambda: adcomb.hist_fwd("add", m, k, v, h0, h, sv, ws=ws), flush)
+    b = time_calls(lambda: adcomb.hist_vjp("add", m, k, v, h0, h, sv, hb, valsbar=vb, hist0bar=h0b,
+                                           want_hist0bar=True, ws=ws), flush)
+    small = {"hist_add_m1000": family_entry(n, f, b, 8 * n + 8 * m, 8 * n + 8 * m, 12 * n + 8 * n, peak)}
+    y, rs = adcomb.reduce_fwd("add", v, ws=ws)
+    yb1, xb = Nrm(1), torch.empty_like(v)
+    f = time_calls(lambda: adcomb.reduce_fwd("add", v, y, rs, ws=ws), flush)
+    b = time_calls(lambda: adcomb.reduce_vjp("add", v, y, rs, yb1, xbar=xb, ws=ws), flush)
+    small["reduce_add"] = family_entry(n, f, b, 4 * n, 4 * n, 4 * n, peak)
+    ys, ybs = adcomb.scan_fwd("add", v, ws=ws), Nrm(n)
+    f = time_calls(lambda: adcomb.scan_fwd("add", v, ys, ws=ws), flush)
+    b = time_calls(lambda: adcomb.scan_vjp("add", v, ys, ybs, xbar=xb, ws=ws), flush)
+    small["scan_add"] = family_entry(n, f, b, 8 * n, 8 * n, 8 * n, peak)
+    out["small_n1e5_m1000"] = small
+    del k, v, h0, hb, vb, xb
+
+    # scans: n = 1e8 fp32 and 1e7 fp64 (+, * with 0.1% zeros, linFnComp)
+    for dtype, n, label in [(torch.float32, 100_000_000, "scan_f32_n1e8"), (torch.float64, 10_000_000, "scan_f64_n1e7")]:
+        es = 4 if dtype == torch.float32 else 8
+        fam = {}
+        for op in ("add", "mul", "lin"):
+            x = scan_x(op, n, dtype)
+            y = adcomb.scan_fwd(op, x, ws=ws)
+            yb, xb = torch.randn(x.shape, generator=gen, device=dev, dtype=dtype), torch.empty_like(x)
+            f = time_calls(lambda: adcomb.scan_fwd(op, x, y, ws=ws), flush)
+            b = time_calls(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws), flush)
+            sf, sb = SCAN_BYTES[op]
+            fam[op] = family_entry(n, f, b, sf * es * n, sb * es * n, sf * es * n, peak)
+            del x, y, yb, xb
+        out[label] = fam
+    # specialised reduces at n = 1e8 fp32
+    n = 100_000_000
+    fam = {}
+    for op in ("add", "mul", "min"):
+        x = U(n, -1, 1) if op != "mul" else U(n, 0.999, 1.001)
+        y, rs = adcomb.reduce_fwd(op, x, ws=ws)
+        yb, xb = torch.ones_like(y), torch.empty_like(x)
+        f = time_calls(lambda: adcomb.reduce_fwd(op, x, y, rs, ws=ws), flush)
+        b = time_calls(lambda: adcomb.reduce_vjp(op, x, y, rs, yb, xbar=xb, ws=ws), flush)
+        rf, rb = REDUCE_BYTES[op]
+        fam[op] = family_entry(n, f, b, 4 * rf * n, 4 * rb * n, 4 * n, peak)
+        del x, xb
+    out["reduce_f32_n1e8"] = fam
+    # general paths: 2x2 matrix scan and reduce at 1e7, linFnComp reduce-by-index at 1e7 / m = 1000
+    n = 10_000_000
+    x = scan_x("mm2", n, torch.float32)
+    gen_fam = {}
+    y = adcomb.scan_fwd("mm2", x, ws=ws)
+    yb, xb = Nrm(x.shape), torch.empty_like(x)
+    f = time_calls(lambda: adcomb.scan_fwd("mm2", x, y, ws=ws), flush)
+    b = time_calls(lambda: adcomb.scan_vjp("mm2", x, y, yb, xbar=xb, ws=ws), flush)
+    gen_fam["scan_mm2"] = family_entry(n, f, b, 32 * n, 64 * n, 32 * n, peak)
+    yr, rs = adcomb.reduce_fwd("mm2", x, ws=ws)
+    ybr = Nrm(4)
+    f = time_calls(lambda: adcomb.reduce_fwd("mm2", x, yr, rs, ws=ws), flush)
+    b = time_calls(lambda: adcomb.reduce_vjp("mm2", x, yr, rs, ybr, xbar=xb, ws=ws), flush)
+    gen_fam["reduce_mm2"] = family_entry(n, f, b, 16 * n, 32 * n, 16 * n, peak)
+    del x, y, yb, xb
+    m = 1000
+    k = torch.randint(0, m, (n,), generator=gen, device=dev, dtype=torch.int32)
+    v = scan_x("lin", n, torch.float32)
+    h, sv = adcomb.hist_fwd("lin", m, k, v, ws=ws)
+    hb, vb = Nrm((m, 2)), torch.empty_like(v)
+    f = time_calls(lambda: adcomb.hist_fwd("lin", m, k, v, None, h, sv, ws=ws), flush)
+    b = time_calls(lambda: adcomb.hist_vjp("lin", m, k, v, None, h, sv, hb, valsbar=vb, ws=ws), flush)
+    # keys + (b, c) in; the vjp reads keys and values and writes the adjoints
+    gen_fam["hist_lin_m1000"] = family_entry(n, f, b, 12 * n, 20 * n, 3 * 8 * n + 8 * n, peak)
+    out["general_n1e7"] = gen_fam
+    del k, v, vb
+    torch.cuda.empty_cache()
+    out["timing"] = ("CUDA events on the launching stream around each call, mean of 10 after 3 warm-ups, "
+                     "a 256 MB L2 flush before each call; frac of the measured copy bandwidth")
+    return out
 
 
 # --------------------------------------------------------- kernel rooflines ----
@@ -673,7 +894,7 @@ def cpu_baseline(n, keys_h, vals_h, hbar_h, sample=SAMPLE):
     dt = time.perf_counter() - t
     return {"value": len(BINS) * len(OPS) * s / dt, "unit": "elements/s", "cores": 1, "kind": "oracle",
             "sample": f"first {s} of the {n} elements of each of the 12 (op, m) instances; forward + vjp, fp64",
-            "seconds": dt}
+            "seconds": dt, **cpu_info()}
 
 
 def run_reference(args, world, rank):
@@ -697,7 +918,8 @@ def run_reference(args, world, rank):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "n": n, "sample_per_instance": s},
         "cpu_baseline": {"value": value, "unit": "elements/s", "cores": 1, "kind": "oracle",
-                         "sample": f"{s} elements of each of the 12 (op, m) instances per step; forward + vjp"},
+                         "sample": f"{s} elements of each of the 12 (op, m) instances per step; forward + vjp",
+                         **cpu_info()},
         "e2e": {"value": value, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))

@@ -161,15 +161,18 @@ adc_status adc_scan_vjp(adc_op op, adc_dtype dtype, int64_t n, const void *x, co
  * output buffers.  The paper has no counterpart: this is a packaging of the
  * same scan kernel whose look-back scratch lives in a file-scope device array
  * of 4 MiB held by every GPU that loads the library until the process exits.
- * Same operators, layouts and results as adc_scan_fwd; nothing is allocated
- * or freed.
+ * Every operator adc_scan_fwd accepts (ADD, MUL, MIN, MAX, LIN, MM2, SOP, MM3,
+ * MM5), with the same layouts and results; nothing is allocated or freed.
  *   Limit : n must satisfy adc_workspace_bytes(ADC_SCAN, op, dtype, n, 0) <= 4 MiB
  *           (about 1.0e9 fp32 + elements, 2.6e8 fp32 *, 8.9e7 fp32 lin,
  *           1.6e7 fp32 mm2, 8.3e6 fp64 mm2); larger n returns
- *           ADC_ERR_WORKSPACE before any work is queued.
+ *           ADC_ERR_WORKSPACE before any work is queued.  An operator code
+ *           outside the enum returns ADC_ERR_INVALID_ARG.
  *   Set-up: the first call on a device, with that device current, looks up the
  *           array's device address; make that first call before capturing a
- *           stream.
+ *           stream.  The address belongs to the device's context: after
+ *           cudaDeviceReset the next call finds a new context id and looks the
+ *           address up again (a set-up call again, so again not under capture).
  *   Sharing: all calls on a device use the same array, which keeps the last
  *           call's contents; each call clears what must start at zero.  Calls
  *           that may overlap on the GPU race and must not be issued.

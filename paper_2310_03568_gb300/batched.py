@@ -223,3 +223,82 @@ def per_instance_loss(desc, keys, vals, want_grad=True, loss_bar=1.0):
         hbar = adcomb.scan_vjp("add", None, None, ybar, ws=ws)
         adcomb.hist_vjp(op, m, k, v, zeros[:m], h, saved, hbar, valsbar=vbar[vo:vo + k.shape[0]], ws=ws)
     return loss, vbar
+
+
+class PerInstanceGraph:
+    """The per-instance baseline with every buffer allocated up front and the
+    whole loop -- per instance reduce_by_index, +-scan and +-reduce forward,
+    then their vjps, several launches per instance -- captured once as a CUDA
+    graph.  Replaying it measures the per-instance launches themselves on the
+    GPU, not Python or ctypes dispatch."""
+
+    def __init__(self, desc, keys, vals, device="cuda"):
+        dev = torch.device(device)
+        self.desc, self.keys, self.vals, self.dev = desc, keys, vals, dev
+        count = len(desc)
+        f32 = dict(dtype=torch.float32, device=dev)
+        total_bins = int((desc["bin_off"] + desc["m"]).max())
+        self.h = torch.empty(total_bins, **f32)
+        self.sc = torch.empty(total_bins, **f32)
+        self.ybar = torch.empty(total_bins, **f32)
+        self.hbar = torch.empty(total_bins, **f32)
+        self.zeros = torch.zeros(int(desc["m"].max()), **f32)
+        self.losses = torch.empty(count, **f32)
+        self.loss = torch.empty(1, **f32)
+        self.lb = torch.ones(1, **f32)
+        self.rsaved = torch.empty(256, dtype=torch.uint8, device=dev)  # + reduce: no residuals
+        self.valsbar = torch.zeros_like(vals)  # padding positions stay 0, as in the batched path
+        ops = ["add" if d["op"] == OPCODE["add"] else "max" for d in desc]
+        sb = [max(adcomb.saved_bytes("hist", op, torch.float32, int(d["n"]), int(d["m"])), 16)
+              for op, d in zip(ops, desc)]
+        soff = _aligned_offsets(sb, 256)
+        self.saved = torch.empty(int(soff[-1] + sb[-1]), dtype=torch.uint8, device=dev)
+        need = max(max(adcomb.workspace_bytes("hist", op, torch.float32, int(d["n"]), int(d["m"])),
+                       adcomb.workspace_bytes("scan", "add", torch.float32, int(d["m"])),
+                       adcomb.workspace_bytes("reduce", "add", torch.float32, int(d["m"])))
+                   for op, d in zip(ops, desc))
+        self.ws = adcomb.Workspace()
+        self.ws.get(need, dev)
+        self.inst = []
+        for i, d in enumerate(desc):
+            n, m, vo, bo = int(d["n"]), int(d["m"]), int(d["val_off"]), int(d["bin_off"])
+            self.inst.append((ops[i], m, keys[vo:vo + n], vals[vo:vo + n], slice(bo, bo + m),
+                              self.saved[int(soff[i]):int(soff[i]) + sb[i]], self.valsbar[vo:vo + n]))
+        self.graph = None
+
+    def forward(self):
+        ws = self.ws
+        for i, (op, m, k, v, b, sv, _) in enumerate(self.inst):
+            adcomb.hist_fwd(op, m, k, v, self.zeros[:m], self.h[b], sv, ws=ws)
+            adcomb.scan_fwd("add", self.h[b], self.sc[b], ws=ws)
+            adcomb.reduce_fwd("add", self.sc[b], y=self.losses[i:i + 1], saved=self.rsaved, ws=ws)
+        torch.sum(self.losses, dim=0, keepdim=True, out=self.loss)
+        return self.loss
+
+    def backward(self):
+        ws = self.ws
+        for op, m, k, v, b, sv, vb in self.inst:
+            adcomb.reduce_vjp("add", self.sc[b], None, None, self.lb, xbar=self.ybar[b], ws=ws)
+            adcomb.scan_vjp("add", None, None, self.ybar[b], xbar=self.hbar[b], ws=ws)
+            adcomb.hist_vjp(op, m, k, v, self.zeros[:m], self.h[b], sv, self.hbar[b], valsbar=vb, ws=ws)
+        return self.valsbar
+
+    def capture(self):
+        s = torch.cuda.Stream(device=self.dev)
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):  # warm-up outside capture (per-device caches, kernel attributes)
+            self.forward()
+            self.backward()
+        torch.cuda.current_stream().wait_stream(s)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            self.forward()
+            self.backward()
+        self.graph = g
+
+    def replay(self):
+        if self.graph is None:
+            self.capture()
+        self.graph.replay()
+        return self.loss, self.valsbar

@@ -1,6 +1,7 @@
 // libadcomb C ABI: argument validation, workspace checks and dispatch.
 // Every entry point validates on the host, zeroes the workspace header (error
 // word and launch counters) on the stream, then queues its kernels.
+#include <atomic>
 #include <mutex>
 
 #include "common.cuh"
@@ -25,15 +26,19 @@ DevCtl make_ctl(void *ws, int slot) {
 }
 
 int num_sms() {
-    static int cache[64] = {0};
+    // Host threads may call at once: the entries are atomics (every writer
+    // stores the same value).
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 132;
-    if (cache[dev] == 0) {
+    int sms = cache[dev].load(std::memory_order_relaxed);
+    if (sms == 0) {
         int v = 0;
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
-        cache[dev] = v > 0 ? v : 132;
+        sms = v > 0 ? v : 132;
+        cache[dev].store(sms, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return sms;
 }
 
 adc_status check_launch() { return cudaGetLastError() == cudaSuccess ? ADC_OK : ADC_ERR_CUDA; }

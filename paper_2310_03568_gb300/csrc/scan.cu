@@ -120,6 +120,17 @@ template <typename T, int ITEMS> struct FwdMul : PlainScan<T, ITEMS, FwdMul<T, I
 template <typename T, int ITEMS, bool MAX> struct FwdSel : PlainScan<T, ITEMS, FwdSel<T, ITEMS, MAX>> {
     __device__ T identity() const { return MAX ? -Num<T>::inf() : Num<T>::inf(); }
     __device__ T combine(T a, T b) const { return (MAX ? (b > a) : (b < a)) ? b : a; }
+    // The scan's loop starts from y_0 = x_0, and a NaN never loses as the
+    // earlier operand, so a NaN x_0 makes every y_i NaN.  The partial scans
+    // here start from the identity, which a NaN cannot beat, so that case is
+    // written out: every output is x_0 when x_0 is NaN.
+    __device__ void store(int64_t c0, int64_t n, const T (&st)[ITEMS], const NoAux &) const {
+        const T x0 = __ldg(this->x);
+        T out[ITEMS];
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) out[k] = x0 != x0 ? x0 : st[k];
+        store_chunk(this->y, c0, n, out);
+    }
 };
 
 // linFnComp (Fig. 8): (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)

@@ -32,6 +32,8 @@
 // stored; later tiles see ERROR and stop waiting at once.
 #pragma once
 
+#include <atomic>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -480,18 +482,20 @@ template <class Op, int ITEMS> struct ScanShape {
 
 // Resident blocks per SM of one range-scan instantiation (cached per device).
 template <class Op, int ITEMS, bool REVERSE> int ranges_blocks_per_sm() {
-    static int cache[64] = {0};
+    // Host threads may call at once: the entries are atomics (every writer
+    // stores the same value).
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (cache[dev] == 0) {
-        int b = 0;
+    int b = cache[dev].load(std::memory_order_relaxed);
+    if (b == 0) {
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE>,
                                                           kScanThreads, 0) != cudaSuccess ||
             b < 1)
             b = 1;
-        cache[dev] = b;
+        cache[dev].store(b, std::memory_order_relaxed);
     }
-    return cache[dev];
+    return b;
 }
 
 // An Op may ask for ranges of a fixed number of tiles (static constexpr int

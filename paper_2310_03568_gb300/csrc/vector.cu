@@ -13,6 +13,7 @@
 // [m][d] operands to [d][n] through shared-memory tiles, call the scalar
 // kernels on the d contiguous columns and transpose the results back.
 // Operators: ADD, MUL, MIN, MAX (scalar elements).
+#include <atomic>
 #include "common.cuh"
 #include "hist_common.cuh"
 #include "internal.h"
@@ -437,7 +438,25 @@ template <typename T, int K> struct VScanFwd {  // K: 0 add, 1 mul, 2 min, 3 max
     }
     __device__ S state(int64_t, int64_t f, Aux &) const { return __ldg(x + f); }
     __device__ void store(int64_t f, const S &inc, const Aux &) const { y[f] = inc; }
+    // The state every column's scan starts from.  For min / max the scan's
+    // loop starts from y_0 = x_0, and a NaN never loses as the earlier operand,
+    // so a NaN in row 0 makes its whole column NaN: starting the column from
+    // that NaN (instead of the identity, which a NaN cannot beat) gives it.
+    __device__ S initial(int64_t c) const {
+        if (K < 2) return identity();
+        const T x0 = __ldg(x + c);
+        return x0 != x0 ? x0 : identity();
+    }
 };
+
+// The state column c's scan starts from: the op's initial(c) where it has one.
+template <class Op> __device__ __forceinline__ typename Op::S vscan_initial(const Op &op, int64_t c, long) {
+    return op.identity();
+}
+template <class Op>
+__device__ __forceinline__ auto vscan_initial(const Op &op, int64_t c, int) -> decltype(op.initial(c)) {
+    return op.initial(c);
+}
 
 // + scan vjp: xbar_i = sum_{j >= i} ybar_j (a reverse + scan).
 template <typename T> struct VScanVjpAdd {
@@ -641,6 +660,7 @@ __global__ void k_vscan_prefix(const Op op, const typename Op::S *__restrict__ a
     const S inc = warp_inclusive_scan(op, v);
     S run = shfl_up(inc, 1);
     if (lane == 0) run = op.identity();
+    run = op.combine(vscan_initial(op, c, 0), run);
     for (int g = g0; g < g1; ++g) {
         pre[(int64_t)g * d + c] = run;
         run = op.combine(run, agg[(int64_t)g * d + c]);
@@ -766,7 +786,7 @@ k_vscan_wprefix(const Op op, const typename Op::S *__restrict__ agg, const int64
     const S inc = warp_inclusive_scan(op, v);
     if (lane == kWarp - 1) s_w[w] = inc;
     __syncthreads();
-    S run = op.identity();
+    S run = vscan_initial(op, c, 0);
     for (int j = 0; j < w; ++j) run = op.combine(run, s_w[j]);
     S ex = shfl_up(inc, 1);
     if (lane > 0) run = op.combine(run, ex);
@@ -814,17 +834,21 @@ k_vscan_wapply(const Op op, const int64_t n, const int64_t d, const int64_t U, c
 // (cached per device) times the units a block holds, fewer for short inputs
 // (at least 64 rows a unit).
 template <class Op, int RP, bool WARP> static int64_t vscan_units(int64_t n) {
-    static int cache[64] = {0};
+    // Host threads may call at once: the entries are atomics (every writer
+    // stores the same value).
+    static std::atomic<int> cache[64];
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) dev = 0;
-    if (cache[dev] == 0) {
+    int per_sm = cache[dev].load(std::memory_order_relaxed);
+    if (per_sm == 0) {
         int b = 0;
         const void *k = WARP ? (const void *)k_vscan_wapply<Op, RP> : (const void *)k_vscan_apply<Op, RP>;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k, kVScanThreads, 0) != cudaSuccess || b < 1) b = 1;
-        cache[dev] = b < kVScanMaxBlocksPerSM ? b : kVScanMaxBlocksPerSM;
+        per_sm = b < kVScanMaxBlocksPerSM ? b : kVScanMaxBlocksPerSM;
+        cache[dev].store(per_sm, std::memory_order_relaxed);
     }
     const int64_t want = (n + 63) / 64;
-    const int64_t cap = (int64_t)num_sms() * cache[dev] * (WARP ? kVScanWarps : 1);
+    const int64_t cap = (int64_t)num_sms() * per_sm * (WARP ? kVScanWarps : 1);
     return want < 1 ? 1 : want < cap ? want : cap;
 }
 

@@ -227,16 +227,15 @@ def test_minmax_scan_nan_and_integer_adjoints(op, engine_id):
     leaves y unchanged.  The kernels read the selections off y (x_i wins step
     i exactly when y_i differs from y_{i-1}); with integer ybar every adjoint
     is an exact sum, so the vjp must equal the oracle's, which compares x with
-    y.  (A NaN x_0 is left out: the identity (+-inf) combined with NaN gives
-    the identity, so the kernels' y_0 is +-inf where the sequential definition
-    y_0 = x_0 gives NaN.)"""
+    y.  A NaN x_0 makes every y_i NaN (y_0 = x_0, and NaN never loses as the
+    earlier operand); all of the adjoint then goes to x_0."""
     g = np.random.default_rng(43)
     try:
         adcomb.debug_set_scan_engine(engine_id)
-        for n in [1000, 100_003]:
+        for n, x0 in [(1000, 1.0), (100_003, 1.0), (1000, np.nan), (100_003, np.nan)]:
             x = ((g.integers(0, 64, n) - 32) / 8.0).astype(np.float32)
             x[g.random(n) < 0.05] = np.nan
-            x[0] = 1.0
+            x[0] = x0
             yb = g.integers(-3, 4, n).astype(np.float32)
             xd = dev(x)
             y = adcomb.scan_fwd(op, xd)

@@ -15,7 +15,8 @@ pytestmark = pytest.mark.gpu
 # uniform scalar rows (("add", "add"), ("add",) * 64, ("max",) * 5, ("mul",) * 3)
 # take the vectorised scan's direct form; the others split into planes
 MIXES = [("add", "mul", "lin", "sop", "mm2", "min"), ("sop", "sop", "sop"), ("mm3", "max", "lin"), ("lin",),
-         ("add", "add"), ("sop",) * 16, ("add",) * 64, ("mm5", "mm5"), ("mul", "mm3"), ("max",) * 5, ("mul",) * 3]
+         ("add", "add"), ("sop",) * 16, ("add",) * 64, ("mm5", "mm5"), ("mul", "mm3"), ("max",) * 5, ("mul",) * 3,
+         ("min",) * 7]
 SIZES = [0, 1, 2, 33, 1025, 4097, 100_003]
 
 
@@ -144,6 +145,28 @@ def test_tuple_rows_equal_blocks_bit_for_bit():
     for c, (_, o, w) in enumerate(blocks):
         assert torch.equal(y[:, o:o + w], ys[c])
         assert torch.equal(xb[:, o:o + w], xbs[c])
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("ops", [("min",) * 7, ("max",) * 3, ("min", "max", "add")], ids="-".join)
+def test_tuple_minmax_ties_and_nans_exact(ops, dt):
+    """Tied levels everywhere and NaNs (5% of the entries, and row 0 in some
+    blocks) through the tuple entry points, with integer ybar: the selections
+    and every adjoint (an exact sum) must equal the oracle's bit for bit.  A
+    NaN never wins after row 0; a NaN in row 0 makes its whole block NaN and
+    sends the block's whole adjoint to row 0."""
+    g = np.random.default_rng(61 + len(ops))
+    for n in (1000, 100_003):
+        x = ((g.integers(0, 64, (n, len(ops))) - 32) / 8.0).astype(dt)
+        x[g.random(x.shape) < 0.05] = np.nan
+        x[0] = 1.0
+        x[0, ::3] = np.nan
+        yb = g.integers(-3, 4, x.shape).astype(dt)
+        xd = dev(x)
+        y = adcomb.tscan_fwd(ops, xd)
+        xb = adcomb.tscan_vjp(ops, xd, y, dev(yb))
+        assert np.array_equal(host(y), oracle.tscan_fwd(ops, x).astype(dt), equal_nan=True)
+        assert np.array_equal(host(xb), oracle.tscan_vjp(ops, x, yb).astype(dt))
 
 
 def test_tuple_single_block_equals_scalar_entry():

@@ -114,14 +114,17 @@ def test_vscan_many_tiles_per_unit(op, d):
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_vscan_minmax_nan_and_integer_adjoints(op, d, dt):
     """The min / max vjps read the selections off y (x_i wins step i exactly
-    when y_i differs from y_{i-1}): with NaNs in x (never selected) after row
-    0 and integer ybar, every adjoint is an exact sum and equals the
-    oracle's, which compares x with y."""
+    when y_i differs from y_{i-1}): with NaNs in x (never selected after row
+    0) and integer ybar, every adjoint is an exact sum and equals the
+    oracle's, which compares x with y.  Row 0 holds NaN in some columns: a
+    NaN x_0 makes its whole column NaN (y_0 = x_0, and NaN never loses as the
+    earlier operand) and sends the column's whole adjoint to x_0."""
     g = np.random.default_rng(95 + d)
     n = 100_003
     x = ((g.integers(0, 64, (n, d)) - 32) / 8.0).astype(dt)
     x[g.random((n, d)) < 0.05] = np.nan
     x[0] = 1.0
+    x[0, ::2] = np.nan
     yb = g.integers(-3, 4, (n, d)).astype(dt)
     xd = dev(x)
     y = adcomb.vscan_fwd(op, xd)
