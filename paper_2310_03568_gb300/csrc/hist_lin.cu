@@ -1,48 +1,48 @@
 // General reduce_by_index for the non-commutative linFnComp operator with up
 // to a few thousand bins (Sec. 4.1, Fig. 4).  The paper sorts the elements by
-// bin (stable), then runs segmented scans; here the stable sort is done
-// hierarchically so that no pass moves the whole input more than once:
-//   1. per chunk of kLChunk elements (one block): a stable counting sort of the
-//      chunk by bin in shared memory (warp ranks from per-bit ballots, per-warp
-//      bin counters, so equal bins keep index order), then a segmented fold per
-//      bin -> the chunk's partial P[bin][chunk] (identity where the bin is
-//      absent);
-//   2. across chunks, per bin, two segmented scans of the small [m][chunks]
-//      matrix with the look-back engine: L[bin][c] = hist0 . P[bin][0..c-1]
-//      and R[bin][c] = P[bin][c+1..]; hist = L . P at the last chunk, and the
-//      bin total A = P[bin][0] . R[bin][0] (for hist0bar);
-//   3. vjp: per chunk again the stable local sort, in-chunk segmented
-//      exclusive prefix and suffix, l_i = L . prefix_i, r_i = suffix_i . R, and
-//      vbar_i = d(l_i . v_i . r_i)/dv_i ^T histbar[k_i], put back in element
-//      order in shared memory and written coalesced.
+// bin (stable) and runs segmented scans over the sorted values; what those
+// scans compute per element is the fold of its bin's values before it (l_i)
+// and after it (r_i), in index order.  Here no element is moved:
+//   1. per chunk of kLThreads * R elements (one block; warp w owns the w-th
+//      run of 32 * R consecutive elements, R rounds of 32): every warp walks
+//      its run in index order and folds each element into its bin's entry of
+//      a warp-private table in shared memory.  Within a round, lanes holding
+//      the same bin (__match_any_sync peers) update one after another in lane
+//      order, so every bin's entry is the ordered fold of the run's values;
+//      the block then composes the warp tables per bin in warp order ->
+//      P[bin][chunk] (identity where the bin is absent);
+//   2. one block per bin composes its row of P in chunk order: the exclusive
+//      prefix L[bin][c] = hist0 . P[bin][0..c-1], the exclusive suffix
+//      R[bin][c] = P[bin][c+1..], hist = L . P at the last chunk and the bin
+//      total A = P[bin][0] . R[bin][0] (for hist0bar);
+//   3. vjp, per chunk: the forward walk again, keeping each element's
+//      exclusive prefix p_i within its warp run, and a backward walk keeping
+//      the product s_i of the c's after it; per bin and warp the block forms
+//      what lies before the run (L . earlier runs) and the product of the c's
+//      after it (later runs, R), and every element gets
+//      vbar_i = d(l_i . v_i . r_i)/dv_i ^T histbar[k_i] with l_i = before . p_i
+//      and r_i.c = s_i * after.c.
 // Within every bin the values meet in index order, as the sequential
 // definition requires; only the bracketing differs (associativity).
-// Residuals: L, R and A (about 2 * 8 * m * n / kLChunk bytes) instead of the
-// global sort's permutation, sorted keys and sorted values (16 bytes/element).
+// Traffic: the forward reads keys and values once (12 B per fp32 element) and
+// moves the [m][chunks] matrices (P, L, R: 8 B per bin and chunk each); the
+// vjp reads keys, values, L and R and writes the adjoints once.
 #include "common.cuh"
 #include "hist_common.cuh"
 #include "internal.h"
-#include "scan_engine.cuh"
-#include "tile_io.cuh"
 
 namespace adc {
 
 constexpr int kLThreads = 256;
 constexpr int kLWarps = kLThreads / kWarp;
-// Bins fit 16 bits, and the vjp's shared memory (per-warp counters, the
-// sorted chunk, prefixes, per-bin L, R, histbar) fits one block: 2047 bins for
-// fp32, 1023 for fp64.
+// The vjp's shared memory (per-warp tables of (b, c) and of c, histbar) fits
+// one block up to 2047 bins (fp32) / 1023 bins (fp64).
 template <typename T> constexpr int64_t lmax_bins() { return sizeof(T) == 4 ? 2047 : 1023; }
 template <typename T> struct LChunk {
-    static constexpr int kRounds = sizeof(T) == 4 ? 16 : 8;     // rounds of 32 elements per warp
-    static constexpr int kSize = kLThreads * kRounds;           // elements per chunk (block)
-    static constexpr int kSpan = kRounds;                       // sorted positions per thread
-    static constexpr int kPad = kSize + kSize / 16;             // padded shared arrays
+    static constexpr int kRounds = sizeof(T) == 4 ? 16 : 8;  // rounds of 32 elements per warp
+    static constexpr int kRun = kWarp * kRounds;             // elements per warp
+    static constexpr int kSize = kLThreads * kRounds;        // elements per chunk (block)
 };
-// Sorted position -> padded shared index: one spare slot every 16, so that a
-// thread walking 16 consecutive positions does not collide with its neighbours.
-__device__ __forceinline__ int pad16(int p) { return p + (p >> 4); }
-__host__ __device__ constexpr size_t al16(size_t v) { return (v + 15) / 16 * 16; }
 
 template <typename T> __device__ __forceinline__ Pair<T> lf(const Pair<T> &a, const Pair<T> &b) {
     return {b.b + b.c * a.b, b.c * a.c};  // (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)
@@ -53,355 +53,296 @@ template <typename T> __device__ __forceinline__ Pair<T> lf_adj(const Pair<T> &l
     return {r.c * g.b, r.c * (l.b * g.b + l.c * g.c)};
 }
 
-// Segmented-scan state: flag = a segment boundary lies inside.
-template <typename T> struct LSeg {
-    Pair<T> v;
-    uint32_t f;
-    uint32_t pad;
-};
-template <typename T> struct LSegFwdOp {  // physical order: a before b
-    __device__ LSeg<T> identity() const { return {lf_id<T>(), 0u, 0u}; }
-    __device__ LSeg<T> combine(const LSeg<T> &a, const LSeg<T> &b) const {
-        return {b.f ? b.v : lf(a.v, b.v), a.f | b.f, 0u};
-    }
-};
-template <typename T> struct LSegRevOp {  // logical order decreasing index: e lies physically before acc
-    __device__ LSeg<T> identity() const { return {lf_id<T>(), 0u, 0u}; }
-    __device__ LSeg<T> combine(const LSeg<T> &acc, const LSeg<T> &e) const {
-        return {e.f ? e.v : lf(e.v, acc.v), acc.f | e.f, 0u};
-    }
-};
-
-// Block-wide exclusive scan of one state per thread, in thread order (fwd) or
-// reverse thread order (rev).  Two __syncthreads().
-template <class Op, typename S, bool REV>
-__device__ __forceinline__ S lblock_excl(const Op &op, const S &a, S *s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // reverse order = a forward scan over mirrored lanes and warps
-    const int vl = REV ? (kWarp - 1 - lane) : lane;
-    const int vw = REV ? (kLWarps - 1 - warp) : warp;
-    S x = a;
-#pragma unroll
-    for (int o = 1; o < kWarp; o <<= 1) {
-        const S up = REV ? shfl_down(x, o) : shfl_up(x, o);
-        if (vl >= o) x = op.combine(up, x);
-    }
-    if (vl == kWarp - 1) s_w[vw] = x;
-    S ex = REV ? shfl_down(x, 1) : shfl_up(x, 1);
-    if (vl == 0) ex = op.identity();
-    __syncthreads();
-    S before = op.identity();
-#pragma unroll
-    for (int w = 0; w < kLWarps; ++w)
-        if (w < vw) before = op.combine(before, s_w[w]);
-    __syncthreads();
-    return op.combine(before, ex);
+// One (b, c) element as one 8- or 16-byte streaming load (the array is
+// 16-byte aligned, so every element is aligned to its size).
+__device__ __forceinline__ Pair<float> ld_pair(const Pair<float> *p) {
+    const float2 t = __ldcs(reinterpret_cast<const float2 *>(p));
+    return {t.x, t.y};
+}
+__device__ __forceinline__ Pair<double> ld_pair(const Pair<double> *p) {
+    const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+    return {t.x, t.y};
 }
 
-// ------------------------------------------------------------ chunk pass --
-// VJP = false: writes P[bin * nc + chunk].  VJP = true: writes vbar.
-template <typename T, bool VJP>
+// One warp run of a chunk: keys (-1 past n) and values, round r at element
+// base + r * 32 + lane, every load issued before the first use.
+template <typename T, int R>
+__device__ __forceinline__ void load_run(const int32_t *__restrict__ keys, const Pair<T> *__restrict__ vals,
+                                         int64_t base, int64_t n, int m, int32_t (&k)[R], Pair<T> (&v)[R]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = base + r * kWarp + lane;
+        k[r] = i < n ? __ldcs(keys + i) : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int64_t i = base + r * kWarp + lane;
+        v[r] = in_range(k[r], m) ? ld_pair(vals + i) : lf_id<T>();
+    }
+}
+
+// One round of a warp walk: upd() runs for every lane with an in-range key,
+// in lane order among lanes that share a key (REV: descending lane order),
+// lanes with different keys at once.  Every such lane first writes its lane
+// number to its key's byte in `tag` (one byte per bin and warp): when each
+// reads its own number back, no two lanes share a key and all update in one
+// step; otherwise __match_any_sync groups the lanes and the groups advance
+// one rank per step.  Warp-wide: all lanes call it.
+template <bool REV, class F>
+__device__ __forceinline__ void ordered_round(int32_t key, bool ok, uint8_t *tag, F &&upd) {
+    const int lane = threadIdx.x & 31;
+    if (ok) tag[key] = (uint8_t)lane;
+    __syncwarp();
+    const bool alone = !ok || tag[key] == (uint8_t)lane;
+    if (__all_sync(0xffffffffu, alone)) {
+        if (ok) upd();
+    } else {
+        const unsigned peers = __match_any_sync(0xffffffffu, ok ? key : -1);
+        const unsigned ahead = REV ? (peers & ~((2u << lane) - 1u)) : (peers & ((1u << lane) - 1u));
+        const int rank = __popc(ahead);
+        for (int q = 0; __any_sync(0xffffffffu, ok && rank >= q); ++q) {
+            if (ok && rank == q) upd();
+            __syncwarp();
+        }
+    }
+    __syncwarp();
+}
+
+// ------------------------------------------------------------ chunk fold --
+// P[bin * nc + chunk] = ordered fold of the chunk's values of that bin.
+template <typename T>
 __global__ void __launch_bounds__(kLThreads)
-k_linh_chunk(const int32_t *__restrict__ keys, const Pair<T> *__restrict__ vals, const int64_t n, const int m,
-             const int64_t nc, Pair<T> *__restrict__ P, const Pair<T> *__restrict__ L, const Pair<T> *__restrict__ R,
-             const Pair<T> *__restrict__ hb, Pair<T> *__restrict__ vbar, const int accumulate) {
+k_linh_fold(const int32_t *__restrict__ keys, const Pair<T> *__restrict__ vals, const int64_t n, const int m,
+            const int64_t nc, Pair<T> *__restrict__ P) {
     using C = LChunk<T>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    // [shared region: per-warp counters, then fwd bin totals / vjp outputs] [values] [bins] [vjp: src, prefixes]
-    const size_t region = (size_t)kLWarps * m * 4 > (VJP ? (size_t)C::kSize * sizeof(Pair<T>) : (size_t)m * sizeof(Pair<T>))
-                              ? (size_t)kLWarps * m * 4
-                              : (VJP ? (size_t)C::kSize * sizeof(Pair<T>) : (size_t)m * sizeof(Pair<T>));
-    int32_t *s_cnt = reinterpret_cast<int32_t *>(smem_raw);
-    Pair<T> *s_tot = reinterpret_cast<Pair<T> *>(smem_raw);  // fwd, after placement
-    Pair<T> *s_out = reinterpret_cast<Pair<T> *>(smem_raw);  // vjp, after placement
-    Pair<T> *s_val = reinterpret_cast<Pair<T> *>(smem_raw + al16(region));
-    uint16_t *s_bin = reinterpret_cast<uint16_t *>(s_val + C::kPad);
-    uint16_t *s_src = s_bin + C::kPad;
-    Pair<T> *s_pre = reinterpret_cast<Pair<T> *>(smem_raw + al16(region) + (size_t)C::kPad * sizeof(Pair<T>) +
-                                                 al16((size_t)C::kPad * 4));
-    Pair<T> *s_lrh = s_pre + C::kPad;  // vjp: L, R and histbar of every bin for this chunk
-    __shared__ int32_t s_part[kLWarps];
-    __shared__ LSeg<T> s_seg[kLWarps];
-
+    Pair<T> *s_tab = reinterpret_cast<Pair<T> *>(smem_raw);              // [kLWarps][m]
+    uint8_t *s_tag = reinterpret_cast<uint8_t *>(s_tab + (size_t)kLWarps * m);  // [kLWarps][m]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t c = blockIdx.x;
-    const int64_t base = c * C::kSize;
-    const int len = (int)((n - base) < (int64_t)C::kSize ? (n - base) : (int64_t)C::kSize);  // may be <= 0 when n = 0
-    for (int j = tid; j < kLWarps * m; j += kLThreads) s_cnt[j] = 0;
-    __syncthreads();
-
-    // ---- stable ranks: warp w owns elements [w * 32 * kRounds, ...), rounds in order
-    int32_t *wc = s_cnt + warp * m;
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t pk[C::kRounds];  // bin << 16 | rank within (warp, bin); bin == m: absent
-    int32_t kk[C::kRounds];
-#pragma unroll
-    for (int r = 0; r < C::kRounds; ++r) {  // all loads in flight before the first use
-        const int t = warp * (kWarp * C::kRounds) + r * kWarp + lane;
-        kk[r] = t < len ? __ldcs(keys + base + t) : -1;
-    }
-    const int nbits = 32 - __clz(m);  // bits of the bin values 0..m (m: absent)
+    Pair<T> *tab = s_tab + (size_t)warp * m;
+    uint8_t *tag = s_tag + (size_t)warp * m;
+    int32_t k[C::kRounds];
+    Pair<T> v[C::kRounds];
+    load_run<T, C::kRounds>(keys, vals, c * C::kSize + (int64_t)warp * C::kRun, n, m, k, v);
+    for (int j = lane; j < m; j += kWarp) tab[j] = lf_id<T>();
+    __syncwarp();
 #pragma unroll
     for (int r = 0; r < C::kRounds; ++r) {
-        const int d = in_range(kk[r], m) ? kk[r] : m;
-        // lanes holding the same bin: intersect one ballot per bit of d
-        unsigned peers = 0xffffffffu;
-        for (int bit = 0; bit < nbits; ++bit) {
-            const unsigned b = __ballot_sync(0xffffffffu, (d >> bit) & 1);
-            peers &= ((d >> bit) & 1) ? b : ~b;
-        }
-        const int before = __popc(peers & lt);
-        int prior = 0;
-        if (d < m) prior = wc[d];
-        __syncwarp();
-        if (d < m && before == 0) wc[d] = prior + __popc(peers);
-        __syncwarp();
-        pk[r] = ((uint32_t)d << 16) | (uint32_t)(prior + before);
+        const int32_t key = k[r];
+        const Pair<T> x = v[r];
+        ordered_round<false>(key, in_range(key, m), tag, [&] { tab[key] = lf(tab[key], x); });
     }
     __syncthreads();
-
-    // ---- bin starts: exclusive scan over bins of the per-bin totals, warps in order within a bin
-    const int per = (m + kLThreads - 1) / kLThreads;
-    const int b0 = tid * per, b1 = (b0 + per < m) ? b0 + per : m;
-    int32_t sum = 0;
-    for (int b = b0; b < b1; ++b)
-        for (int w = 0; w < kLWarps; ++w) sum += s_cnt[w * m + b];
-    int32_t inc = sum;
+    for (int j = tid; j < m; j += kLThreads) {
+        Pair<T> acc = s_tab[j];
 #pragma unroll
-    for (int o = 1; o < kWarp; o <<= 1) {
-        const int32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == kWarp - 1) s_part[warp] = inc;
-    __syncthreads();
-    int32_t run = inc - sum, V = 0;
-#pragma unroll
-    for (int w = 0; w < kLWarps; ++w) {
-        if (w < warp) run += s_part[w];
-        V += s_part[w];
-    }
-    for (int b = b0; b < b1; ++b)
-        for (int w = 0; w < kLWarps; ++w) {
-            const int32_t x = s_cnt[w * m + b];
-            s_cnt[w * m + b] = run;
-            run += x;
-        }
-    __syncthreads();
-
-    // ---- placement (values read here, once, coalesced, all in flight together)
-    Pair<T> vv[C::kRounds];
-#pragma unroll
-    for (int r = 0; r < C::kRounds; ++r) {
-        const int t = warp * (kWarp * C::kRounds) + r * kWarp + lane;
-        if ((int)(pk[r] >> 16) < m) vv[r] = vals[base + t];
-    }
-#pragma unroll
-    for (int r = 0; r < C::kRounds; ++r) {
-        const int t = warp * (kWarp * C::kRounds) + r * kWarp + lane;
-        const int d = (int)(pk[r] >> 16);
-        if (d < m) {
-            const int p = pad16(s_cnt[warp * m + d] + (int)(pk[r] & 0xffffu));
-            s_val[p] = vv[r];
-            s_bin[p] = (uint16_t)d;
-            if (VJP) s_src[p] = (uint16_t)t;
-        }
-    }
-    __syncthreads();
-    if (!VJP) {
-        for (int j = tid; j < m; j += kLThreads) s_tot[j] = lf_id<T>();
-    } else {
-        for (int j = tid; j < C::kSize; j += kLThreads) s_out[j] = Pair<T>{T(0), T(0)};
-        for (int j = tid; j < m; j += kLThreads) {
-            s_lrh[3 * j] = L[(int64_t)j * nc + c];
-            s_lrh[3 * j + 1] = R[(int64_t)j * nc + c];
-            s_lrh[3 * j + 2] = hb[j];
-        }
-    }
-    __syncthreads();
-
-    // ---- forward segmented walk over this thread's sorted positions
-    const int p0 = tid * C::kSpan;
-    const LSegFwdOp<T> fop;
-    LSeg<T> agg = fop.identity();
-#pragma unroll
-    for (int j = 0; j < C::kSpan; ++j) {
-        const int p = p0 + j;
-        if (p < V) {
-            const int q = pad16(p);
-            const bool head = p == 0 || s_bin[q] != s_bin[pad16(p - 1)];
-            agg = fop.combine(agg, LSeg<T>{s_val[q], head ? 1u : 0u, 0u});
-        }
-    }
-    const LSeg<T> carry = lblock_excl<LSegFwdOp<T>, LSeg<T>, false>(fop, agg, s_seg);
-    Pair<T> acc = carry.v;
-#pragma unroll
-    for (int j = 0; j < C::kSpan; ++j) {
-        const int p = p0 + j;
-        if (p < V) {
-            const int q = pad16(p);
-            const int bin = s_bin[q];
-            if (p == 0 || bin != s_bin[pad16(p - 1)]) acc = lf_id<T>();
-            if (VJP) s_pre[q] = acc;  // exclusive in-chunk prefix of this bin
-            acc = lf(acc, s_val[q]);
-            if (!VJP && (p == V - 1 || bin != s_bin[pad16(p + 1)])) s_tot[bin] = acc;
-        }
-    }
-    if (!VJP) {
-        __syncthreads();
-        for (int j = tid; j < m; j += kLThreads) P[(int64_t)j * nc + c] = s_tot[j];
-        return;
-    }
-
-    // ---- vjp: reverse segmented walk (suffixes), then the map
-    const LSegRevOp<T> rop;
-    LSeg<T> ragg = rop.identity();
-#pragma unroll
-    for (int j = C::kSpan - 1; j >= 0; --j) {
-        const int p = p0 + j;
-        if (p < V) {
-            const int q = pad16(p);
-            const bool tail = p == V - 1 || s_bin[q] != s_bin[pad16(p + 1)];
-            ragg = rop.combine(ragg, LSeg<T>{s_val[q], tail ? 1u : 0u, 0u});
-        }
-    }
-    const LSeg<T> rcarry = lblock_excl<LSegRevOp<T>, LSeg<T>, true>(rop, ragg, s_seg);
-    Pair<T> racc = rcarry.v;
-#pragma unroll
-    for (int j = C::kSpan - 1; j >= 0; --j) {
-        const int p = p0 + j;
-        if (p < V) {
-            const int q = pad16(p);
-            const int bin = s_bin[q];
-            if (p == V - 1 || bin != s_bin[pad16(p + 1)]) racc = lf_id<T>();
-            const Pair<T> l = lf(s_lrh[3 * bin], s_pre[q]);
-            const Pair<T> rr = lf(racc, s_lrh[3 * bin + 1]);
-            s_out[s_src[q]] = lf_adj(l, rr, s_lrh[3 * bin + 2]);
-            racc = lf(s_val[q], racc);
-        }
-    }
-    __syncthreads();
-    for (int t = tid; t < len; t += kLThreads) {
-        const Pair<T> g = s_out[t];
-        if (accumulate) {
-            const Pair<T> o = vbar[base + t];
-            vbar[base + t] = Pair<T>{o.b + g.b, o.c + g.c};
-        } else {
-            vbar[base + t] = g;
-        }
+        for (int w = 1; w < kLWarps; ++w) acc = lf(acc, s_tab[(size_t)w * m + j]);
+        P[(int64_t)j * nc + c] = acc;
     }
 }
 
-// ------------------------------------------------------- column scans --
-// Over the [m][nc] matrix P (bin-major).  Forward: element (bin, c) carries
-// hist0[bin] at c = 0 (a segment start) and P[bin][c-1] otherwise, so the
-// inclusive value is L[bin][c]; at the last chunk hist[bin] = L . P.
-template <typename T, int ITEMS> struct ColFwd {
-    using State = LSeg<T>;
-    struct Aux {
-        Pair<T> v[ITEMS];
-    };
-    struct Raw {
-        Pair<T> v[ITEMS];
-        Pair<T> vprev;
-    };
-    const Pair<T> *P;
-    const Pair<T> *h0;
-    Pair<T> *Lout;
-    Pair<T> *hist;
-    int64_t nc;
-    __device__ State identity() const { return {lf_id<T>(), 0u, 0u}; }
-    __device__ State combine(const State &a, const State &b) const { return {b.f ? b.v : lf(a.v, b.v), a.f | b.f, 0u}; }
-    __device__ void fetch(int64_t c0, int64_t N, Raw &r) const {
-        load_chunk(P, c0, N, r.v, lf_id<T>());
-        r.vprev = (c0 > 0 && c0 <= N) ? P[c0 - 1] : lf_id<T>();
-    }
-    __device__ void build(int64_t c0, int64_t N, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
-        int64_t bin = c0 / nc, cc = c0 - bin * nc;
+// ------------------------------------------------------------- bin rows --
+// Block-wide exclusive scan of one state per thread in thread order (REV:
+// reverse thread order) for linFnComp; two __syncthreads().
+template <typename T, bool REV>
+__device__ __forceinline__ Pair<T> lblock_excl(Pair<T> a, Pair<T> *s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int vl = REV ? (kWarp - 1 - lane) : lane;
+    const int vw = REV ? (kLWarps - 1 - warp) : warp;
+    // REV: a forward scan over mirrored lanes and warps with the operands
+    // swapped (later elements come first in logical order)
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            aux.v[j] = r.v[j];
-            const bool head = cc == 0;
-            const Pair<T> q = head ? (h0 ? h0[bin] : lf_id<T>()) : (j == 0 ? r.vprev : r.v[j - 1]);
-            st[j] = (c0 + j < N) ? State{q, head ? 1u : 0u, 0u} : identity();
-            if (++cc == nc) {
-                cc = 0;
-                ++bin;
-            }
-        }
+    for (int o = 1; o < kWarp; o <<= 1) {
+        const Pair<T> up = REV ? shfl_down(a, o) : shfl_up(a, o);
+        if (vl >= o) a = REV ? lf(a, up) : lf(up, a);
     }
-    __device__ void store(int64_t c0, int64_t N, const State (&st)[ITEMS], const Aux &aux) const {
-        Pair<T> o[ITEMS];
+    if (vl == kWarp - 1) s_w[vw] = a;
+    Pair<T> ex = REV ? shfl_down(a, 1) : shfl_up(a, 1);
+    if (vl == 0) ex = lf_id<T>();
+    __syncthreads();
+    Pair<T> before = lf_id<T>();
 #pragma unroll
-        for (int j = 0; j < ITEMS; ++j) o[j] = st[j].v;
-        store_chunk(Lout, c0, N, o);
-        int64_t bin = c0 / nc, cc = c0 - bin * nc;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (c0 + j < N && cc == nc - 1) hist[bin] = lf(st[j].v, aux.v[j]);
-            if (++cc == nc) {
-                cc = 0;
-                ++bin;
-            }
-        }
-    }
-};
+    for (int w = 0; w < kLWarps; ++w)
+        if (w < vw) before = REV ? lf(s_w[w], before) : lf(before, s_w[w]);
+    __syncthreads();
+    return REV ? lf(ex, before) : lf(before, ex);
+}
 
-// Reverse (logical order = decreasing index): element (bin, c) carries
-// P[bin][c+1], identity at the last chunk (a segment start in this order), so
-// the inclusive value is R[bin][c]; at c = 0 the bin total A = P[bin][0] . R.
-template <typename T, int ITEMS> struct ColRev {
-    using State = LSeg<T>;
-    struct Aux {
-        Pair<T> v[ITEMS];
-    };
-    struct Raw {
-        Pair<T> v[ITEMS];
-        Pair<T> vnext;
-    };
-    const Pair<T> *P;
-    Pair<T> *Rout;
-    Pair<T> *A;
-    int64_t nc;
-    __device__ State identity() const { return {lf_id<T>(), 0u, 0u}; }
-    __device__ State combine(const State &acc, const State &e) const {
-        return {e.f ? e.v : lf(e.v, acc.v), acc.f | e.f, 0u};
-    }
-    __device__ void fetch(int64_t c0, int64_t N, Raw &r) const {
-        load_chunk(P, c0, N, r.v, lf_id<T>());
-        r.vnext = (c0 + ITEMS < N) ? P[c0 + ITEMS] : lf_id<T>();
-    }
-    __device__ void build(int64_t c0, int64_t N, const Raw &r, State (&st)[ITEMS], Aux &aux) const {
-        int64_t bin = c0 / nc, cc = c0 - bin * nc;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            aux.v[j] = r.v[j];
-            const bool head = cc == nc - 1;
-            const Pair<T> q = head ? lf_id<T>() : (j + 1 < ITEMS ? r.v[j + 1] : r.vnext);
-            st[j] = (c0 + j < N) ? State{q, head ? 1u : 0u, 0u} : identity();
-            if (++cc == nc) {
-                cc = 0;
-                ++bin;
-            }
-        }
-    }
-    __device__ void store(int64_t c0, int64_t N, const State (&st)[ITEMS], const Aux &aux) const {
-        Pair<T> o[ITEMS];
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) o[j] = st[j].v;
-        store_chunk(Rout, c0, N, o);
-        int64_t bin = c0 / nc, cc = c0 - bin * nc;
-#pragma unroll
-        for (int j = 0; j < ITEMS; ++j) {
-            if (c0 + j < N && cc == 0) A[bin] = lf(aux.v[j], st[j].v);
-            if (++cc == nc) {
-                cc = 0;
-                ++bin;
-            }
-        }
-    }
-};
+// One block per bin j: L[j][c], R[j][c], hist[j], A[j] from the row P[j][.].
+// The row goes through shared memory in segments of kRowSeg entries (loads
+// and stores coalesced); within a segment thread t composes its 8 consecutive
+// entries and a block scan gives what lies before (L) or after (R) them.
+constexpr int kRowItems = 8;
+constexpr int kRowSeg = kLThreads * kRowItems;
 
-template <typename T> struct ColItems { static constexpr int v = 64 / (2 * (int)sizeof(T)); };
+template <typename T>
+__global__ void __launch_bounds__(kLThreads)
+k_linh_rows(const Pair<T> *__restrict__ P, const Pair<T> *__restrict__ h0, const int64_t nc,
+            Pair<T> *__restrict__ L, Pair<T> *__restrict__ R, Pair<T> *__restrict__ hist, Pair<T> *__restrict__ A) {
+    __shared__ Pair<T> s_seg[kRowSeg];
+    __shared__ Pair<T> s_w[kLWarps];
+    __shared__ Pair<T> s_tot;
+    const int tid = threadIdx.x;
+    const int64_t j = blockIdx.x;
+    const Pair<T> *row = P + j * nc;
+    // forward: L = hist0 . the entries before
+    Pair<T> carry = h0 ? h0[j] : lf_id<T>();
+    for (int64_t s0 = 0; s0 < nc; s0 += kRowSeg) {
+        const int len = (int)((nc - s0) < kRowSeg ? (nc - s0) : kRowSeg);
+        for (int e = tid; e < len; e += kLThreads) s_seg[e] = row[s0 + e];
+        __syncthreads();
+        Pair<T> v[kRowItems], agg = lf_id<T>();
+#pragma unroll
+        for (int k = 0; k < kRowItems; ++k) {
+            const int idx = tid * kRowItems + k;
+            v[k] = idx < len ? s_seg[idx] : lf_id<T>();
+            agg = lf(agg, v[k]);
+        }
+        const Pair<T> ex = lblock_excl<T, false>(agg, s_w);
+        if (tid == kLThreads - 1) s_tot = lf(ex, agg);
+        Pair<T> run = lf(carry, ex);
+#pragma unroll
+        for (int k = 0; k < kRowItems; ++k) {
+            const int idx = tid * kRowItems + k;
+            if (idx < len) {
+                s_seg[idx] = run;
+                run = lf(run, v[k]);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < len; e += kLThreads) L[j * nc + s0 + e] = s_seg[e];
+        carry = lf(carry, s_tot);
+        __syncthreads();
+    }
+    if (tid == 0) hist[j] = carry;
+    // reverse: R = the entries after, from the last segment down
+    Pair<T> rcarry = lf_id<T>();
+    for (int64_t s0 = (nc - 1) / kRowSeg * kRowSeg; s0 >= 0; s0 -= kRowSeg) {
+        const int len = (int)((nc - s0) < kRowSeg ? (nc - s0) : kRowSeg);
+        for (int e = tid; e < len; e += kLThreads) s_seg[e] = row[s0 + e];
+        __syncthreads();
+        Pair<T> v[kRowItems], agg = lf_id<T>();
+#pragma unroll
+        for (int k = 0; k < kRowItems; ++k) {
+            const int idx = tid * kRowItems + k;
+            v[k] = idx < len ? s_seg[idx] : lf_id<T>();
+            agg = lf(agg, v[k]);
+        }
+        const Pair<T> rex = lblock_excl<T, true>(agg, s_w);  // the later threads' entries
+        if (tid == 0) s_tot = lf(agg, rex);
+        Pair<T> rrun = lf(rex, rcarry);
+#pragma unroll
+        for (int k = kRowItems - 1; k >= 0; --k) {
+            const int idx = tid * kRowItems + k;
+            if (idx < len) {
+                s_seg[idx] = rrun;
+                rrun = lf(v[k], rrun);
+            }
+        }
+        __syncthreads();
+        for (int e = tid; e < len; e += kLThreads) R[j * nc + s0 + e] = s_seg[e];
+        rcarry = lf(s_tot, rcarry);
+        __syncthreads();
+    }
+    if (tid == 0) A[j] = rcarry;  // P[j][0] . R[j][0]: the bin's whole fold
+}
+
+// ------------------------------------------------------------------- vjp --
+template <typename T>
+__global__ void __launch_bounds__(kLThreads, 2)
+k_linh_vjp(const int32_t *__restrict__ keys, const Pair<T> *__restrict__ vals, const int64_t n, const int m,
+           const int64_t nc, const Pair<T> *__restrict__ L, const Pair<T> *__restrict__ R,
+           const Pair<T> *__restrict__ hb, Pair<T> *__restrict__ vbar, const int accumulate) {
+    using C = LChunk<T>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Pair<T> *s_tab = reinterpret_cast<Pair<T> *>(smem_raw);  // [kLWarps][m]: folds, then (before . g, after.c)
+    Pair<T> *s_g = s_tab + (size_t)kLWarps * m;              // [m] histbar
+    T *s_q = reinterpret_cast<T *>(s_g + m);                  // [kLWarps][m] products of c (backward walk)
+    uint8_t *s_tag = reinterpret_cast<uint8_t *>(s_q + (size_t)kLWarps * m);  // [kLWarps][m]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t c = blockIdx.x;
+    const int64_t base = c * C::kSize + (int64_t)warp * C::kRun;
+    Pair<T> *tab = s_tab + (size_t)warp * m;
+    T *qt = s_q + (size_t)warp * m;
+    uint8_t *tag = s_tag + (size_t)warp * m;
+    int32_t k[C::kRounds];
+    Pair<T> v[C::kRounds];
+    load_run<T, C::kRounds>(keys, vals, base, n, m, k, v);
+    for (int j = lane; j < m; j += kWarp) {
+        tab[j] = lf_id<T>();
+        qt[j] = T(1);
+    }
+    for (int j = tid; j < m; j += kLThreads) s_g[j] = hb[j];
+    __syncwarp();
+    // forward walk: p_i = the run's fold of i's bin before i
+    Pair<T> p[C::kRounds];
+#pragma unroll
+    for (int r = 0; r < C::kRounds; ++r) {
+        const int32_t key = k[r];
+        const Pair<T> x = v[r];
+        Pair<T> pr = lf_id<T>();
+        ordered_round<false>(key, in_range(key, m), tag, [&] {
+            pr = tab[key];
+            tab[key] = lf(pr, x);
+        });
+        p[r] = pr;
+    }
+    // backward walk: s_i = product of the c's of i's bin after i in the run
+    T sv[C::kRounds];
+#pragma unroll
+    for (int r = C::kRounds - 1; r >= 0; --r) {
+        const int32_t key = k[r];
+        const T xc = v[r].c;
+        T sr = T(1);
+        ordered_round<true>(key, in_range(key, m), tag, [&] {
+            sr = qt[key];
+            qt[key] = xc * sr;
+        });
+        sv[r] = sr;
+    }
+    __syncthreads();
+    // per bin and warp run: u = <L . earlier runs, g> and the product of the
+    // c's after the run (later runs, then R)
+    for (int j = tid; j < m; j += kLThreads) {
+        const Pair<T> g = s_g[j];
+        Pair<T> before = L[(int64_t)j * nc + c];
+        T fc[kLWarps], u[kLWarps];
+#pragma unroll
+        for (int w = 0; w < kLWarps; ++w) {
+            const Pair<T> f = s_tab[(size_t)w * m + j];
+            u[w] = g.b * before.b + g.c * before.c;
+            fc[w] = f.c;
+            before = lf(before, f);
+        }
+        T after = R[(int64_t)j * nc + c].c;
+#pragma unroll
+        for (int w = kLWarps - 1; w >= 0; --w) {
+            s_tab[(size_t)w * m + j] = Pair<T>{u[w], after};
+            after = fc[w] * after;
+        }
+    }
+    __syncthreads();
+    // vbar_i = (rc g.b, rc <l_i, g>) with l_i = before . p_i, rc = s_i * after
+#pragma unroll
+    for (int r = 0; r < C::kRounds; ++r) {
+        const int64_t i = base + r * kWarp + lane;
+        if (i >= n) continue;
+        Pair<T> out{T(0), T(0)};
+        if (in_range(k[r], m)) {
+            const Pair<T> ua = tab[k[r]];
+            const Pair<T> g = s_g[k[r]];
+            const T rc = sv[r] * ua.c;
+            out = Pair<T>{rc * g.b, rc * (g.b * p[r].b + p[r].c * ua.b)};
+        }
+        if (accumulate) {
+            const Pair<T> o = vbar[i];
+            out = Pair<T>{o.b + out.b, o.c + out.c};
+        }
+        vbar[i] = out;
+    }
+}
 
 // hist0bar[j] (+)= d(hist0 . A)/d hist0 ^T histbar[j] = A.c * histbar[j]
 template <typename T>
@@ -420,7 +361,7 @@ template <typename T> static int64_t num_chunks(int64_t n) {
 }
 
 struct LinLayout {
-    size_t P, fwdreg, revreg, ws_bytes;  // workspace
+    size_t P, ws_bytes;                  // workspace
     size_t L, R, A, saved_bytes;         // residuals
 };
 
@@ -428,15 +369,8 @@ template <typename T> static LinLayout lin_layout(int64_t n, int64_t m) {
     LinLayout o;
     const int64_t nc = num_chunks<T>(n);
     const size_t cells = (size_t)m * (size_t)nc * sizeof(Pair<T>);
-    constexpr int I = ColItems<T>::v;
-    size_t w = kWsHeader;
-    o.P = w;
-    w = align_up(w + cells, 256);
-    o.fwdreg = w;
-    w = align_up(w + ScanShape<ColFwd<T, I>, I>::region((int64_t)m * nc), 256);
-    o.revreg = w;
-    w = align_up(w + ScanShape<ColRev<T, I>, I>::region((int64_t)m * nc), 256);
-    o.ws_bytes = w;
+    o.P = kWsHeader;
+    o.ws_bytes = align_up(kWsHeader + cells, 256);
     o.L = 0;
     o.R = align_up(cells, 256);
     o.A = 2 * align_up(cells, 256);
@@ -455,13 +389,9 @@ size_t linh_saved_bytes(adc_dtype dt, int64_t n, int64_t m) {
     return dt == ADC_F64 ? lin_layout<double>(n, m).saved_bytes : lin_layout<float>(n, m).saved_bytes;
 }
 
-template <typename T, bool VJP> static size_t chunk_smem(int m) {
-    using C = LChunk<T>;
-    const size_t a = (size_t)kLWarps * m * 4;
-    const size_t b = VJP ? (size_t)C::kSize * sizeof(Pair<T>) : (size_t)m * sizeof(Pair<T>);
-    size_t s = al16(a > b ? a : b) + (size_t)C::kPad * sizeof(Pair<T>) + al16((size_t)C::kPad * 4);
-    if (VJP) s += (size_t)C::kPad * sizeof(Pair<T>) + (size_t)3 * m * sizeof(Pair<T>);
-    return s;
+template <typename T> static size_t fold_smem(int64_t m) { return (size_t)kLWarps * m * (sizeof(Pair<T>) + 1); }
+template <typename T> static size_t vjp_smem(int64_t m) {
+    return (size_t)(kLWarps + 1) * m * sizeof(Pair<T>) + (size_t)kLWarps * m * (sizeof(T) + 1);
 }
 
 template <typename T>
@@ -469,26 +399,16 @@ static adc_status linh_fwd_t(int64_t n, int64_t m, const int32_t *keys, const Pa
                              Pair<T> *hist, void *saved, void *ws, cudaStream_t s) {
     const LinLayout Lo = lin_layout<T>(n, m);
     const int64_t nc = num_chunks<T>(n);
-    char *w = static_cast<char *>(ws);
     char *sv = static_cast<char *>(saved);
-    Pair<T> *P = reinterpret_cast<Pair<T> *>(w + Lo.P);
-    Pair<T> *L = reinterpret_cast<Pair<T> *>(sv + Lo.L);
-    Pair<T> *R = reinterpret_cast<Pair<T> *>(sv + Lo.R);
-    Pair<T> *A = reinterpret_cast<Pair<T> *>(sv + Lo.A);
-    const size_t smem = chunk_smem<T, false>((int)m);
-    if (cudaFuncSetAttribute(k_linh_chunk<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-        cudaSuccess)
+    Pair<T> *P = reinterpret_cast<Pair<T> *>(static_cast<char *>(ws) + Lo.P);
+    const size_t smem = fold_smem<T>(m);
+    if (cudaFuncSetAttribute(k_linh_fold<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return ADC_ERR_CUDA;
-    k_linh_chunk<T, false><<<(unsigned)nc, kLThreads, smem, s>>>(keys, vals, n, (int)m, nc, P, nullptr, nullptr,
-                                                                 nullptr, nullptr, 0);
-    adc_status st = check_launch();
-    if (st != ADC_OK) return st;
-    constexpr int I = ColItems<T>::v;
-    const int64_t N = m * nc;
-    ColFwd<T, I> fw{P, h0, L, hist, nc};
-    if ((st = run_scan<ColFwd<T, I>, I, false>(fw, N, ws, 24, w + Lo.fwdreg, s)) != ADC_OK) return st;
-    ColRev<T, I> rv{P, R, A, nc};
-    return run_scan<ColRev<T, I>, I, true>(rv, N, ws, 25, w + Lo.revreg, s);
+    k_linh_fold<T><<<(unsigned)nc, kLThreads, smem, s>>>(keys, vals, n, (int)m, nc, P);
+    k_linh_rows<T><<<(unsigned)m, kLThreads, 0, s>>>(P, h0, nc, reinterpret_cast<Pair<T> *>(sv + Lo.L),
+                                                     reinterpret_cast<Pair<T> *>(sv + Lo.R), hist,
+                                                     reinterpret_cast<Pair<T> *>(sv + Lo.A));
+    return check_launch();
 }
 
 template <typename T>
@@ -501,12 +421,10 @@ static adc_status linh_vjp_t(int64_t n, int64_t m, const int32_t *keys, const Pa
     const Pair<T> *R = reinterpret_cast<const Pair<T> *>(sv + Lo.R);
     const Pair<T> *A = reinterpret_cast<const Pair<T> *>(sv + Lo.A);
     if (n > 0) {
-        const size_t smem = chunk_smem<T, true>((int)m);
-        if (cudaFuncSetAttribute(k_linh_chunk<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-            cudaSuccess)
+        const size_t smem = vjp_smem<T>(m);
+        if (cudaFuncSetAttribute(k_linh_vjp<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
             return ADC_ERR_CUDA;
-        k_linh_chunk<T, true><<<(unsigned)nc, kLThreads, smem, s>>>(keys, vals, n, (int)m, nc, nullptr, L, R, hb, vb,
-                                                                    acc);
+        k_linh_vjp<T><<<(unsigned)nc, kLThreads, smem, s>>>(keys, vals, n, (int)m, nc, L, R, hb, vb, acc);
     }
     if (h0b) {
         const int64_t g = (m + 255) / 256;
