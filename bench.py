@@ -718,7 +718,8 @@ def run_kernels(args):
         xb = torch.empty_like(x)
         vb_bytes = (2 if op == "add" else 4) * n * es
         variants = ([(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] +
-                    [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] + [(1, 0, "per-tile")])
+                    [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] + [(1, 0, "per-tile"),
+                                                                                         (4, 0, "tma")])
         for eng, rt, label in variants:
             adcomb.debug_set_scan_engine(eng)
             adcomb.debug_set_scan_range_tiles(rt)
@@ -738,9 +739,13 @@ def run_kernels(args):
         y = adcomb.scan_fwd(op, x, ws=ws)
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
-        row(f"scan {op} fwd float32", n, 8 * n, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
-        # the vjp reads y and ybar (the selections come from y), writes xbar
-        row(f"scan {op} vjp float32", n, 12 * n, timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        for eng, label in [(0, "auto"), (4, "tma")]:
+            adcomb.debug_set_scan_engine(eng)
+            row(f"scan {op} fwd float32 [{label}]", n, 8 * n, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
+            # the vjp reads y and ybar (the selections come from y), writes xbar
+            row(f"scan {op} vjp float32 [{label}]", n, 12 * n,
+                timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
+        adcomb.debug_set_scan_engine(0)
         del x, y, yb, xb
     # vectorised operators (Irwim / Iswim): the paper's [n][d] shapes, d = 16 (reduce, scan), 10 (hist)
     for fam, op, n, d in [("vscan", "add", 10_000_000, 16), ("vscan", "mul", 10_000_000, 16),

@@ -412,8 +412,9 @@ void adc_debug_set_stall_tile(int64_t tile);
  * Test hook: scan engine selection -- 0 automatic (range-partitioned for large
  * n, per-tile look-back otherwise), 1 per-tile look-back only, 2 range-
  * partitioned wherever it applies, 3 range-partitioned with the range staged
- * in shared memory by bulk (TMA) copies.  In the fault-injection hook above,
- * the "tile" of the range engines is a range.
+ * in shared memory by bulk (TMA) copies, 4 per-tile look-back with each
+ * block's tile staged in shared memory by bulk copies.  In the fault-injection
+ * hook above, the "tile" of the range engines is a range.
  */
 void adc_debug_set_scan_engine(int engine);
 

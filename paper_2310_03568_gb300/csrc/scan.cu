@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "internal.h"
 #include "scan_engine.cuh"
+#include "scan_tma.cuh"
 #include "scan_staged.cuh"
 #include "tile_io.cuh"
 
@@ -656,11 +657,11 @@ template <typename T> struct Items {
     static constexpr int vmatq = 1;
 };
 
-// Staged (TMA) engine: forced by the test hook (3), chosen automatically for
-// the large, single-array scans where it measured faster.
+// Engines fed by bulk (TMA) copies into shared memory: the range-staged one
+// (test hook 3) and the per-tile one (test hook 4).
 static bool use_staged(int64_t n, int64_t regular_tile) {
     if (n <= 0) return false;
-    if (g_scan_engine == 3) return true;
+    if (g_scan_engine == 3 || g_scan_engine == 4) return true;
     (void)regular_tile;
     return false;
 }
@@ -746,12 +747,25 @@ static adc_status launch(const Op &o, int64_t n, void *ws, cudaStream_t s) {
 }
 template <class Op, int ITEMS, bool REVERSE>
 static adc_status launch_staged(const Op &o, int64_t n, void *ws, cudaStream_t s) {
+    if (g_scan_engine == 4) return run_scan_tma<Op, ITEMS, REVERSE>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
     return run_scan_staged<Op, ITEMS, REVERSE>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
 }
 
 template <typename T>
 static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
     using I = Items<T>;
+    if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && g_scan_engine == 4 && n > 0) {
+        if (op == ADC_OP_MAX) {
+            FwdSel<T, I::s_scalar, true> o;
+            o.x = static_cast<const T *>(x);
+            o.y = static_cast<T *>(y);
+            return launch_staged<decltype(o), I::s_scalar, false>(o, n, ws, s);
+        }
+        FwdSel<T, I::s_scalar, false> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch_staged<decltype(o), I::s_scalar, false>(o, n, ws, s);
+    }
     if (op == ADC_OP_MIN || op == ADC_OP_MAX) {
         if (op == ADC_OP_MAX) {
             FwdSel<T, I::scalar, true> o;
@@ -853,6 +867,16 @@ template <typename T>
 static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y, const void *ybar, void *xbar,
                              int acc, void *ws, cudaStream_t s) {
     using I = Items<T>;
+    if ((op == ADC_OP_MIN || op == ADC_OP_MAX) && g_scan_engine == 4 && n > 0) {
+        if (op == ADC_OP_MAX) {
+            VjpSel<T, I::s_scalar, true> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                           static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+            return launch_staged<decltype(o), I::s_scalar, true>(o, n, ws, s);
+        }
+        VjpSel<T, I::s_scalar, false> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                        static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return launch_staged<decltype(o), I::s_scalar, true>(o, n, ws, s);
+    }
     if (op == ADC_OP_MIN || op == ADC_OP_MAX) {
         if (op == ADC_OP_MAX) {
             VjpSel<T, I::vscalar, true> o{static_cast<const T *>(x), static_cast<const T *>(y),

@@ -27,7 +27,7 @@ def lib():
     adcomb.set_spin_limit(0)
 
 
-@pytest.mark.parametrize("engine", [1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.mark.parametrize("engine", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
 @pytest.mark.parametrize("op,stall", [("add", 3), ("lin", 0), ("mm2", 17)])
 def test_stalled_tile_times_out_and_context_survives(op, stall, engine):
     g = np.random.default_rng(8)
@@ -38,7 +38,7 @@ def test_stalled_tile_times_out_and_context_survives(op, stall, engine):
     try:
         adcomb.debug_set_scan_engine(engine)
         adcomb.set_spin_limit(2000)          # ~0.1-1 ms per wait
-        adcomb.debug_set_stall_tile(stall)   # a tile (per-tile engine) or a range (range engine)
+        adcomb.debug_set_stall_tile(stall)   # a tile (per-tile engines) or a range (range engines)
         adcomb.scan_fwd(op, xd, ws=ws)       # queues fine: the failure is on the device
         assert adcomb.check_device_error(ws) == 5  # ADC_ERR_TIMEOUT
     finally:

@@ -73,11 +73,12 @@ def lib():
     adcomb.debug_set_scan_range_tiles(0)
 
 
-@pytest.fixture(params=[1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.fixture(params=[1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
 def engine(request):
-    """All scan engines: per-tile look-back, range-partitioned, and
+    """All scan engines: per-tile look-back, range-partitioned,
     range-partitioned with TMA staging in shared memory (forced even for small
-    n, where a range may be a single ragged tile)."""
+    n, where a range may be a single ragged tile), and one tile per block
+    staged in shared memory by TMA."""
     adcomb.debug_set_scan_engine(request.param)
     yield request.param
     adcomb.debug_set_scan_engine(0)
@@ -100,7 +101,7 @@ def test_scan_accumulate(op, engine):
     check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)
 
 
-@pytest.mark.parametrize("engine_id", [0, 3], ids=["auto", "staged"])
+@pytest.mark.parametrize("engine_id", [0, 3, 4], ids=["auto", "staged", "tma"])
 @pytest.mark.parametrize("range_tiles", [0, 3, 16])
 @pytest.mark.parametrize("op", ["add", "lin", "mm2", "sop"])
 def test_scan_ranges_engine_many_tiles(op, range_tiles, engine_id):
@@ -192,7 +193,7 @@ def test_mmq_scan(op, dt, engine_id):
         adcomb.debug_set_scan_engine(0)
 
 
-@pytest.mark.parametrize("engine_id", [1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.mark.parametrize("engine_id", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_minmax_scan(op, dt, engine_id):
@@ -220,7 +221,7 @@ def test_minmax_scan(op, dt, engine_id):
         adcomb.debug_set_scan_engine(0)
 
 
-@pytest.mark.parametrize("engine_id", [1, 2, 3], ids=["per-tile", "ranges", "staged"])
+@pytest.mark.parametrize("engine_id", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_minmax_scan_nan_and_integer_adjoints(op, engine_id):
     """NaN never wins a comparison, so a NaN x_i (i > 0) is never selected and
