@@ -84,6 +84,8 @@ def parse():
     p.add_argument("--only", default=None,
                    help="with --kernels: run only the families whose label contains this text, "
                         "e.g. 'scan add float32', 'reduce mul', 'hist add m=1000'")
+    p.add_argument("--prefetch", action="store_true",
+                   help="with --kernels: time the range-partitioned scans with L2 prefetch of each range")
     p.add_argument("--range-tiles", default="0",
                    help="with --kernels: comma list of tiles per range for the range-partitioned scan (0 = default)")
     return p.parse_args()
@@ -719,7 +721,11 @@ def run_kernels(args):
         vb_bytes = (2 if op == "add" else 4) * n * es
         variants = ([(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] +
                     [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] + [(1, 0, "per-tile"),
-                                                                                         (4, 0, "tma")])
+                                                                                         (4, 0, "tma"),
+                                                                                         (5, 0, "ranges16")])
+        if args.prefetch:
+            variants = [(2, rt, f"ranges rt={rt} prefetch") for rt in rts]
+        adcomb.debug_set_scan_prefetch(1 if args.prefetch else 0)
         for eng, rt, label in variants:
             adcomb.debug_set_scan_engine(eng)
             adcomb.debug_set_scan_range_tiles(rt)
@@ -729,6 +735,7 @@ def run_kernels(args):
                 timeit(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws)))
         adcomb.debug_set_scan_engine(0)
         adcomb.debug_set_scan_range_tiles(0)
+        adcomb.debug_set_scan_prefetch(0)
         del x, y, yb, xb
     # min / max scans (the general arity-1 rule), values on 1024 levels
     for op in ("min", "max"):
@@ -739,7 +746,7 @@ def run_kernels(args):
         y = adcomb.scan_fwd(op, x, ws=ws)
         yb = torch.randn_like(x)
         xb = torch.empty_like(x)
-        for eng, label in [(0, "auto"), (4, "tma")]:
+        for eng, label in [(0, "auto"), (4, "tma"), (5, "ranges16")]:
             adcomb.debug_set_scan_engine(eng)
             row(f"scan {op} fwd float32 [{label}]", n, 8 * n, timeit(lambda: adcomb.scan_fwd(op, x, y, ws=ws)))
             # the vjp reads y and ybar (the selections come from y), writes xbar
@@ -866,7 +873,7 @@ def run_kernels(args):
                         row(f"bench {op} m={m} fwd [{label}]", NB, 8 * NB,
                             timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
                     adcomb.debug_force_hist_strategy(-1)
-                forms = [(1, "gather"), (2, "scatter")] if op != "mul" else [(0, "")]
+                forms = [(1, "gather"), (2, "scatter"), (3, "bitmap")] if op != "mul" else [(0, "")]
                 for f, label in forms:
                     adcomb.debug_set_sel_vjp_form(f)
                     row(f"bench {op} m={m} vjp {label}".strip(), NB, (12 if op == "mul" else 4) * NB,

@@ -427,6 +427,13 @@ void adc_debug_set_scan_engine(int engine);
 void adc_debug_set_scan_range_tiles(int tiles);
 
 /*
+ * Tuning hook: 1 makes every block of the range-partitioned scan engine
+ * prefetch its range's input into L2 (bulk prefetches) when it starts; 0 (the
+ * default) does not.  Results do not depend on it.
+ */
+void adc_debug_set_scan_prefetch(int on);
+
+/*
  * Test hook: force the forward histogram strategy of ADD/MUL/MIN/MAX
  * (0: per-warp shared-memory copies, 1: one shared-memory copy per block,
  * 2: global atomics, 3: per-thread shared-memory tables, 4: partition by bin
@@ -443,7 +450,9 @@ void adc_debug_force_hist_strategy(int strategy);
  * Tuning hook: form of the min/max reduce-by-index vjp -- 0 automatic (a
  * gather pass over the keys when bins are sparse, 8m > n; else a zero-fill
  * plus a scatter of the m adjoints), 1 always the gather, 2 always the
- * zero-fill + scatter.  Results are identical.
+ * zero-fill + scatter, 3 a bitmap of the selected elements (one bit each,
+ * set from is[]) and one streaming pass that gathers only for set bits.
+ * Results are identical.
  */
 void adc_debug_set_sel_vjp_form(int form);
 

@@ -79,6 +79,7 @@ def lib():
                 "adc_debug_set_sel_vjp_form": ([i32], None),
                 "adc_debug_set_scan_engine": ([i32], None),
                 "adc_debug_set_scan_range_tiles": ([i32], None),
+                "adc_debug_set_scan_prefetch": ([i32], None),
                 "adc_status_string": ([i32], ctypes.c_char_p),
                 "adc_version": ([], ctypes.c_char_p),
             }
@@ -282,6 +283,11 @@ def debug_set_scan_engine(engine):
 def debug_set_scan_range_tiles(tiles):
     """Tiles per range of the range-partitioned scan engine; 0 lets the library choose."""
     lib().adc_debug_set_scan_range_tiles(int(tiles))
+
+
+def debug_set_scan_prefetch(on):
+    """1: each range of the range-partitioned scan engine is prefetched into L2 when its block starts."""
+    lib().adc_debug_set_scan_prefetch(int(bool(on)))
 
 
 # ------------------------------------------------- vectorised operators ----

@@ -13,6 +13,7 @@ static long long g_spin_limit = 1ll << 22;
 static long long g_stall_tile = -1;
 int g_scan_engine = 0;
 int g_scan_range_tiles = 0;
+int g_scan_prefetch = 0;
 
 long long spin_limit() { return g_spin_limit; }
 
@@ -22,6 +23,7 @@ DevCtl make_ctl(void *ws, int slot) {
     c.counter = counter_slot(ws, slot);
     c.spin_limit = g_spin_limit;
     c.stall_tile = g_stall_tile;
+    c.prefetch = g_scan_prefetch;
     return c;
 }
 
@@ -413,7 +415,8 @@ void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1
 
 void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
 
-void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 4) ? engine : 0; }
+void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 5) ? engine : 0; }
 void adc_debug_set_scan_range_tiles(int tiles) { g_scan_range_tiles = tiles > 0 ? tiles : 0; }
+void adc_debug_set_scan_prefetch(int on) { g_scan_prefetch = on ? 1 : 0; }
 
 }  // extern "C"

@@ -23,6 +23,7 @@ struct DevCtl {
     unsigned *counter;      // dynamic tile counter
     long long spin_limit;   // bound on polling iterations
     long long stall_tile;   // fault-injection: tile that never publishes (-1: off)
+    int prefetch;           // range engine: prefetch each range into L2
 };
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {

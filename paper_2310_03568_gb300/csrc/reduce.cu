@@ -88,6 +88,10 @@ template <typename T, int Q> struct GMMQ {
 
 // ------------------------------------------------------- simple reduction --
 // Workspace: [header][ticket u32 @ +8 in header][partials G states]
+// The operators here (+, the lifted * and min/max, sumOfProd) are
+// commutative, so a thread may take any of the tile's elements: it takes
+// 16-byte words t, t + kRedThreads, ..., so that a warp's load covers 512
+// contiguous bytes.  The lifted operators get each element's own index.
 template <class Op, typename T, int ITEMS>
 __global__ void __launch_bounds__(kRedThreads)
 k_reduce_simple(const Op op, const T *__restrict__ x, const int64_t n, const int64_t tiles_per_block,
@@ -95,18 +99,25 @@ k_reduce_simple(const Op op, const T *__restrict__ x, const int64_t n, const int
                 typename Op::State *__restrict__ result) {
     using S = typename Op::State;
     constexpr int TILE = kRedThreads * ITEMS;
+    constexpr int WE = 16 / sizeof(T) < ITEMS ? 16 / sizeof(T) : ITEMS;  // elements per word
+    constexpr int NWD = ITEMS / WE;                                       // words per thread and tile
     __shared__ S tmp[kRedThreads / kWarp];
     __shared__ bool last;
     const int64_t t0 = (int64_t)blockIdx.x * tiles_per_block;
     S acc = op.identity();
     for (int64_t t = t0; t < t0 + tiles_per_block; ++t) {
-        const int64_t c0 = t * TILE + (int64_t)threadIdx.x * ITEMS;
-        if (c0 >= n) break;
-        T v[ITEMS];
-        load_chunk(x, c0, n, v, T{});
+        if (t * TILE >= n) break;
+        T v[NWD][WE];
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k)
-            if (c0 + k < n) acc = op.combine(acc, op.lift(v[k], c0 + k));
+        for (int j = 0; j < NWD; ++j)
+            load_chunk(x, t * TILE + ((int64_t)j * kRedThreads + threadIdx.x) * WE, n, v[j], T{});
+#pragma unroll
+        for (int j = 0; j < NWD; ++j) {
+            const int64_t c0 = t * TILE + ((int64_t)j * kRedThreads + threadIdx.x) * WE;
+#pragma unroll
+            for (int k = 0; k < WE; ++k)
+                if (c0 + k < n) acc = op.combine(acc, op.lift(v[j][k], c0 + k));
+        }
     }
     S total;
     block_exclusive_fwd<Op, kRedThreads>(op, acc, tmp, &total);

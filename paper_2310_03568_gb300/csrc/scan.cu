@@ -695,7 +695,9 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
     case ADC_OP_MAX:
         a = ScanShape<FwdSel<T, I::scalar, false>, I::scalar>::region(n);
         b = ScanShape<VjpSel<T, I::vscalar, false>, I::vscalar>::region(n);
-        return kWsHeader + (a > b ? a : b);
+        c = ScanShape<FwdSel<T, I::s_scalar, false>, I::s_scalar>::region(n);
+        d = ScanShape<VjpSel<T, I::s_scalar, false>, I::s_scalar>::region(n);
+        return kWsHeader + max4(a, b, c, d);
     case ADC_OP_SOP:
         a = ScanShape<FwdSop<T, I::pair>, I::pair>::region(n);
         b = ScanShape<VjpSop<T, I::vpair>, I::vpair>::region(n);
@@ -751,6 +753,102 @@ static adc_status launch_staged(const Op &o, int64_t n, void *ws, cudaStream_t s
     return run_scan_staged<Op, ITEMS, REVERSE>(o, n, ws, 0, static_cast<char *>(ws) + kWsHeader, s);
 }
 
+// The engines of run_scan with 16 bytes of each array per thread per tile
+// (test hook 5): consecutive threads hold consecutive 16-byte words, so a
+// warp's load or store covers 512 contiguous bytes.
+template <typename T>
+static adc_status scan_fwd_items16(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
+    using I = Items<T>;
+    switch (op) {
+    case ADC_OP_ADD: {
+        FwdAdd<T, I::s_scalar> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::s_scalar, false>(o, n, ws, s);
+    }
+    case ADC_OP_MUL: {
+        FwdMul<T, I::s_scalar> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::s_scalar, false>(o, n, ws, s);
+    }
+    case ADC_OP_MIN: {
+        FwdSel<T, I::s_scalar, false> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::s_scalar, false>(o, n, ws, s);
+    }
+    case ADC_OP_MAX: {
+        FwdSel<T, I::s_scalar, true> o;
+        o.x = static_cast<const T *>(x);
+        o.y = static_cast<T *>(y);
+        return launch<decltype(o), I::s_scalar, false>(o, n, ws, s);
+    }
+    case ADC_OP_LIN: {
+        FwdLin<T, I::s_pair> o;
+        o.x = static_cast<const Pair<T> *>(x);
+        o.y = static_cast<Pair<T> *>(y);
+        return launch<decltype(o), I::s_pair, false>(o, n, ws, s);
+    }
+    case ADC_OP_SOP: {
+        FwdSop<T, I::s_pair> o;
+        o.x = static_cast<const Pair<T> *>(x);
+        o.y = static_cast<Pair<T> *>(y);
+        return launch<decltype(o), I::s_pair, false>(o, n, ws, s);
+    }
+    case ADC_OP_MM2: {
+        FwdMM2<T, I::s_mat> o;
+        o.x = static_cast<const Mat2<T> *>(x);
+        o.y = static_cast<Mat2<T> *>(y);
+        return launch<decltype(o), I::s_mat, false>(o, n, ws, s);
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
+template <typename T>
+static adc_status scan_vjp_items16(adc_op op, int64_t n, const void *x, const void *y, const void *ybar, void *xbar,
+                                   int acc, void *ws, cudaStream_t s) {
+    using I = Items<T>;
+    switch (op) {
+    case ADC_OP_ADD: {
+        VjpAdd<T, I::s_scalar> o{static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return launch<decltype(o), I::s_scalar, true>(o, n, ws, s);
+    }
+    case ADC_OP_MUL: {
+        VjpMul<T, I::s_scalar> o{static_cast<const T *>(x), static_cast<const T *>(y), static_cast<const T *>(ybar),
+                                 static_cast<T *>(xbar), acc};
+        return launch<decltype(o), I::s_scalar, true>(o, n, ws, s);
+    }
+    case ADC_OP_MIN: {
+        VjpSel<T, I::s_scalar, false> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                        static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return launch<decltype(o), I::s_scalar, true>(o, n, ws, s);
+    }
+    case ADC_OP_MAX: {
+        VjpSel<T, I::s_scalar, true> o{static_cast<const T *>(x), static_cast<const T *>(y),
+                                       static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
+        return launch<decltype(o), I::s_scalar, true>(o, n, ws, s);
+    }
+    case ADC_OP_LIN: {
+        VjpLin<T, I::s_pair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
+                               static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
+        return launch<decltype(o), I::s_pair, true>(o, n, ws, s);
+    }
+    case ADC_OP_SOP: {
+        VjpSop<T, I::s_pair> o{static_cast<const Pair<T> *>(x), static_cast<const Pair<T> *>(y),
+                               static_cast<const Pair<T> *>(ybar), static_cast<Pair<T> *>(xbar), acc};
+        return launch<decltype(o), I::s_pair, true>(o, n, ws, s);
+    }
+    case ADC_OP_MM2: {
+        VjpMM2<T, I::s_mat> o{static_cast<const Mat2<T> *>(x), static_cast<const Mat2<T> *>(y),
+                              static_cast<const Mat2<T> *>(ybar), static_cast<Mat2<T> *>(xbar), acc};
+        return launch<decltype(o), I::s_mat, true>(o, n, ws, s);
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+
 template <typename T>
 static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
     using I = Items<T>;
@@ -789,6 +887,7 @@ static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void 
         SegFwdMMQ<T, 5, L> o{static_cast<const MatQ<T, 5> *>(x), static_cast<MatQ<T, 5> *>(y), n};
         return launch<decltype(o), 1, false>(o, (n + L - 1) / L, ws, s);
     }
+    if (g_scan_engine == 5 && n > 0) return scan_fwd_items16<T>(op, n, x, y, ws, s);
     if (use_staged(n, 0)) {
         switch (op) {
         case ADC_OP_ADD: {
@@ -901,6 +1000,7 @@ static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y,
                              static_cast<M *>(xbar), acc, n};
         return launch<decltype(o), 1, true>(o, (n + L - 1) / L, ws, s);
     }
+    if (g_scan_engine == 5 && n > 0) return scan_vjp_items16<T>(op, n, x, y, ybar, xbar, acc, ws, s);
     if (use_staged(n, 0)) {
         switch (op) {
         case ADC_OP_ADD: {

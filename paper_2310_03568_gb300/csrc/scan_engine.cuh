@@ -55,6 +55,18 @@ template <class Op> constexpr bool per_tile_only(long) { return false; }
 template <class Op> constexpr auto per_tile_only(int) -> decltype(Op::kPerTileOnly, bool()) {
     return Op::kPerTileOnly;
 }
+// Ops that name their input arrays (kStreams, stream(s), Elem) can have a
+// block's range prefetched into L2 by bulk prefetches.
+template <class Op> constexpr int op_streams(long) { return 0; }
+template <class Op> constexpr auto op_streams(int) -> decltype(Op::kStreams, int()) { return Op::kStreams; }
+
+// L2 prefetch of [p, p + bytes): p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2_bulk(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+// Test and tuning hook: the range engine prefetches each block's range into
+// L2 when the block starts (0 off, 1 on).
+extern int g_scan_prefetch;
 
 // ---------------------------------------------------- tagged tile status --
 // A published tile state S is stored as K = sizeof(S)/4 64-bit words, each
@@ -294,7 +306,7 @@ __device__ __forceinline__ S block_scan_excl(const Op &op, const S &a, S *s_warp
 // Traffic: the input twice (less what L2 keeps), the output once.  Same Op
 // interface as k_scan.
 template <typename S> constexpr int range_max_tiles() {
-    return (int)((32 * 1024) / (8 * sizeof(S))) < 128 ? (int)((32 * 1024) / (8 * sizeof(S))) : 128;
+    return (int)((32 * 1024) / (8 * sizeof(S))) < 256 ? (int)((32 * 1024) / (8 * sizeof(S))) : 256;
 }
 
 template <class Op, int THREADS, int ITEMS, bool REVERSE>
@@ -331,6 +343,21 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
         for (int k = 0; k < ITEMS; ++k) a = op.combine(a, st[REVERSE ? ITEMS - 1 - k : k]);
         return a;
     };
+    if constexpr (op_streams<Op>(0) > 0) {
+        // the range's input into L2 in 64 KB pieces, so that both phases read
+        // it from there (the range is whole tiles: every piece starts on a
+        // 16-byte boundary; a ragged end shorter than 16 bytes is not prefetched)
+        if (ctl.prefetch && tid < op_streams<Op>(0) && cnt > 0) {
+            using E = typename Op::Elem;
+            const int64_t p0 = REVERSE ? (num_tiles - t0 - cnt) : t0;  // first physical tile
+            int64_t lo = p0 * (int64_t)TILE * (int64_t)sizeof(E);
+            int64_t hi = (p0 + cnt) * (int64_t)TILE * (int64_t)sizeof(E);
+            const int64_t nb = n * (int64_t)sizeof(E);
+            if (hi > nb) hi = nb & ~(int64_t)15;
+            const char *base = reinterpret_cast<const char *>(op.stream(tid));
+            for (; lo < hi; lo += 65536) prefetch_l2_bulk(base + lo, (uint32_t)(hi - lo < 65536 ? hi - lo : 65536));
+        }
+    }
 
     // ---- phase A: warp-tile aggregates
     typename Op::Raw raw;
@@ -535,7 +562,7 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     if (rt > 0) R = (T + rt - 1) / rt;
     if (R > T) R = T;
     const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * R &&
-                        (g_scan_engine == 2 || (g_scan_engine == 0 && T >= 4 * G));
+                        (g_scan_engine == 2 || g_scan_engine == 5 || (g_scan_engine == 0 && T >= 4 * G));
     if (ranges) {
         k_scan_ranges<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)R, kScanThreads, 0, s>>>(
             op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),

@@ -27,7 +27,7 @@ def lib():
     adcomb.set_spin_limit(0)
 
 
-@pytest.mark.parametrize("engine", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
+@pytest.mark.parametrize("engine", [1, 2, 3, 4, 5], ids=["per-tile", "ranges", "staged", "tma", "ranges16"])
 @pytest.mark.parametrize("op,stall", [("add", 3), ("lin", 0), ("mm2", 17)])
 def test_stalled_tile_times_out_and_context_survives(op, stall, engine):
     g = np.random.default_rng(8)

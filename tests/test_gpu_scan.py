@@ -73,12 +73,13 @@ def lib():
     adcomb.debug_set_scan_range_tiles(0)
 
 
-@pytest.fixture(params=[1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
+@pytest.fixture(params=[1, 2, 3, 4, 5], ids=["per-tile", "ranges", "staged", "tma", "ranges16"])
 def engine(request):
     """All scan engines: per-tile look-back, range-partitioned,
     range-partitioned with TMA staging in shared memory (forced even for small
-    n, where a range may be a single ragged tile), and one tile per block
-    staged in shared memory by TMA."""
+    n, where a range may be a single ragged tile), one tile per block staged
+    in shared memory by TMA, and the range engine with 16 bytes per thread per
+    tile."""
     adcomb.debug_set_scan_engine(request.param)
     yield request.param
     adcomb.debug_set_scan_engine(0)
@@ -101,7 +102,7 @@ def test_scan_accumulate(op, engine):
     check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)
 
 
-@pytest.mark.parametrize("engine_id", [0, 3, 4], ids=["auto", "staged", "tma"])
+@pytest.mark.parametrize("engine_id", [0, 3, 4, 5], ids=["auto", "staged", "tma", "ranges16"])
 @pytest.mark.parametrize("range_tiles", [0, 3, 16])
 @pytest.mark.parametrize("op", ["add", "lin", "mm2", "sop"])
 def test_scan_ranges_engine_many_tiles(op, range_tiles, engine_id):
@@ -116,6 +117,32 @@ def test_scan_ranges_engine_many_tiles(op, range_tiles, engine_id):
         adcomb.debug_set_scan_range_tiles(range_tiles)
         check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
     finally:
+        adcomb.debug_set_scan_range_tiles(0)
+        adcomb.debug_set_scan_engine(0)
+
+
+@pytest.mark.parametrize("range_tiles", [0, 8])
+@pytest.mark.parametrize("op", ["add", "mul", "lin", "mm2", "min"])
+def test_scan_ranges_with_l2_prefetch(op, range_tiles):
+    """The range engine with every block's range prefetched into L2 (tuning
+    hook): the same results as without."""
+    g = np.random.default_rng(18)
+    n = {"add": 12_000_003, "mul": 12_000_003, "lin": 6_000_001, "mm2": 3_000_001, "min": 12_000_003}[op]
+    x = make_x(g, op, n, np.float32) if op != "min" else ((g.integers(0, 1024, n) - 512) / 64.0).astype(np.float32)
+    try:
+        adcomb.debug_set_scan_engine(2)
+        adcomb.debug_set_scan_range_tiles(range_tiles)
+        adcomb.debug_set_scan_prefetch(1)
+        if op == "min":
+            xd = dev(x)
+            y = adcomb.scan_fwd(op, xd)
+            assert np.array_equal(host(y), oracle.scan_fwd(op, x).astype(np.float32))
+            yb = g.integers(-3, 4, n).astype(np.float32)
+            assert np.array_equal(host(adcomb.scan_vjp(op, xd, y, dev(yb))), oracle.scan_vjp(op, x, yb).astype(np.float32))
+        else:
+            check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32)
+    finally:
+        adcomb.debug_set_scan_prefetch(0)
         adcomb.debug_set_scan_range_tiles(0)
         adcomb.debug_set_scan_engine(0)
 
@@ -193,7 +220,7 @@ def test_mmq_scan(op, dt, engine_id):
         adcomb.debug_set_scan_engine(0)
 
 
-@pytest.mark.parametrize("engine_id", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
+@pytest.mark.parametrize("engine_id", [1, 2, 3, 4, 5], ids=["per-tile", "ranges", "staged", "tma", "ranges16"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_minmax_scan(op, dt, engine_id):
@@ -221,7 +248,7 @@ def test_minmax_scan(op, dt, engine_id):
         adcomb.debug_set_scan_engine(0)
 
 
-@pytest.mark.parametrize("engine_id", [1, 2, 3, 4], ids=["per-tile", "ranges", "staged", "tma"])
+@pytest.mark.parametrize("engine_id", [1, 2, 3, 4, 5], ids=["per-tile", "ranges", "staged", "tma", "ranges16"])
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_minmax_scan_nan_and_integer_adjoints(op, engine_id):
     """NaN never wins a comparison, so a NaN x_i (i > 0) is never selected and
