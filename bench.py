@@ -53,7 +53,8 @@ def launches(phase, op, m, n):
     partitioned by bin range (m >= 2^18), count + count scan + scatter +
     per-bucket tables (which also finalise);
     the * vjp is coefficient tables + gather; the min/max vjp is a zero-fill +
-    scatter, or one gather pass when bins are sparse (8m > n)."""
+    scatter, or, when bins are sparse (8m > n), a bitmap of the selected
+    elements + one streaming pass."""
     if phase == "fwd":
         if m >= (1 << 18):
             return 4
@@ -63,9 +64,7 @@ def launches(phase, op, m, n):
         # min/max whose packed table exceeds a block but whose values fit:
         # value rows + row reduce + index pass + decode
         return 4 if m * 8 > 200 * 1024 and m * 4 <= 200 * 1024 else 3
-    if op == "mul":
-        return 2
-    return 1 if m * 8 > n else 2
+    return 2
 
 
 def parse():

@@ -447,12 +447,12 @@ void adc_debug_set_scan_prefetch(int on);
 void adc_debug_force_hist_strategy(int strategy);
 
 /*
- * Tuning hook: form of the min/max reduce-by-index vjp -- 0 automatic (a
- * gather pass over the keys when bins are sparse, 8m > n; else a zero-fill
- * plus a scatter of the m adjoints), 1 always the gather, 2 always the
- * zero-fill + scatter, 3 a bitmap of the selected elements (one bit each,
- * set from is[]) and one streaming pass that gathers only for set bits.
- * Results are identical.
+ * Tuning hook: form of the min/max reduce-by-index vjp -- 0 automatic (the
+ * bitmap form when bins are sparse, 8m > n; else a zero-fill plus a scatter
+ * of the m adjoints), 1 a gather pass over the keys (is[k_i] == i), 2 the
+ * zero-fill + scatter, 3 a bitmap of the selected elements (one bit each, set
+ * from is[]) and one streaming pass that gathers only for set bits.  Results
+ * are identical.
  */
 void adc_debug_set_sel_vjp_form(int form);
 

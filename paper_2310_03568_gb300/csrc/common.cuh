@@ -60,6 +60,12 @@ __device__ __forceinline__ uint64_t ordered_key(double v) {
     return (u & 0x8000000000000000ull) ? ~u : (u | 0x8000000000000000ull);
 }
 
+// a / b for the zero-count vjps, where a is often an exact zero (a product
+// that underflowed): a zero numerator gives a * b instead, the same signed
+// zero, without the division (measured on the * reduce vjp at n = 1e8 with
+// an underflowed product: 0.225 -> 0.143 ms).
+template <typename T> __device__ __forceinline__ T div_or_zero(T a, T b) { return a == T(0) ? a * b : a / b; }
+
 // ------------------------------------------------------- tuple element types --
 template <typename T> struct Pair { T b, c; };        // linFnComp element x -> b + c*x
 template <typename T> struct Mat2 { T a, b, c, d; };  // [[a, b], [c, d]]

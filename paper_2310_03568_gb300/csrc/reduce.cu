@@ -355,7 +355,7 @@ __global__ void k_vjp_mul(T *__restrict__ xbar, const T *__restrict__ x, const T
     const int64_t nv = (n + V - 1) / V;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     auto grad = [&](T a) -> T {
-        if (n0 == 0) return (p / a) * yb;
+        if (n0 == 0) return div_or_zero(p, a) * yb;
         if (n0 == 1 && a == T(0)) return p * yb;
         return T(0);
     };

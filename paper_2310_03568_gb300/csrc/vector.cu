@@ -300,7 +300,7 @@ k_vred_vjp(const T *__restrict__ x, const T *__restrict__ ybar, const char *__re
     }
     auto grad = [&](T a, int64_t row) -> T {
         if (OPK == 0) return yb;
-        if (OPK == 1) return k == 0 ? (p / a) * yb : ((k == 1 && a == T(0)) ? p * yb : T(0));
+        if (OPK == 1) return k == 0 ? div_or_zero(p, a) * yb : ((k == 1 && a == T(0)) ? p * yb : T(0));
         return row == k ? yb : T(0);
     };
     // eight elements per thread and step, their loads issued first

@@ -346,7 +346,8 @@ def test_hist_unsupported_and_invalid():
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["min", "max"])
 def test_hist_sel_vjp_forms(op, dt):
-    """Both forms of the min/max vjp (gather pass; zero-fill + scatter), forced
+    """Every form of the min/max vjp (gather pass; zero-fill + scatter; bitmap
+    of the selected elements + streaming pass), forced
     on both sides of the automatic threshold, equal the oracle bit-exactly
     (each adjoint is one histbar value or zero; with accumulate, one add)."""
     g = np.random.default_rng(61)
@@ -358,7 +359,7 @@ def test_hist_sel_vjp_forms(op, dt):
             h, saved = adcomb.hist_fwd(op, m, dev(k), dev(v))
             ref, _ = oracle.hist_vjp(op, m, k, v, hb)
             old = synth.normal(g, n, dt)
-            for form in (0, 1, 2):
+            for form in (0, 1, 2, 3):
                 adcomb.debug_set_sel_vjp_form(form)
                 vb, _ = adcomb.hist_vjp(op, m, dev(k), dev(v), None, h, saved, dev(hb))
                 assert np.array_equal(host(vb), ref.astype(dt)), (n, m, form)
