@@ -719,9 +719,9 @@ def run_kernels(args):
         xb = torch.empty_like(x)
         vb_bytes = (2 if op == "add" else 4) * n * es
         variants = ([(2, rt, "ranges" if rt == 0 else f"ranges rt={rt}") for rt in rts] +
-                    [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] + [(1, 0, "per-tile"),
-                                                                                         (4, 0, "tma"),
-                                                                                         (5, 0, "ranges16")])
+                    [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] +
+                    [(5, rt, "ranges16" if rt == 0 else f"ranges16 rt={rt}") for rt in rts] +
+                    [(1, 0, "per-tile"), (4, 0, "tma")])
         if args.prefetch:
             variants = [(2, rt, f"ranges rt={rt} prefetch") for rt in rts]
         adcomb.debug_set_scan_prefetch(1 if args.prefetch else 0)

@@ -305,6 +305,13 @@ __device__ __forceinline__ S block_scan_excl(const Op &op, const S &a, S *s_warp
 // its part of a tile from its prefix, again without block barriers.
 // Traffic: the input twice (less what L2 keeps), the output once.  Same Op
 // interface as k_scan.
+// Tiles whose loads the range engine keeps in flight per thread: about 64
+// bytes of input each (1 for the 64-byte tiles, up to 4 for 16-byte ones).
+template <class Op, int ITEMS> constexpr int range_prefetch() {
+    constexpr int per = (int)sizeof(typename Op::Raw);
+    return per >= 64 ? 1 : (64 / per > 4 ? 4 : (64 / per < 1 ? 1 : 64 / per));
+}
+
 template <typename S> constexpr int range_max_tiles() {
     return (int)((32 * 1024) / (8 * sizeof(S))) < 256 ? (int)((32 * 1024) / (8 * sizeof(S))) : 256;
 }
@@ -359,16 +366,26 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
         }
     }
 
-    // ---- phase A: warp-tile aggregates
-    typename Op::Raw raw;
-    if (cnt > 0) op.fetch(chunk0(t0), n, raw);
-    for (int i = 0; i < cnt; ++i) {
-        S st[ITEMS];
-        typename Op::Aux aux;
-        op.build(chunk0(t0 + i), n, raw, st, aux);
-        if (i + 1 < cnt) op.fetch(chunk0(t0 + i + 1), n, raw);
-        const S winc = warp_inclusive_scan(op, thread_agg(st));
-        if (lane == kWarp - 1) s_wt[i * NW + warp] = winc;
+    // ---- phase A: warp-tile aggregates; the loads of PF tiles in flight
+    // (PF > 1 where a thread's tile is small: about 64 bytes in flight each)
+    constexpr int PF = range_prefetch<Op, ITEMS>();
+    typename Op::Raw raw[PF];
+#pragma unroll
+    for (int q = 0; q < PF; ++q)
+        if (q < cnt) op.fetch(chunk0(t0 + q), n, raw[q]);
+    for (int i0 = 0; i0 < cnt; i0 += PF) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int i = i0 + q;
+            if (i < cnt) {
+                S st[ITEMS];
+                typename Op::Aux aux;
+                op.build(chunk0(t0 + i), n, raw[q], st, aux);
+                if (i + PF < cnt) op.fetch(chunk0(t0 + i + PF), n, raw[q]);
+                const S winc = warp_inclusive_scan(op, thread_agg(st));
+                if (lane == kWarp - 1) s_wt[i * NW + warp] = winc;
+            }
+        }
     }
     __syncthreads();
 
@@ -462,24 +479,33 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
     __syncthreads();
 
     // ---- phase B: rescan, last tile of phase A first; warps independent
-    if (cnt > 0) op.fetch(chunk0(t0 + cnt - 1), n, raw);
-    for (int i = cnt - 1; i >= 0; --i) {
-        S st[ITEMS];
-        typename Op::Aux aux;
-        const int64_t c0 = chunk0(t0 + i);
-        op.build(c0, n, raw, st, aux);
-        if (i > 0) op.fetch(chunk0(t0 + i - 1), n, raw);
-        S ex = shfl_up(warp_inclusive_scan(op, thread_agg(st)), 1);
-        if (lane == 0) ex = op.identity();
-        S run = op.combine(s_wt[i * NW + warp], ex);
 #pragma unroll
-        for (int k = 0; k < ITEMS; ++k) {
-            const int kk = REVERSE ? ITEMS - 1 - k : k;
-            const S exk = run;
-            run = op.combine(run, st[kk]);
-            st[kk] = exclusive_store<Op>(0) ? exk : run;
+    for (int q = 0; q < PF; ++q)
+        if (q < cnt) op.fetch(chunk0(t0 + cnt - 1 - q), n, raw[q]);
+    for (int j0 = 0; j0 < cnt; j0 += PF) {
+#pragma unroll
+        for (int q = 0; q < PF; ++q) {
+            const int j = j0 + q;
+            if (j < cnt) {
+                const int i = cnt - 1 - j;
+                S st[ITEMS];
+                typename Op::Aux aux;
+                const int64_t c0 = chunk0(t0 + i);
+                op.build(c0, n, raw[q], st, aux);
+                if (j + PF < cnt) op.fetch(chunk0(t0 + i - PF), n, raw[q]);
+                S ex = shfl_up(warp_inclusive_scan(op, thread_agg(st)), 1);
+                if (lane == 0) ex = op.identity();
+                S run = op.combine(s_wt[i * NW + warp], ex);
+#pragma unroll
+                for (int k = 0; k < ITEMS; ++k) {
+                    const int kk = REVERSE ? ITEMS - 1 - k : k;
+                    const S exk = run;
+                    run = op.combine(run, st[kk]);
+                    st[kk] = exclusive_store<Op>(0) ? exk : run;
+                }
+                op.store(c0, n, st, aux);
+            }
         }
-        op.store(c0, n, st, aux);
     }
 }
 
