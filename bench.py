@@ -474,7 +474,7 @@ def run_batched(dev, peak, seed=4):
             "speedup_vs_graph": ms_graph / ms_batched, "speedup": ms_pi / ms_batched,
             "batched_values_per_s": total / (ms_batched * 1e-3),
             "algorithmic_bytes": alg, "achieved_gbs": gbs, "frac": gbs / peak,
-            "tuned": {"chunk": tuned["chunk"], "smem_bins": tuned["smem_bins"]},
+            "tuned": {"chunk": tuned["chunk"], "smem_bins": tuned["smem_bins"], "items": tuned["items"]},
             "gradients_bit_identical": same and same_graph,
             "loss_batched": float(p.loss.item()), "loss_per_instance": float(loss_pi.item()),
             "loss_per_instance_graph": float(pig.loss.item())}

@@ -434,6 +434,14 @@ void adc_debug_set_scan_range_tiles(int tiles);
 void adc_debug_set_scan_prefetch(int on);
 
 /*
+ * Tuning hook: elements per thread and step of the batched histogram launch
+ * (1, 4 or 8; anything else selects the default, 4).  A step's key and value
+ * loads are all issued before its atomic updates.  Results do not depend on it
+ * beyond the order of the + atomics.
+ */
+void adc_debug_set_batched_items(int items);
+
+/*
  * Test hook: force the forward histogram strategy of ADD/MUL/MIN/MAX
  * (0: per-warp shared-memory copies, 1: one shared-memory copy per block,
  * 2: global atomics, 3: per-thread shared-memory tables, 4: partition by bin

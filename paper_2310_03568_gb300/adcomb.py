@@ -80,6 +80,7 @@ def lib():
                 "adc_debug_set_scan_engine": ([i32], None),
                 "adc_debug_set_scan_range_tiles": ([i32], None),
                 "adc_debug_set_scan_prefetch": ([i32], None),
+                "adc_debug_set_batched_items": ([i32], None),
                 "adc_status_string": ([i32], ctypes.c_char_p),
                 "adc_version": ([], ctypes.c_char_p),
             }
@@ -283,6 +284,11 @@ def debug_set_scan_engine(engine):
 def debug_set_scan_range_tiles(tiles):
     """Tiles per range of the range-partitioned scan engine; 0 lets the library choose."""
     lib().adc_debug_set_scan_range_tiles(int(tiles))
+
+
+def debug_set_batched_items(items):
+    """Elements per thread and step of the batched histogram launch (1, 4 or 8)."""
+    lib().adc_debug_set_batched_items(int(items))
 
 
 def debug_set_scan_prefetch(on):

@@ -37,6 +37,9 @@ __device__ __forceinline__ unsigned long long bmax_key(float v, int64_t i) {
 }
 __device__ __forceinline__ int64_t bmax_index(unsigned long long k) { return (int64_t)(0xffffffffu - (uint32_t)k); }
 
+// Elements per thread and step of the histogram launch (1, 4 or 8; tuning hook).
+static int g_batched_ipt = 4;
+
 __global__ void k_b_init(const adc_instance *__restrict__ desc, float *__restrict__ hist,
                          unsigned long long *__restrict__ tab) {
     const adc_instance d = desc[blockIdx.x];
@@ -46,6 +49,27 @@ __global__ void k_b_init(const adc_instance *__restrict__ desc, float *__restric
     }
 }
 
+// IPT elements per thread and step (e = base + j * blockDim.x, j < IPT): the
+// step's key and value loads are all issued before its atomics.
+template <int IPT, class F>
+__device__ __forceinline__ void b_elements(const int32_t *__restrict__ k, const float *__restrict__ v, int64_t len,
+                                           int64_t m, F &&update) {
+    for (int64_t e0 = threadIdx.x; e0 < len; e0 += (int64_t)IPT * blockDim.x) {
+        int32_t kk[IPT];
+        float vv[IPT];
+#pragma unroll
+        for (int j = 0; j < IPT; ++j) {
+            const int64_t e = e0 + (int64_t)j * blockDim.x;
+            kk[j] = e < len ? __ldcs(k + e) : -1;
+            vv[j] = e < len ? __ldcs(v + e) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < IPT; ++j)
+            if ((uint32_t)kk[j] < (uint64_t)m) update(kk[j], vv[j], e0 + (int64_t)j * blockDim.x);
+    }
+}
+
+template <int IPT>
 __global__ void __launch_bounds__(kBHistThreads)
 k_b_hist(const adc_instance *__restrict__ desc, const adc_work *__restrict__ items, const int64_t n_items,
          const int32_t *__restrict__ keys, const float *__restrict__ vals, float *__restrict__ hist,
@@ -71,42 +95,30 @@ k_b_hist(const adc_instance *__restrict__ desc, const adc_work *__restrict__ ite
             if (use_smem) {
                 for (int64_t j = threadIdx.x; j < m; j += blockDim.x) sf[j] = 0.f;
                 __syncthreads();
-                for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
-                    const int32_t kk = __ldcs(k + e);
-                    if ((uint32_t)kk < (uint64_t)m) atomicAdd(sf + kk, __ldcs(v + e));
-                }
+                b_elements<IPT>(k, v, len, m, [&](int32_t kk, float x, int64_t) { atomicAdd(sf + kk, x); });
                 __syncthreads();
                 for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
                     if (sf[j] != 0.f) atomicAdd(g + j, sf[j]);
             } else {
-                for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
-                    const int32_t kk = __ldcs(k + e);
-                    if ((uint32_t)kk < (uint64_t)m) atomicAdd(g + kk, __ldcs(v + e));
-                }
+                b_elements<IPT>(k, v, len, m, [&](int32_t kk, float x, int64_t) { atomicAdd(g + kk, x); });
             }
         } else {
             unsigned long long *g = tab + d.bin_off;
             if (use_smem) {
                 for (int64_t j = threadIdx.x; j < m; j += blockDim.x) su[j] = 0ull;
                 __syncthreads();
-                for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
-                    const int32_t kk = __ldcs(k + e);
-                    if ((uint32_t)kk < (uint64_t)m) {
-                        const unsigned long long key = bmax_key(__ldcs(v + e), it.start + e);
-                        if (key > *reinterpret_cast<volatile unsigned long long *>(su + kk)) atomicMax(su + kk, key);
-                    }
-                }
+                b_elements<IPT>(k, v, len, m, [&](int32_t kk, float x, int64_t e) {
+                    const unsigned long long key = bmax_key(x, it.start + e);
+                    if (key > *reinterpret_cast<volatile unsigned long long *>(su + kk)) atomicMax(su + kk, key);
+                });
                 __syncthreads();
                 for (int64_t j = threadIdx.x; j < m; j += blockDim.x)
                     if (su[j] > __ldcg(g + j)) atomicMax(g + j, su[j]);
             } else {
-                for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
-                    const int32_t kk = __ldcs(k + e);
-                    if ((uint32_t)kk < (uint64_t)m) {
-                        const unsigned long long key = bmax_key(__ldcs(v + e), it.start + e);
-                        if (key > __ldcg(g + kk)) atomicMax(g + kk, key);
-                    }
-                }
+                b_elements<IPT>(k, v, len, m, [&](int32_t kk, float x, int64_t e) {
+                    const unsigned long long key = bmax_key(x, it.start + e);
+                    if (key > __ldcg(g + kk)) atomicMax(g + kk, key);
+                });
             }
         }
     }
@@ -314,12 +326,18 @@ adc_status adc_batched_hist_scan_fwd(const adc_instance *desc, int32_t count, co
     if (cudaMemsetAsync(ws, 0, kWsHeader, s) != cudaSuccess) return ADC_ERR_CUDA;
     k_b_init<<<count, 256, 0, s>>>(desc, hist, tab);
     if (n_items > 0) {
-        if (cudaFuncSetAttribute(k_b_hist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return ADC_ERR_CUDA;
         int per_sm = (int)((200 * 1024) / (smem + 1024));
         per_sm = per_sm < 1 ? 1 : (per_sm > 4 ? 4 : per_sm);
-        k_b_hist<<<num_sms() * per_sm, kBHistThreads, smem, s>>>(desc, items, n_items, keys, vals, hist, tab,
-                                                                   smem_bins, counter_slot(ws, 0));
+        const unsigned grid = (unsigned)(num_sms() * per_sm);
+        unsigned *ctr = counter_slot(ws, 0);
+        auto run = [&](auto kern) -> bool {
+            if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+                return false;
+            kern<<<grid, kBHistThreads, smem, s>>>(desc, items, n_items, keys, vals, hist, tab, smem_bins, ctr);
+            return true;
+        };
+        const bool ok = g_batched_ipt == 1 ? run(k_b_hist<1>) : g_batched_ipt == 8 ? run(k_b_hist<8>) : run(k_b_hist<4>);
+        if (!ok) return ADC_ERR_CUDA;
     }
     k_b_scan_loss<<<count, kBScanThreads, 0, s>>>(desc, count, vals, hist, tab, scan, is, loss_parts, loss,
                                                    counter_slot(ws, 1));
@@ -346,3 +364,7 @@ adc_status adc_batched_hist_scan_vjp(const adc_instance *desc, int32_t count, co
 }
 
 }  // extern "C"
+
+extern "C" void adc_debug_set_batched_items(int items) {
+    g_batched_ipt = (items == 1 || items == 8) ? items : 4;
+}

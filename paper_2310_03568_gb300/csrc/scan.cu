@@ -107,11 +107,13 @@ template <typename E, int ITEMS, class Derived> struct PlainScan {
 };
 
 template <typename T, int ITEMS> struct FwdAdd : PlainScan<T, ITEMS, FwdAdd<T, ITEMS>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ T identity() const { return T(0); }
     __device__ T combine(T a, T b) const { return a + b; }
 };
 
 template <typename T, int ITEMS> struct FwdMul : PlainScan<T, ITEMS, FwdMul<T, ITEMS>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ T identity() const { return T(1); }
     __device__ T combine(T a, T b) const { return a * b; }
 };
@@ -119,6 +121,7 @@ template <typename T, int ITEMS> struct FwdMul : PlainScan<T, ITEMS, FwdMul<T, I
 // min / max scans: the running extremum; the earlier operand wins ties (the
 // lifted operator of Fig. 5 with the lowest index first).
 template <typename T, int ITEMS, bool MAX> struct FwdSel : PlainScan<T, ITEMS, FwdSel<T, ITEMS, MAX>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ T identity() const { return MAX ? -Num<T>::inf() : Num<T>::inf(); }
     __device__ T combine(T a, T b) const { return (MAX ? (b > a) : (b < a)) ? b : a; }
     // The scan's loop starts from y_0 = x_0, and a NaN never loses as the
@@ -136,12 +139,14 @@ template <typename T, int ITEMS, bool MAX> struct FwdSel : PlainScan<T, ITEMS, F
 
 // linFnComp (Fig. 8): (b1,c1) . (b2,c2) = (b2 + c2*b1, c2*c1)
 template <typename T, int ITEMS> struct FwdLin : PlainScan<Pair<T>, ITEMS, FwdLin<T, ITEMS>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ Pair<T> identity() const { return {T(0), T(1)}; }
     __device__ Pair<T> combine(const Pair<T> &a, const Pair<T> &b) const { return {b.b + b.c * a.b, b.c * a.c}; }
 };
 
 // sumOfProd (Fig. 8): (p1,s1) . (p2,s2) = (p1 + p2 + s1*s2, s1 + s2)
 template <typename T, int ITEMS> struct FwdSop : PlainScan<Pair<T>, ITEMS, FwdSop<T, ITEMS>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ Pair<T> identity() const { return {T(0), T(0)}; }
     __device__ Pair<T> combine(const Pair<T> &a, const Pair<T> &b) const {
         return {a.b + b.b + a.c * b.c, a.c + b.c};
@@ -149,6 +154,7 @@ template <typename T, int ITEMS> struct FwdSop : PlainScan<Pair<T>, ITEMS, FwdSo
 };
 
 template <typename T, int ITEMS> struct FwdMM2 : PlainScan<Mat2<T>, ITEMS, FwdMM2<T, ITEMS>> {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     __device__ Mat2<T> identity() const { return mat_eye<T>(); }
     __device__ Mat2<T> combine(const Mat2<T> &a, const Mat2<T> &b) const { return mat_mul(a, b); }
 };
@@ -156,6 +162,7 @@ template <typename T, int ITEMS> struct FwdMM2 : PlainScan<Mat2<T>, ITEMS, FwdMM
 // ---------------------------------------------------------------- vjp ops --
 // Sec. 5.3.1: the adjoint of a +-scan is a reverse +-scan of ybar.
 template <typename T, int ITEMS> struct VjpAdd {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     using State = T;
     using Aux = NoAux;
     using Raw = Chunk<T, ITEMS>;
@@ -201,6 +208,7 @@ template <typename E, int ITEMS> struct VjpRaw {
 
 // Product scan: J_{i+1} = x_{i+1}; xbar_i = y_{i-1} * lambda_i.
 template <typename T, int ITEMS> struct VjpMul {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
     using State = AffS<T>;
     using Raw = VjpRaw<T, ITEMS>;
@@ -249,6 +257,7 @@ template <typename T, int ITEMS> struct VjpMul {
 template <typename T> __device__ __forceinline__ bool same_value(T a, T b) { return a == b || (a != a && b != b); }
 
 template <typename T, int ITEMS, bool MAX> struct VjpSel {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     using State = AffS<T>;
     struct Raw {
         Chunk<T, ITEMS> yb;
@@ -298,6 +307,7 @@ template <typename T, int ITEMS, bool MAX> struct VjpSel {
 // linFnComp scan: J = diag(c_{i+1}, c_{i+1}) (Sec. 5.3.4);
 // bbar_i = lambda.b, cbar_i = lambda.b * B_{i-1} + lambda.c * C_{i-1}, (B,C)_{-1} = (0,1).
 template <typename T, int ITEMS> struct VjpLin {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
     using State = AffP<T>;
     using Raw = VjpRaw<Pair<T>, ITEMS>;
@@ -356,6 +366,7 @@ template <typename T, int ITEMS> struct VjpLin {
 template <typename T> struct AffU { T vp, vs, sig; };
 
 template <typename T, int ITEMS> struct VjpSop {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     static constexpr int kRangeTiles = sizeof(T) == 4 ? 8 : 0;
     using State = AffU<T>;
     using Raw = VjpRaw<Pair<T>, ITEMS>;
@@ -406,6 +417,7 @@ template <typename T, int ITEMS> struct VjpSop {
 template <typename T> struct AffM { Mat2<T> v, c; };
 
 template <typename T, int ITEMS> struct VjpMM2 {
+    static constexpr bool kKeepPrefix = sizeof(T) == 8;  // fp64: the combine is the bound
     using State = AffM<T>;
     using Raw = VjpRaw<Mat2<T>, ITEMS>;
     struct Aux { Mat2<T> yprev[ITEMS]; };

@@ -55,6 +55,17 @@ template <class Op> constexpr bool per_tile_only(long) { return false; }
 template <class Op> constexpr auto per_tile_only(int) -> decltype(Op::kPerTileOnly, bool()) {
     return Op::kPerTileOnly;
 }
+// An Op may ask (kKeepPrefix) the range engine to keep, from phase A, every
+// thread's exclusive prefix within its warp for every tile of the range in
+// shared memory, so that phase B needs neither the thread folds nor the warp
+// scans again: worth it where the combine itself is the bound (fp64 on this
+// part's FP64 pipe).  Ranges are then at most keep_tiles<S>() tiles long.
+template <class Op> constexpr bool keep_prefix(long) { return false; }
+template <class Op> constexpr auto keep_prefix(int) -> decltype(Op::kKeepPrefix, bool()) { return Op::kKeepPrefix; }
+template <typename S, int THREADS> constexpr int keep_tiles() {
+    return (int)((32 * 1024) / (THREADS * sizeof(S))) < 1 ? 1 : (int)((32 * 1024) / (THREADS * sizeof(S)));
+}
+
 // Ops that name their input arrays (kStreams, stream(s), Elem) can have a
 // block's range prefetched into L2 by bulk prefetches.
 template <class Op> constexpr int op_streams(long) { return 0; }
@@ -324,9 +335,12 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
     constexpr int TILE = THREADS * ITEMS;
     constexpr int NW = THREADS / kWarp;
     constexpr int K = Tagged<S>::K;
-    constexpr int MT = range_max_tiles<S>();
+    constexpr bool KEEP = keep_prefix<Op>(0);
+    constexpr int KT = KEEP ? keep_tiles<S, THREADS>() : 1;
+    constexpr int MT = KEEP ? KT : range_max_tiles<S>();  // KEEP ranges are at most KT tiles
     __shared__ unsigned s_range;
     __shared__ S s_wt[MT * NW];  // warp-tile aggregates, then their exclusive prefixes
+    __shared__ S s_tp[KT * THREADS];  // KEEP: each thread's exclusive prefix in its warp, per tile
     __shared__ S s_lbv[NW];
     __shared__ int s_lbinc[NW], s_lberr[NW];
     __shared__ S s_range_agg;
@@ -384,6 +398,11 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
                 if (i + PF < cnt) op.fetch(chunk0(t0 + i + PF), n, raw[q]);
                 const S winc = warp_inclusive_scan(op, thread_agg(st));
                 if (lane == kWarp - 1) s_wt[i * NW + warp] = winc;
+                if constexpr (KEEP) {
+                    S ex = shfl_up(winc, 1);
+                    if (lane == 0) ex = op.identity();
+                    s_tp[i * THREADS + tid] = ex;
+                }
             }
         }
     }
@@ -493,8 +512,13 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
                 const int64_t c0 = chunk0(t0 + i);
                 op.build(c0, n, raw[q], st, aux);
                 if (j + PF < cnt) op.fetch(chunk0(t0 + i - PF), n, raw[q]);
-                S ex = shfl_up(warp_inclusive_scan(op, thread_agg(st)), 1);
-                if (lane == 0) ex = op.identity();
+                S ex;
+                if constexpr (KEEP) {
+                    ex = s_tp[i * THREADS + tid];
+                } else {
+                    ex = shfl_up(warp_inclusive_scan(op, thread_agg(st)), 1);
+                    if (lane == 0) ex = op.identity();
+                }
                 S run = op.combine(s_wt[i * NW + warp], ex);
 #pragma unroll
                 for (int k = 0; k < ITEMS; ++k) {
@@ -584,7 +608,12 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     // smaller ranges (blocks claim them in start order, so the look-back only
     // ever waits on running blocks).
     int64_t R = G;
-    const int rt = g_scan_range_tiles > 0 ? g_scan_range_tiles : range_tiles_hint<Op>(0);
+    int rt = g_scan_range_tiles > 0 ? g_scan_range_tiles : range_tiles_hint<Op>(0);
+    if constexpr (keep_prefix<Op>(0)) {  // one range per resident block, at most the kept tiles long
+        constexpr int KT = keep_tiles<typename Op::State, kScanThreads>();
+        if (rt <= 0) rt = (int)((T + G - 1) / G);
+        if (rt > KT) rt = KT;
+    }
     if (rt > 0) R = (T + rt - 1) / rt;
     if (R > T) R = T;
     const bool ranges = T <= (int64_t)range_max_tiles<typename Op::State>() * R &&

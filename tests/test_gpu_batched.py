@@ -77,14 +77,20 @@ def test_batched_matches_oracle_and_closed_form():
     check_problem(p, desc, keys, vals, oracle_reference(desc, keys, vals))
 
 
+@pytest.mark.parametrize("items", [1, 4, 8])
 @pytest.mark.parametrize("chunk,smem_bins", [(1 << 10, 2048), (1 << 16, 8192), (1 << 20, 0), (333, 24000)])
-def test_batched_tunings_agree(chunk, smem_bins):
+def test_batched_tunings_agree(chunk, smem_bins, items):
+    from paper_2310_03568_gb300 import adcomb
     w = small_workload(seed=32, count=24)
     desc, keys, vals = B.layout(w)
     p = B.BatchedHistScan(desc, keys, vals, chunk=chunk, smem_bins=smem_bins)
-    p.forward()
-    p.backward()
-    torch.cuda.synchronize()
+    try:
+        adcomb.debug_set_batched_items(items)
+        p.forward()
+        p.backward()
+        torch.cuda.synchronize()
+    finally:
+        adcomb.debug_set_batched_items(4)
     check_problem(p, desc, keys, vals, oracle_reference(desc, keys, vals))
 
 
@@ -185,7 +191,9 @@ def test_autotuner_picks_a_configuration_and_caches_it(tmp_path, monkeypatch):
     p = B.BatchedHistScan(desc, keys, vals)
     entry = autotune.tune_batched(p)
     assert entry["chunk"] in autotune.BATCHED_CHUNKS and entry["smem_bins"] in autotune.BATCHED_SMEM_BINS
-    assert len(entry["candidates"]) == len(autotune.BATCHED_CHUNKS) * len(autotune.BATCHED_SMEM_BINS)
+    assert entry["items"] in autotune.BATCHED_ITEMS
+    assert len(entry["candidates"]) == (len(autotune.BATCHED_CHUNKS) * len(autotune.BATCHED_SMEM_BINS) *
+                                        len(autotune.BATCHED_ITEMS))
     p.forward()
     p.backward()
     torch.cuda.synchronize()
@@ -193,6 +201,7 @@ def test_autotuner_picks_a_configuration_and_caches_it(tmp_path, monkeypatch):
     autotune._cache = None  # reload from the file: a cache hit, no re-measurement
     again = autotune.tune_batched(B.BatchedHistScan(desc, keys, vals))
     assert again["chunk"] == entry["chunk"] and again["smem_bins"] == entry["smem_bins"]
+    assert again["items"] == entry["items"]
     # single-call histogram strategy
     n, m = 400_000, 401
     g = np.random.default_rng(36)
@@ -206,5 +215,17 @@ def test_autotuner_picks_a_configuration_and_caches_it(tmp_path, monkeypatch):
         ref, idx = oracle.hist_fwd("max", m, k, v)
         assert np.array_equal(h.cpu().numpy(), ref.astype(np.float32))
         assert np.array_equal(saved.view(torch.int32).cpu().numpy()[:m], idx.astype(np.int32))
+        # single-call scan: items per thread and tile shape
+        x = synth.scan_values(g, "lin", 3_000_001)
+        xd = torch.tensor(x, device="cuda")
+        e = autotune.tune_scan("lin", xd)
+        assert (e["engine"], e["range_tiles"]) in autotune.SCAN_CANDIDATES
+        assert len(e["candidates"]) == len(autotune.SCAN_CANDIDATES)
+        y = adcomb.scan_fwd("lin", xd).cpu().numpy()
+        yr = oracle.scan_fwd("lin", x)
+        assert np.abs(y - yr).max() <= 1e-3 * np.abs(yr).max()
+        autotune._cache = None  # a cache hit selects the same configuration again
+        assert autotune.tune_scan("lin", xd)["engine"] == e["engine"]
     finally:
+        autotune.apply_scan(None)
         adcomb.debug_force_hist_strategy(-1)
