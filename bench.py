@@ -722,6 +722,8 @@ def run_kernels(args):
                     [(3, rt, "staged" if rt == 0 else f"staged rt={rt}") for rt in rts] +
                     [(5, rt, "ranges16" if rt == 0 else f"ranges16 rt={rt}") for rt in rts] +
                     [(1, 0, "per-tile"), (4, 0, "tma")])
+        if op in ("mm3", "mm5"):  # bulk-staged segment forms (automatic) and the register forms
+            variants = [(0, 0, "bulk-staged"), (2, 0, "ranges"), (1, 0, "per-tile")]
         if args.prefetch:
             variants = [(2, rt, f"ranges rt={rt} prefetch") for rt in rts]
         adcomb.debug_set_scan_prefetch(1 if args.prefetch else 0)

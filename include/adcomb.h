@@ -413,8 +413,12 @@ void adc_debug_set_stall_tile(int64_t tile);
  * n, per-tile look-back otherwise), 1 per-tile look-back only, 2 range-
  * partitioned wherever it applies, 3 range-partitioned with the range staged
  * in shared memory by bulk (TMA) copies, 4 per-tile look-back with each
- * block's tile staged in shared memory by bulk copies.  In the fault-injection
- * hook above, the "tile" of the range engines is a range.
+ * block's tile staged in shared memory by bulk copies, 5 the range engine with
+ * 16 bytes of each array per thread per tile, 6 the bulk-staged segment forms
+ * of the q x q matrix scans (ADC_OP_MM3 / ADC_OP_MM5; also what 0 picks for
+ * them, while 1 and 2 pick their register forms).  Other values restore 0.
+ * In the fault-injection hook
+ * above, the "tile" of the range engines is a range.
  */
 void adc_debug_set_scan_engine(int engine);
 

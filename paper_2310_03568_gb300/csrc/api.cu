@@ -415,7 +415,7 @@ void adc_set_spin_limit(int64_t iterations) { g_spin_limit = iterations < 1 ? (1
 
 void adc_debug_set_stall_tile(int64_t tile) { g_stall_tile = tile; }
 
-void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 5) ? engine : 0; }
+void adc_debug_set_scan_engine(int engine) { g_scan_engine = (engine >= 0 && engine <= 6) ? engine : 0; }
 void adc_debug_set_scan_range_tiles(int tiles) { g_scan_range_tiles = tiles > 0 ? tiles : 0; }
 void adc_debug_set_scan_prefetch(int on) { g_scan_prefetch = on ? 1 : 0; }
 

@@ -121,6 +121,41 @@ template <typename T, int Q> __device__ __forceinline__ MatQ<T, Q> matq_zero() {
     for (int i = 0; i < Q * Q; ++i) z.a[i] = T(0);
     return z;
 }
+// The q x q vjp's affine maps L -> v + L c (c a product of transposed elements).
+template <typename T, int Q> struct AffQ { MatQ<T, Q> v, c; };
+// In-place products for the matrix segment walks (one row of temporaries):
+// A <- A B, and A <- A B^T with B given untransposed.
+template <typename T, int Q> __device__ __forceinline__ void matq_mul_right(MatQ<T, Q> &A, const MatQ<T, Q> &B) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T r[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            T acc = A.a[Q * i] * B.a[j];
+#pragma unroll
+            for (int k = 1; k < Q; ++k) acc += A.a[Q * i + k] * B.a[Q * k + j];
+            r[j] = acc;
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) A.a[Q * i + j] = r[j];
+    }
+}
+template <typename T, int Q> __device__ __forceinline__ void matq_mul_right_t(MatQ<T, Q> &A, const MatQ<T, Q> &B) {
+#pragma unroll
+    for (int i = 0; i < Q; ++i) {
+        T r[Q];
+#pragma unroll
+        for (int j = 0; j < Q; ++j) {
+            T acc = A.a[Q * i] * B.a[Q * j];
+#pragma unroll
+            for (int k = 1; k < Q; ++k) acc += A.a[Q * i + k] * B.a[Q * j + k];
+            r[j] = acc;
+        }
+#pragma unroll
+        for (int j = 0; j < Q; ++j) A.a[Q * i + j] = r[j];
+    }
+}
+
 
 // --------------------------------------------------- L2-coherent state I/O --
 // Look-back states are plain structs of T; they are read with ld.global.cg

@@ -9,9 +9,12 @@
 // reverse scan consumes elements.  The final map
 // xbar_i = d(y_{i-1} . x_i)/dx_i ^T lambda_i (y_{-1} = e) is fused into the
 // store, so a vjp reads x, y, ybar once and writes xbar once.
+#include <type_traits>
+
 #include "common.cuh"
 #include "internal.h"
 #include "scan_engine.cuh"
+#include "scan_mmq.cuh"
 #include "scan_tma.cuh"
 #include "scan_staged.cuh"
 #include "tile_io.cuh"
@@ -469,8 +472,6 @@ struct FwdMMQ : PlainScan<MatQ<T, Q>, ITEMS, FwdMMQ<T, Q, ITEMS>> {
     __device__ MatQ<T, Q> combine(const MatQ<T, Q> &a, const MatQ<T, Q> &b) const { return matq_mul(a, b); }
 };
 
-template <typename T, int Q> struct AffQ { MatQ<T, Q> v, c; };
-
 template <typename T, int Q, int ITEMS> struct VjpMMQ {
     using E = MatQ<T, Q>;
     using State = AffQ<T, Q>;
@@ -516,39 +517,6 @@ template <typename T, int Q, int ITEMS> struct VjpMMQ {
 // vjp's affine maps, so it costs one matrix product per element instead of
 // two.  Loads are per thread over its own contiguous run (L1 keeps the lines
 // between the two walks).
-// In-place products for the segment walks (one row of temporaries):
-// A <- A B, and A <- A B^T with B given untransposed.
-template <typename T, int Q> __device__ __forceinline__ void matq_mul_right(MatQ<T, Q> &A, const MatQ<T, Q> &B) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        T r[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            T acc = A.a[Q * i] * B.a[j];
-#pragma unroll
-            for (int k = 1; k < Q; ++k) acc += A.a[Q * i + k] * B.a[Q * k + j];
-            r[j] = acc;
-        }
-#pragma unroll
-        for (int j = 0; j < Q; ++j) A.a[Q * i + j] = r[j];
-    }
-}
-template <typename T, int Q> __device__ __forceinline__ void matq_mul_right_t(MatQ<T, Q> &A, const MatQ<T, Q> &B) {
-#pragma unroll
-    for (int i = 0; i < Q; ++i) {
-        T r[Q];
-#pragma unroll
-        for (int j = 0; j < Q; ++j) {
-            T acc = A.a[Q * i] * B.a[Q * j];
-#pragma unroll
-            for (int k = 1; k < Q; ++k) acc += A.a[Q * i + k] * B.a[Q * j + k];
-            r[j] = acc;
-        }
-#pragma unroll
-        for (int j = 0; j < Q; ++j) A.a[Q * i + j] = r[j];
-    }
-}
-
 template <typename T, int Q, int SEG> struct SegFwdMMQ {
     using E = MatQ<T, Q>;
     using State = E;
@@ -683,6 +651,16 @@ static size_t max4(size_t a, size_t b, size_t c, size_t d) {
     return ab > cd ? ab : cd;
 }
 
+// The bulk-staged matrix segment scans (scan_mmq.cuh) at the run length and
+// block size MMQStaged picks.
+template <typename T, int Q, bool VJP> using MMQStagedOp =
+    typename std::conditional<VJP, StagedVjpMMQ<T, Q, MMQStaged<T, Q, true>::threads, MMQStaged<T, Q, true>::seg>,
+                              StagedFwdMMQ<T, Q, MMQStaged<T, Q, false>::threads, MMQStaged<T, Q, false>::seg>>::type;
+template <typename T, int Q, bool VJP> static size_t mmq_staged_region(int64_t n) {
+    constexpr int L = MMQStaged<T, Q, VJP>::seg;
+    return ScanShape<MMQStagedOp<T, Q, VJP>, 1>::region((n + L - 1) / L);
+}
+
 template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
     using I = Items<T>;
     size_t a = 0, b = 0, c = 0, d = 0;
@@ -720,13 +698,17 @@ template <typename T> static size_t scan_ws_t(adc_op op, int64_t n) {
         const int64_t runs = (n + SegLen<3>::value - 1) / SegLen<3>::value;
         a = ScanShape<FwdMMQ<T, 3, I::mat3>, I::mat3>::region(n);
         b = ScanShape<SegVjpMMQ<T, 3, SegLen<3>::value>, 1>::region(runs);
-        return kWsHeader + (a > b ? a : b);
+        c = mmq_staged_region<T, 3, false>(n);
+        d = mmq_staged_region<T, 3, true>(n);
+        return kWsHeader + max4(a, b, c, d);
     }
     case ADC_OP_MM5: {
         const int64_t runs = (n + SegLen<5>::value - 1) / SegLen<5>::value;
         a = ScanShape<SegFwdMMQ<T, 5, SegLen<5>::value>, 1>::region(runs);
         b = ScanShape<SegVjpMMQ<T, 5, SegLen<5>::value>, 1>::region(runs);
-        return kWsHeader + (a > b ? a : b);
+        c = mmq_staged_region<T, 5, false>(n);
+        d = mmq_staged_region<T, 5, true>(n);
+        return kWsHeader + max4(a, b, c, d);
     }
     default: return 0;
     }
@@ -861,6 +843,27 @@ static adc_status scan_vjp_items16(adc_op op, int64_t n, const void *x, const vo
     }
 }
 
+// q x q matrix scans: the bulk-staged segment forms (scan_mmq.cuh; the API
+// has checked that every array is 16-byte aligned) unless the engine hook
+// asks for the register forms (1: per-tile, 2: ranges where the forward has
+// one); hook 6 asks for the staged forms explicitly.
+static bool mmq_staged_ok() { return g_scan_engine == 0 || g_scan_engine == 6; }
+template <typename T, int Q>
+static adc_status mmq_fwd_staged(int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
+    constexpr int L = MMQStaged<T, Q, false>::seg;
+    MMQStagedOp<T, Q, false> o{static_cast<const MatQ<T, Q> *>(x), static_cast<MatQ<T, Q> *>(y), n};
+    return launch<decltype(o), 1, false>(o, (n + L - 1) / L, ws, s);
+}
+template <typename T, int Q>
+static adc_status mmq_vjp_staged(int64_t n, const void *x, const void *y, const void *ybar, void *xbar, int acc,
+                                 void *ws, cudaStream_t s) {
+    using M = MatQ<T, Q>;
+    constexpr int L = MMQStaged<T, Q, true>::seg;
+    MMQStagedOp<T, Q, true> o{static_cast<const M *>(x), static_cast<const M *>(y), static_cast<const M *>(ybar),
+                              static_cast<M *>(xbar), acc, n};
+    return launch<decltype(o), 1, true>(o, (n + L - 1) / L, ws, s);
+}
+
 template <typename T>
 static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void *ws, cudaStream_t s) {
     using I = Items<T>;
@@ -887,6 +890,10 @@ static adc_status scan_fwd_t(adc_op op, int64_t n, const void *x, void *y, void 
         o.x = static_cast<const T *>(x);
         o.y = static_cast<T *>(y);
         return launch<decltype(o), I::scalar, false>(o, n, ws, s);
+    }
+    if ((op == ADC_OP_MM3 || op == ADC_OP_MM5) && mmq_staged_ok()) {
+        if (op == ADC_OP_MM3) return mmq_fwd_staged<T, 3>(n, x, y, ws, s);
+        return mmq_fwd_staged<T, 5>(n, x, y, ws, s);
     }
     if (op == ADC_OP_MM3) {  // the 3x3 forward holds a few matrices per thread without spilling
         FwdMMQ<T, 3, I::mat3> o;
@@ -997,6 +1004,10 @@ static adc_status scan_vjp_t(adc_op op, int64_t n, const void *x, const void *y,
         VjpSel<T, I::vscalar, false> o{static_cast<const T *>(x), static_cast<const T *>(y),
                                        static_cast<const T *>(ybar), static_cast<T *>(xbar), acc};
         return launch<decltype(o), I::vscalar, true>(o, n, ws, s);
+    }
+    if ((op == ADC_OP_MM3 || op == ADC_OP_MM5) && mmq_staged_ok()) {
+        if (op == ADC_OP_MM3) return mmq_vjp_staged<T, 3>(n, x, y, ybar, xbar, acc, ws, s);
+        return mmq_vjp_staged<T, 5>(n, x, y, ybar, xbar, acc, ws, s);
     }
     if (op == ADC_OP_MM3 || op == ADC_OP_MM5) {
         if (op == ADC_OP_MM3) {

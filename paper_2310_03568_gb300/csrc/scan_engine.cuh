@@ -55,6 +55,21 @@ template <class Op> constexpr bool per_tile_only(long) { return false; }
 template <class Op> constexpr auto per_tile_only(int) -> decltype(Op::kPerTileOnly, bool()) {
     return Op::kPerTileOnly;
 }
+// A per-tile-only Op may also ask for its own block size (kThreads) and for
+// dynamic shared memory (kDynSmem bytes, e.g. to stage its tile).
+template <class Op> constexpr int op_threads(long) { return 256; }
+template <class Op> constexpr auto op_threads(int) -> decltype(Op::kThreads, int()) { return Op::kThreads; }
+template <class Op> constexpr size_t op_dyn_smem(long) { return 0; }
+template <class Op> constexpr auto op_dyn_smem(int) -> decltype(Op::kDynSmem, size_t()) { return Op::kDynSmem; }
+// A per-tile-only Op may stage its tile in shared memory by bulk copies
+// (kBulkStaged): thread 0 calls op.stage_init() (its mbarrier) when it claims
+// the tile, op.fetch() has thread 0 issue the copies, and every thread then
+// waits through op.staged_wait(limit), bounded, before build().  A wait that
+// runs out marks the tile ERROR and records kErrTimeout, as a look-back that
+// runs out does; thread 0 then gives the copies a second bounded wait before
+// the block leaves.
+template <class Op> constexpr bool bulk_staged(long) { return false; }
+template <class Op> constexpr auto bulk_staged(int) -> decltype(Op::kBulkStaged, bool()) { return Op::kBulkStaged; }
 // An Op may ask (kKeepPrefix) the range engine to keep, from phase A, every
 // thread's exclusive prefix within its warp for every tile of the range in
 // shared memory, so that phase B needs neither the thread folds nor the warp
@@ -86,7 +101,12 @@ extern int g_scan_prefetch;
 // written and read with single-copy-atomic 64-bit accesses, so a reader that
 // sees the same non-zero tag in all K words holds a consistent state -- one
 // round trip per poll, no separate flag and no acquire/release pair.  Mixed
-// tags mean a write in progress: poll again.
+// tags mean a write in progress: poll again.  The arrays are word-major:
+// word k of tile j sits at slot[k * stride + j] (stride = the launch's tile
+// count), so a warp polling 32 consecutive tiles reads 256 contiguous bytes
+// per word instead of touching 32 lines -- for large states (tags_first);
+// small ones keep their K words together (slot[j * K + k]: word-major
+// measured slower for them, e.g. the 2x2 per-tile forward 0.19 -> 0.27 ms).
 template <typename S> struct Tagged {
     static constexpr int K = sizeof(S) / 4;
     static_assert(sizeof(S) % 4 == 0, "state must be made of 32-bit words");
@@ -101,25 +121,50 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-template <typename S> __device__ __forceinline__ void publish(unsigned long long *slot, const S &v, unsigned tag) {
-    const unsigned *w = reinterpret_cast<const unsigned *>(&v);
-#pragma unroll
-    for (int k = 0; k < Tagged<S>::K; ++k) st_relaxed_u64(slot + k, ((unsigned long long)tag << 32) | w[k]);
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
 }
-__device__ __forceinline__ void publish_tag(unsigned long long *slot, int K, unsigned tag) {
-    for (int k = 0; k < K; ++k) st_relaxed_u64(slot + k, (unsigned long long)tag << 32);
+__device__ __forceinline__ void st_release_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Large states (more than 4 words) are read tag first by the look-back (see
+// wait_tag); small ones are polled in full, one round trip per poll.
+template <typename S> constexpr bool tags_first() { return Tagged<S>::K > 4; }
+
+// A large state's word 0 goes last, as a release: a reader that acquires
+// word 0 with the tag then finds every other word in place, so it reads the
+// state once (measured: the 3x3 vjp 0.62 -> 0.55 ms).  Small states keep
+// relaxed stores only (a release per publish slowed the fp32 * vjp's
+// 6000-range scan by a fifth); their readers check every word's tag.
+template <typename S>
+__device__ __forceinline__ void publish(unsigned long long *slot, const S &v, unsigned tag, int64_t stride) {
+    const unsigned *w = reinterpret_cast<const unsigned *>(&v);
+    const unsigned long long t = (unsigned long long)tag << 32;
+#pragma unroll
+    for (int k = Tagged<S>::K - 1; k > 0; --k) st_relaxed_u64(slot + k * stride, t | w[k]);
+    if constexpr (tags_first<S>())
+        st_release_u64(slot, t | w[0]);
+    else
+        st_relaxed_u64(slot, t | w[0]);
+}
+__device__ __forceinline__ void publish_tag(unsigned long long *slot, int K, unsigned tag, int64_t stride) {
+    for (int k = 0; k < K; ++k) st_relaxed_u64(slot + k * stride, (unsigned long long)tag << 32);
 }
 
 // One poll of tile j: returns kFlagInc / kFlagAgg with the state in *out,
 // kFlagError if the tile failed, or kFlagNone if nothing complete is visible.
 template <typename S>
-__device__ __forceinline__ unsigned poll_tile(const unsigned long long *agg, const unsigned long long *inc, S *out) {
+__device__ __forceinline__ unsigned poll_tile(const unsigned long long *agg, const unsigned long long *inc, S *out,
+                                              int64_t stride) {
     constexpr int K = Tagged<S>::K;
     unsigned long long a[K], b[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-        b[k] = ld_relaxed_u64(inc + k);
-        a[k] = ld_relaxed_u64(agg + k);
+        b[k] = ld_relaxed_u64(inc + k * stride);
+        a[k] = ld_relaxed_u64(agg + k * stride);
     }
     unsigned *w = reinterpret_cast<unsigned *>(out);
     bool inc_ok = true, agg_ok = true, err = false;
@@ -146,15 +191,58 @@ __device__ __forceinline__ unsigned poll_tile(const unsigned long long *agg, con
 // Bounded spin until tile j shows a complete state.
 template <typename S>
 __device__ __forceinline__ unsigned wait_tile(const unsigned long long *agg, const unsigned long long *inc, S *out,
-                                              long long limit) {
+                                              long long limit, int64_t stride) {
     long long it = 0;
-    unsigned f = poll_tile(agg, inc, out);
+    unsigned f = poll_tile(agg, inc, out, stride);
     while (f == kFlagNone) {
         if (++it > limit) return kFlagError;
         __nanosleep(32);
-        f = poll_tile(agg, inc, out);
+        f = poll_tile(agg, inc, out, stride);
     }
     return f;
+}
+
+// Large states (tags_first): a look-back lane first spins on the two tag
+// words of its tile only, and reads the whole state afterwards, only where
+// the ordered reduction needs it (at or before the nearest inclusive
+// prefix).  Measured on the 3x3 forward (9-word states): polling every state
+// in full read 1.7 GB of L2 for 0.18 GB of input; one full poll before the
+// tag spin still doubled the kernel's time.
+// Bounded spin until tile j shows a tag: kFlagInc, kFlagAgg or kFlagError
+// (also on expiry).  Both tag words are loaded together, with acquire (see
+// publish).
+__device__ __forceinline__ unsigned wait_tag(const unsigned long long *agg, const unsigned long long *inc,
+                                             long long limit) {
+    long long it = 0;
+    while (true) {
+        const unsigned tb = (unsigned)(ld_acquire_u64(inc) >> 32);
+        const unsigned ta = (unsigned)(ld_acquire_u64(agg) >> 32);
+        if (tb == kFlagInc || tb == kFlagError) return tb;
+        if (ta == kFlagAgg) return kFlagAgg;
+        if (++it > limit) return kFlagError;
+        __nanosleep(32);
+    }
+}
+// Reads a state whose first word showed `tag`, spinning (bounded) until every
+// word carries it; false on expiry.
+template <typename S>
+__device__ __forceinline__ bool read_tagged(const unsigned long long *slot, unsigned tag, S *out, long long limit,
+                                            int64_t stride) {
+    constexpr int K = Tagged<S>::K;
+    unsigned *w = reinterpret_cast<unsigned *>(out);
+    long long it = 0;
+    while (true) {
+        bool ok = true;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const unsigned long long v = ld_relaxed_u64(slot + k * stride);
+            ok &= (unsigned)(v >> 32) == tag;
+            w[k] = (unsigned)v;
+        }
+        if (ok) return true;
+        if (++it > limit) return false;
+        __nanosleep(32);
+    }
 }
 
 template <class Op, int THREADS, int ITEMS, bool REVERSE>
@@ -165,6 +253,8 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
     constexpr int TILE = THREADS * ITEMS;
     constexpr int NW = THREADS / kWarp;
     constexpr int K = Tagged<S>::K;
+    constexpr int64_t SO = tags_first<S>() ? 1 : K;          // slot offset of a tile
+    const int64_t WS = tags_first<S>() ? num_tiles : 1;      // word stride (word-major for large states)
     static_assert(NW <= kWarp, "block too large");
     __shared__ unsigned s_tile;
     __shared__ S s_warp[NW];   // per-warp totals, then per-warp exclusive prefixes
@@ -178,7 +268,10 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
     // One tile per block, claimed when the block starts: its aggregate is
     // published one load latency after the claim, so no tile a successor
     // waits on is ever held back behind other work.
-    if (tid == 0) s_tile = atomicAdd(ctl.counter, 1u);
+    if (tid == 0) {
+        s_tile = atomicAdd(ctl.counter, 1u);
+        if constexpr (bulk_staged<Op>(0)) op.stage_init();
+    }
     __syncthreads();
     const long long t = s_tile;
     {
@@ -186,6 +279,16 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
         const int64_t c0 = p * (int64_t)TILE + (int64_t)jc * ITEMS;
         typename Op::Raw raw;
         op.fetch(c0, n, raw);
+        if constexpr (bulk_staged<Op>(0)) {
+            if (!__syncthreads_and(op.staged_wait(ctl.spin_limit))) {
+                if (tid == 0) {
+                    publish_tag(incw + t * SO, K, kFlagError, WS);
+                    set_error(ctl.err, kErrTimeout);
+                    op.staged_wait(ctl.spin_limit);
+                }
+                return;
+            }
+        }
         S st[ITEMS];
         typename Op::Aux aux;
         op.build(c0, n, raw, st, aux);
@@ -208,8 +311,8 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
                 const S total = shfl_idx(wi, NW - 1);
                 if (lane == 0) {
                     s_total = total;
-                    publish(aggw + t * K, total, kFlagAgg);
-                    if (t == 0) publish(incw, total, kFlagInc);
+                    publish(aggw + t * SO, total, kFlagAgg, WS);
+                    if (t == 0) publish(incw, total, kFlagInc, WS);
                 }
                 if (lane < NW) s_warp[lane] = wex;
             }
@@ -222,10 +325,19 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
                     const long long tj = base - (long long)kWarp * warp - lane;  // warp 0 lane 0: nearest
                     S v = op.identity();
                     unsigned f = kFlagInc;
-                    if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
-                    const bool err = __any_sync(0xffffffffu, f == kFlagError);
+                    if constexpr (tags_first<S>()) {
+                        if (tj >= 0) f = wait_tag(aggw + tj * SO, incw + tj * SO, ctl.spin_limit);
+                    } else {
+                        if (tj >= 0) f = wait_tile(aggw + tj * SO, incw + tj * SO, &v, ctl.spin_limit, WS);
+                    }
                     const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
                     const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
+                    bool bad = f == kFlagError;
+                    if constexpr (tags_first<S>()) {
+                        if (tj >= 0 && lane <= stop && !bad)
+                            bad = !read_tagged(f == kFlagInc ? incw + tj * SO : aggw + tj * SO, f, &v, ctl.spin_limit, WS);
+                    }
+                    const bool err = __any_sync(0xffffffffu, bad);
                     if (lane > stop) v = op.identity();
 #pragma unroll
                     for (int o = 1; o < kWarp; o <<= 1) {  // ordered: farthest (highest lane) first
@@ -256,10 +368,10 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
                 }
                 if (tid == 0) {
                     if (abort) {
-                        publish_tag(incw + t * K, K, kFlagError);
+                        publish_tag(incw + t * SO, K, kFlagError, WS);
                         set_error(ctl.err, kErrTimeout);
                     } else {
-                        publish(incw + t * K, op.combine(prefix, s_total), kFlagInc);
+                        publish(incw + t * SO, op.combine(prefix, s_total), kFlagInc, WS);
                     }
                 }
             } else {
@@ -335,6 +447,8 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
     constexpr int TILE = THREADS * ITEMS;
     constexpr int NW = THREADS / kWarp;
     constexpr int K = Tagged<S>::K;
+    constexpr int64_t SO = tags_first<S>() ? 1 : K;          // slot offset of a tile
+    const int64_t WS = tags_first<S>() ? num_tiles : 1;      // word stride (word-major for large states)
     constexpr bool KEEP = keep_prefix<Op>(0);
     constexpr int KT = KEEP ? keep_tiles<S, THREADS>() : 1;
     constexpr int MT = KEEP ? KT : range_max_tiles<S>();  // KEEP ranges are at most KT tiles
@@ -431,16 +545,16 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
     if (r == ctl.stall_tile) {  // fault injection: this range never publishes
         abort = true;
     } else {
-        if (tid == 0) publish(aggw + r * K, range_agg, kFlagAgg);
+        if (tid == 0) publish(aggw + r * SO, range_agg, kFlagAgg, WS);
         if (r == 0) {
-            if (tid == 0) publish(incw, range_agg, kFlagInc);
+            if (tid == 0) publish(incw, range_agg, kFlagInc, WS);
         } else {
             long long base = r - 1;
             while (true) {
                 const long long tj = base - (long long)kWarp * warp - lane;
                 S v = op.identity();
                 unsigned f = kFlagInc;
-                if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
+                if (tj >= 0) f = wait_tile(aggw + tj * SO, incw + tj * SO, &v, ctl.spin_limit, WS);
                 const bool err = __any_sync(0xffffffffu, f == kFlagError);
                 const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
                 const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
@@ -474,10 +588,10 @@ k_scan_ranges(const Op op, const int64_t n, const int64_t num_tiles, unsigned lo
             }
             if (tid == 0) {
                 if (abort) {
-                    publish_tag(incw + r * K, K, kFlagError);
+                    publish_tag(incw + r * SO, K, kFlagError, WS);
                     set_error(ctl.err, kErrTimeout);
                 } else {
-                    publish(incw + r * K, op.combine(prefix, range_agg), kFlagInc);
+                    publish(incw + r * SO, op.combine(prefix, range_agg), kFlagInc, WS);
                 }
             }
         }
@@ -552,7 +666,7 @@ inline ScanWs scan_ws_layout(int64_t num_tiles, size_t state_bytes) {
 constexpr int kScanThreads = 256;
 
 template <class Op, int ITEMS> struct ScanShape {
-    static constexpr int TILE = kScanThreads * ITEMS;
+    static constexpr int TILE = op_threads<Op>(0) * ITEMS;
     static int64_t tiles(int64_t n) { return (n + TILE - 1) / TILE; }
     static size_t region(int64_t n) { return scan_ws_layout(tiles(n), sizeof(typename Op::State)).bytes; }
 };
@@ -598,7 +712,14 @@ adc_status run_scan(const Op &op, int64_t n, void *ws, int slot, void *region, c
     if (cudaMemsetAsync(w, 0, L.bytes, s) != cudaSuccess) return ADC_ERR_CUDA;
     const DevCtl ctl = make_ctl(ws, slot);
     if constexpr (per_tile_only<Op>(0)) {
-        k_scan<Op, kScanThreads, ITEMS, REVERSE><<<(unsigned)T, kScanThreads, 0, s>>>(
+        constexpr int TH = op_threads<Op>(0);
+        constexpr size_t dyn = op_dyn_smem<Op>(0);
+        if constexpr (dyn > 0) {
+            if (cudaFuncSetAttribute(k_scan<Op, TH, ITEMS, REVERSE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)dyn) != cudaSuccess)
+                return ADC_ERR_CUDA;
+        }
+        k_scan<Op, TH, ITEMS, REVERSE><<<(unsigned)T, TH, dyn, s>>>(
             op, n, T, reinterpret_cast<unsigned long long *>(w + L.agg_off),
             reinterpret_cast<unsigned long long *>(w + L.inc_off), ctl);
         return check_launch();

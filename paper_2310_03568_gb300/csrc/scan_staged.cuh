@@ -75,6 +75,8 @@ k_scan_staged(const Op op, const int64_t n, const int64_t num_tiles, const int r
     constexpr int TILE = THREADS * ITEMS;
     constexpr int NW = THREADS / kWarp;
     constexpr int K = Tagged<S>::K;
+    constexpr int64_t SO = tags_first<S>() ? 1 : K;          // slot offset of a tile
+    const int64_t WS = tags_first<S>() ? num_tiles : 1;      // word stride (word-major for large states)
     constexpr int NS = Op::kStreams;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) unsigned long long s_bar[2][kStageGroups];
@@ -199,7 +201,7 @@ k_scan_staged(const Op op, const int64_t n, const int64_t num_tiles, const int r
         if (s_abort) {
             abort = true;
             if (tid == 0) {
-                publish_tag(incw + r * K, K, kFlagError);
+                publish_tag(incw + r * SO, K, kFlagError, WS);
                 set_error(ctl.err, kErrTimeout);
             }
             break;
@@ -228,16 +230,16 @@ k_scan_staged(const Op op, const int64_t n, const int64_t num_tiles, const int r
         if (r == ctl.stall_tile) {  // fault injection: this range never publishes
             abort = true;
         } else {
-            if (tid == 0) publish(aggw + r * K, range_agg, kFlagAgg);
+            if (tid == 0) publish(aggw + r * SO, range_agg, kFlagAgg, WS);
             if (r == 0) {
-                if (tid == 0) publish(incw, range_agg, kFlagInc);
+                if (tid == 0) publish(incw, range_agg, kFlagInc, WS);
             } else {
                 long long base = r - 1;
                 while (true) {
                     const long long tj = base - (long long)kWarp * warp - lane;
                     S v = op.identity();
                     unsigned f = kFlagInc;
-                    if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
+                    if (tj >= 0) f = wait_tile(aggw + tj * SO, incw + tj * SO, &v, ctl.spin_limit, WS);
                     const bool err = __any_sync(0xffffffffu, f == kFlagError);
                     const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
                     const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
@@ -271,10 +273,10 @@ k_scan_staged(const Op op, const int64_t n, const int64_t num_tiles, const int r
                 }
                 if (tid == 0) {
                     if (abort) {
-                        publish_tag(incw + r * K, K, kFlagError);
+                        publish_tag(incw + r * SO, K, kFlagError, WS);
                         set_error(ctl.err, kErrTimeout);
                     } else {
-                        publish(incw + r * K, op.combine(prefix, range_agg), kFlagInc);
+                        publish(incw + r * SO, op.combine(prefix, range_agg), kFlagInc, WS);
                     }
                 }
             }

@@ -49,6 +49,8 @@ k_scan_tma(const Op op, const int64_t n, const int64_t num_tiles, unsigned long 
     constexpr int TILE = kTmaSubTiles * SUB;
     constexpr int NW = THREADS / kWarp;
     constexpr int K = Tagged<S>::K;
+    constexpr int64_t SO = tags_first<S>() ? 1 : K;          // slot offset of a tile
+    const int64_t WS = tags_first<S>() ? num_tiles : 1;      // word stride (word-major for large states)
     constexpr int NS = Op::kStreams;
     constexpr int NE = kTmaSubTiles * NW;        // (sub-tile, warp) entries in logical order
     constexpr int EPL = (NE + kWarp - 1) / kWarp;  // entries per lane of warp 0
@@ -114,7 +116,7 @@ k_scan_tma(const Op op, const int64_t n, const int64_t num_tiles, unsigned long 
     };
     if (!__syncthreads_and(mbar_wait_bounded(&s_bar, 0u, ctl.spin_limit))) {
         if (tid == 0) {
-            publish_tag(incw + t * K, K, kFlagError);
+            publish_tag(incw + t * SO, K, kFlagError, WS);
             set_error(ctl.err, kErrTimeout);
             mbar_wait_bounded(&s_bar, 0u, ctl.spin_limit);  // a second chance for the copy to land
         }
@@ -159,16 +161,16 @@ k_scan_tma(const Op op, const int64_t n, const int64_t num_tiles, unsigned long 
     if (t == ctl.stall_tile) {  // fault injection: this tile never publishes
         abort = true;
     } else {
-        if (tid == 0) publish(aggw + t * K, tile_agg, kFlagAgg);
+        if (tid == 0) publish(aggw + t * SO, tile_agg, kFlagAgg, WS);
         if (t == 0) {
-            if (tid == 0) publish(incw, tile_agg, kFlagInc);
+            if (tid == 0) publish(incw, tile_agg, kFlagInc, WS);
         } else {
             long long base = t - 1;
             while (true) {
                 const long long tj = base - (long long)kWarp * warp - lane;
                 S v = op.identity();
                 unsigned f = kFlagInc;
-                if (tj >= 0) f = wait_tile(aggw + tj * K, incw + tj * K, &v, ctl.spin_limit);
+                if (tj >= 0) f = wait_tile(aggw + tj * SO, incw + tj * SO, &v, ctl.spin_limit, WS);
                 const bool err = __any_sync(0xffffffffu, f == kFlagError);
                 const unsigned incmask = __ballot_sync(0xffffffffu, f == kFlagInc);
                 const int stop = incmask ? (__ffs(incmask) - 1) : (kWarp - 1);
@@ -202,10 +204,10 @@ k_scan_tma(const Op op, const int64_t n, const int64_t num_tiles, unsigned long 
             }
             if (tid == 0) {
                 if (abort) {
-                    publish_tag(incw + t * K, K, kFlagError);
+                    publish_tag(incw + t * SO, K, kFlagError, WS);
                     set_error(ctl.err, kErrTimeout);
                 } else {
-                    publish(incw + t * K, op.combine(prefix, tile_agg), kFlagInc);
+                    publish(incw + t * SO, op.combine(prefix, tile_agg), kFlagInc, WS);
                 }
             }
         }

@@ -33,11 +33,14 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
                  "l"(src), "r"(bytes), "r"(smem_u32(bar))
                  : "memory");
 }
-// Bounded wait for the phase of the given parity; false if the limit ran out.
+// Bounded wait for the phase of the given parity (polls with a short sleep
+// between them, so waiting warps leave the shared-memory pipe to the others);
+// false if the limit ran out.
 __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long *bar, uint32_t parity, long long limit) {
     long long it = 0;
     while (!mbar_try_wait(bar, parity)) {
         if (++it > limit) return false;
+        __nanosleep(32);
     }
     return true;
 }

@@ -52,6 +52,33 @@ def test_stalled_tile_times_out_and_context_survives(op, stall, engine):
     np.testing.assert_allclose(host(y).reshape(ref.shape), ref, rtol=1e-3, atol=1e-2)
 
 
+@pytest.mark.parametrize("op", ["mm3", "mm5"])
+def test_bulk_staged_matrix_scan_stall_times_out(op):
+    """The bulk-staged matrix segment scans (forward, and the vjp's reverse
+    scan): the stalled tile's block still waits for its own bulk copies before
+    it leaves, the tiles after it time out, and the context survives."""
+    g = np.random.default_rng(10)
+    n = 60_000
+    x = synth.scan_values(g, op + "_orth", n)
+    yb = synth.normal(g, x.shape)
+    xd, ybd = dev(x), dev(yb)
+    y = adcomb.scan_fwd(op, xd)
+    ws = adcomb.Workspace()
+    for call in (lambda: adcomb.scan_fwd(op, xd, ws=ws), lambda: adcomb.scan_vjp(op, xd, y, ybd, ws=ws)):
+        try:
+            adcomb.set_spin_limit(2000)
+            adcomb.debug_set_stall_tile(3)
+            call()
+            assert adcomb.check_device_error(ws) == 5
+        finally:
+            adcomb.debug_set_stall_tile(-1)
+            adcomb.set_spin_limit(0)
+    xb = adcomb.scan_vjp(op, xd, y, ybd, ws=ws)
+    assert adcomb.check_device_error(ws) == 0
+    ref = oracle.scan_vjp(op, x, yb)
+    np.testing.assert_allclose(host(xb).reshape(ref.shape), ref, rtol=1e-3, atol=1e-2)
+
+
 def test_reverse_scan_stall_times_out():
     g = np.random.default_rng(9)
     n = 150_000

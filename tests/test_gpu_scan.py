@@ -201,17 +201,21 @@ def test_mm2_scan_full_size(op):
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("engine_id", [0, 1, 2], ids=["auto", "per-tile", "ranges"])
+@pytest.mark.parametrize("engine_id", [0, 1, 2, 6], ids=["auto", "per-tile", "ranges", "bulk-staged"])
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 @pytest.mark.parametrize("op", ["mm3", "mm5"])
 def test_mmq_scan(op, dt, engine_id):
     """q x q matrix-product scans (q = 3, 5): forward and the RBDS vjp with
-    M_{i+1}^T, at sizes spanning several tiles (forward tiles of 1024 / 512 /
-    256 matrices, vjp tiles of 256) and ragged tails."""
+    M_{i+1}^T, at sizes spanning several tiles and ragged tails.  Automatic
+    and hook 6: the bulk-staged segment forms (runs of 7 / 5 matrices, tiles
+    of 896 / 448 (3x3) and 640 / 320 / 160 (5x5) matrices); hooks 1 and 2:
+    the register forms (3x3 forward tiles of 1024 / 512 matrices, segment
+    runs of 8 in blocks of 256)."""
     g = np.random.default_rng(31 + len(op))
     try:
         adcomb.debug_set_scan_engine(engine_id)
-        for n in [0, 1, 2, 33, 255, 256, 257, 1025, 3 * 1024 + 1, 20_003]:
+        for n in [0, 1, 2, 7, 8, 9, 33, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 3 * 1024 + 1, 20_003,
+                  100_003]:
             x = make_x(g, op, n, dt)
             check_scan(op, x, synth.normal(g, x.shape, dt), dt)
         x = make_x(g, op, 3001, dt)
