@@ -1,6 +1,8 @@
 // Device-side building blocks shared by the libadcomb kernels (sm_103a).
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -198,15 +200,32 @@ template <typename S> __device__ __forceinline__ S shfl_idx(const S &v, int lane
     return out;
 }
 
+// v <- combine(v of lane (lane - o), v) where `active`: an Op with a large
+// state may provide shfl_combine(v, o, down, active) doing the shuffles and
+// the combine piecewise (fewer live registers than the whole shuffled state
+// plus the result); down = true takes the value of lane (lane + o) instead.
+template <class Op, typename S> constexpr bool has_shfl_combine(long) { return false; }
+template <class Op, typename S>
+constexpr auto has_shfl_combine(int)
+    -> decltype(std::declval<const Op &>().shfl_combine(std::declval<S &>(), 0, true, true), bool()) {
+    return true;
+}
+template <class Op, typename S>
+__device__ __forceinline__ void shfl_combine(const Op &op, S &v, int o, bool down, bool active) {
+    if constexpr (has_shfl_combine<Op, S>(0)) {
+        op.shfl_combine(v, o, down, active);
+    } else {
+        const S other = down ? shfl_down(v, o) : shfl_up(v, o);
+        if (active) v = op.combine(other, v);
+    }
+}
+
 // Inclusive warp scan in lane order for an associative (not necessarily
 // commutative) operator: lane l ends with x_0 . x_1 . ... . x_l.
 template <class Op, typename S> __device__ __forceinline__ S warp_inclusive_scan(const Op &op, S v) {
     const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        S up = shfl_up(v, o);
-        if (lane >= o) v = op.combine(up, v);
-    }
+    for (int o = 1; o < 32; o <<= 1) shfl_combine(op, v, o, false, lane >= o);
     return v;
 }
 

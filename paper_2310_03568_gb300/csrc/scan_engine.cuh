@@ -70,6 +70,12 @@ template <class Op> constexpr auto op_dyn_smem(int) -> decltype(Op::kDynSmem, si
 // the block leaves.
 template <class Op> constexpr bool bulk_staged(long) { return false; }
 template <class Op> constexpr auto bulk_staged(int) -> decltype(Op::kBulkStaged, bool()) { return Op::kBulkStaged; }
+// Such an Op may also finish its tile after store() (kFinish: e.g. stage a
+// further input into space store() has freed): every thread calls
+// op.finish(c0, n, limit), which returns false, alike in every thread, if a
+// bounded wait in it ran out; the engine then records kErrTimeout.
+template <class Op> constexpr bool op_finish(long) { return false; }
+template <class Op> constexpr auto op_finish(int) -> decltype(Op::kFinish, bool()) { return Op::kFinish; }
 // An Op may ask (kKeepPrefix) the range engine to keep, from phase A, every
 // thread's exclusive prefix within its warp for every tile of the range in
 // shared memory, so that phase B needs neither the thread folds nor the warp
@@ -340,10 +346,8 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
                     const bool err = __any_sync(0xffffffffu, bad);
                     if (lane > stop) v = op.identity();
 #pragma unroll
-                    for (int o = 1; o < kWarp; o <<= 1) {  // ordered: farthest (highest lane) first
-                        const S other = shfl_down(v, o);
-                        if (lane + o < kWarp) v = op.combine(other, v);
-                    }
+                    for (int o = 1; o < kWarp; o <<= 1)  // ordered: farthest (highest lane) first
+                        shfl_combine(op, v, o, true, lane + o < kWarp);
                     if (lane == 0) {
                         s_lbv[warp] = v;
                         s_lbinc[warp] = incmask != 0;
@@ -387,6 +391,9 @@ k_scan(const Op op, const int64_t n, const int64_t num_tiles, unsigned long long
                     st[kk] = exclusive_store<Op>(0) ? ex : run;
                 }
                 op.store(c0, n, st, aux);
+                if constexpr (op_finish<Op>(0)) {
+                    if (!op.finish(c0, n, ctl.spin_limit) && tid == 0) set_error(ctl.err, kErrTimeout);
+                }
             }
         }
     }

@@ -21,7 +21,9 @@
 // tile starts 16-byte aligned (the API requires 16-byte aligned arrays).
 // Elements outside the array are never read from it: the vjp's x_n (after the
 // last element) and y_{-1} (before the first) are the identity, written into
-// the stage by thread 0.
+// the stage by thread 0.  Every wait on a copy is bounded (the engine's spin
+// limit); a block whose wait runs out gives the copy a second bounded wait
+// before it leaves, and the call reports a timeout.
 #pragma once
 
 #include <stdint.h>
@@ -180,10 +182,14 @@ template <typename T, int Q, int TH, int SEG> struct StagedFwdMMQ {
 
 // vjp (reverse): the run's state composes f_i(L) = Ybar_i + L M_{i+1}^T from
 // its last element down; the re-walk applies lambda_i = Ybar_i + lambda_{i+1}
-// M_{i+1}^T from the incoming lambda and writes Mbar_i = P_{i-1}^T lambda_i
-// over the staged Ybar_i.
-// Stage: [mbarrier: 16 B][x_e, e = e0 .. e0 + TE (one past the tile): TB + H]
-//        [y_e, e = e0 - 1 .. e0 + TE - 1 (one before): H + TB][ybar: TB].
+// M_{i+1}^T from the incoming lambda and writes lambda_i over the staged
+// Ybar_i.  y is needed only for the last step, Mbar_i = P_{i-1}^T lambda_i:
+// finish() bulk-copies the tile's y (one element before it included) into
+// the x stage the re-walk has freed, and the block then forms Mbar_i one
+// element per thread (odd word strides again) and copies it out.  Two arrays
+// in shared memory instead of three: three blocks fit an SM instead of two.
+// Stage: [mbarriers: 16 B][x_e, e = e0 .. e0 + TE (one past the tile), later
+//        y_e, e = e0 - 1 .. e0 + TE - 1: TB + H][ybar, then lambda, then Mbar: TB].
 template <typename T, int Q, int TH, int SEG> struct StagedVjpMMQ {
     using G = MMQGeom<T, Q, TH, SEG>;
     using E = MatQ<T, Q>;
@@ -193,10 +199,10 @@ template <typename T, int Q, int TH, int SEG> struct StagedVjpMMQ {
     static constexpr bool kExclusiveStore = true;
     static constexpr bool kPerTileOnly = true;
     static constexpr bool kBulkStaged = true;
+    static constexpr bool kFinish = true;
     static constexpr int kThreads = TH;
     static constexpr size_t kOffX = 16;
-    static constexpr size_t kOffY = kOffX + G::TB + G::H;
-    static constexpr size_t kOffG = kOffY + G::H + G::TB;
+    static constexpr size_t kOffG = kOffX + G::TB + G::H;
     static constexpr size_t kDynSmem = kOffG + G::TB;
     const E *x, *y, *ybar;
     E *xbar;
@@ -206,24 +212,54 @@ template <typename T, int Q, int TH, int SEG> struct StagedVjpMMQ {
     __device__ State combine(const State &acc, const State &e) const {
         return {matq_add(e.v, matq_mul(acc.v, e.c)), matq_mul(acc.c, e.c)};
     }
+    // The scans' combine, piecewise: v <- combine(other, v) with `other` the
+    // state of lane (lane -/+ o), fetched one row at a time -- new v = v.v +
+    // other.v v.c, new c = other.c v.c -- so that about three matrices are
+    // live instead of six (the 5x5 fp32 state is 50 words).
+    __device__ void shfl_combine(State &s, int o, bool down, bool active) const {
+        E nc;
+#pragma unroll
+        for (int i = 0; i < Q; ++i) {
+            T ov[Q], oc[Q];
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                ov[j] = down ? __shfl_down_sync(0xffffffffu, s.v.a[Q * i + j], o)
+                             : __shfl_up_sync(0xffffffffu, s.v.a[Q * i + j], o);
+                oc[j] = down ? __shfl_down_sync(0xffffffffu, s.c.a[Q * i + j], o)
+                             : __shfl_up_sync(0xffffffffu, s.c.a[Q * i + j], o);
+            }
+#pragma unroll
+            for (int j = 0; j < Q; ++j) {
+                T av = s.v.a[Q * i + j], ac = T(0);
+#pragma unroll
+                for (int k = 0; k < Q; ++k) {
+                    av += ov[k] * s.c.a[Q * k + j];
+                    ac += oc[k] * s.c.a[Q * k + j];
+                }
+                nc.a[Q * i + j] = active ? ac : s.c.a[Q * i + j];
+                if (active) s.v.a[Q * i + j] = av;  // row i of v is read by no later row
+            }
+        }
+        s.c = nc;
+    }
+    // two mbarriers: the inputs of build() / store(), then y for finish()
+    __device__ unsigned long long *bar(int i) const { return mmq_stage_bar() + i; }
     __device__ void stage_init() const {
-        mbar_init(mmq_stage_bar(), 1);
+        mbar_init(bar(0), 1);
+        mbar_init(bar(1), 1);
         mbar_init_fence();
     }
-    __device__ bool staged_wait(long long limit) const { return mbar_wait_bounded(mmq_stage_bar(), 0u, limit); }
+    __device__ bool staged_wait(long long limit) const { return mbar_wait_bounded(bar(0), 0u, limit); }
     __device__ void fetch(int64_t c0, int64_t, Raw &) const {
         if (threadIdx.x != 0) return;
         const int64_t e0 = (c0 / TH) * (int64_t)G::TE;
         const int64_t o = e0 * G::B, nb = n * G::B;
-        const StageSpan sx(o, o + G::TB + G::H, nb), sy(o - G::H, o + G::TB, nb), sg(o, o + G::TB, nb);
+        const StageSpan sx(o, o + G::TB + G::H, nb), sg(o, o + G::TB, nb);
         char *base = mmq_stage_base();
-        unsigned long long *bar = mmq_stage_bar();
-        mbar_expect_tx(bar, sx.bulk_bytes() + sy.bulk_bytes() + sg.bulk_bytes());
-        sx.issue(base + kOffX, reinterpret_cast<const char *>(x), o, bar);
-        sy.issue(base + kOffY, reinterpret_cast<const char *>(y), o - G::H, bar);
-        sg.issue(base + kOffG, reinterpret_cast<const char *>(ybar), o, bar);
-        // identities outside the array (bytes no copy above writes)
-        if (e0 == 0) put_eye<T, Q>(reinterpret_cast<T *>(base + kOffY + G::H - G::B));
+        mbar_expect_tx(bar(0), sx.bulk_bytes() + sg.bulk_bytes());
+        sx.issue(base + kOffX, reinterpret_cast<const char *>(x), o, bar(0));
+        sg.issue(base + kOffG, reinterpret_cast<const char *>(ybar), o, bar(0));
+        // x_n (after the last element) is the identity (bytes no copy above writes)
         if (n - e0 <= G::TE) put_eye<T, Q>(reinterpret_cast<T *>(base + kOffX + (n - e0) * G::B));
     }
     __device__ void build(int64_t c0, int64_t items, const Raw &, State (&st)[1], Aux &) const {
@@ -246,53 +282,76 @@ template <typename T, int Q, int TH, int SEG> struct StagedVjpMMQ {
         st[0] = s;
     }
     __device__ void store(int64_t c0, int64_t items, const State (&ex)[1], const Aux &) const {
-        T *sg0 = reinterpret_cast<T *>(mmq_stage_base() + kOffG);
-        if (c0 < items) {
-            const int le = (int)(c0 % TH) * SEG;
-            const T *sx = reinterpret_cast<const T *>(mmq_stage_base() + kOffX) + le * G::QQ;
-            // y_{i-1} sits one element before y_i's slot, which is H bytes into the y stage
-            const T *sy = reinterpret_cast<const T *>(mmq_stage_base() + kOffY + G::H - G::B) + le * G::QQ;
-            T *sg = sg0 + le * G::QQ;
-            const int64_t lo = c0 * SEG;
-            const int cnt = (int)((lo + SEG < n) ? SEG : n - lo);
-            E lam = ex[0].v;
-            for (int k = cnt - 1; k >= 0; --k) {
-                matq_mul_right_t(lam, ld_matq<T, Q>(sx + (k + 1) * G::QQ));
+        if (c0 >= items) return;
+        const int le = (int)(c0 % TH) * SEG;
+        const T *sx = reinterpret_cast<const T *>(mmq_stage_base() + kOffX) + le * G::QQ;
+        T *sg = reinterpret_cast<T *>(mmq_stage_base() + kOffG) + le * G::QQ;
+        const int64_t lo = c0 * SEG;
+        const int cnt = (int)((lo + SEG < n) ? SEG : n - lo);
+        E lam = ex[0].v;
+        for (int k = cnt - 1; k >= 0; --k) {
+            matq_mul_right_t(lam, ld_matq<T, Q>(sx + (k + 1) * G::QQ));
 #pragma unroll
-                for (int q = 0; q < G::QQ; ++q) lam.a[q] += sg[k * G::QQ + q];
-                const E P = ld_matq<T, Q>(sy + k * G::QQ);
-                // Mbar_i = P_{i-1}^T lambda_i, into this thread's own ybar slots
+            for (int q = 0; q < G::QQ; ++q) {
+                lam.a[q] += sg[k * G::QQ + q];
+                sg[k * G::QQ + q] = lam.a[q];  // this thread's own slots
+            }
+        }
+    }
+    __device__ bool finish(int64_t c0, int64_t, long long limit) const {
+        const int64_t e0 = (c0 / TH) * (int64_t)G::TE;
+        const int64_t ne = (n - e0 < G::TE) ? n - e0 : G::TE;
+        char *base = mmq_stage_base();
+        __syncthreads();  // every re-walk is done with the x stage
+        if (threadIdx.x == 0) {
+            const int64_t o = e0 * G::B;
+            const StageSpan sy(o - G::H, o + G::TB, n * G::B);
+            fence_proxy_async_smem();  // the walks' reads of the x stage come before the copy's writes
+            mbar_expect_tx(bar(1), sy.bulk_bytes());
+            sy.issue(base + kOffX, reinterpret_cast<const char *>(y), o - G::H, bar(1));
+            // y_{-1} (before the first element) is the identity
+            if (e0 == 0) put_eye<T, Q>(reinterpret_cast<T *>(base + kOffX + G::H - G::B));
+        }
+        if (!__syncthreads_and(mbar_wait_bounded(bar(1), 0u, limit))) {
+            if (threadIdx.x == 0) mbar_wait_bounded(bar(1), 0u, limit);  // a second chance for the copy to land
+            return false;
+        }
+        // Mbar_i = P_{i-1}^T lambda_i, one element per thread, in place of lambda_i
+        const T *py = reinterpret_cast<const T *>(base + kOffX + G::H - G::B);  // y_{i-1} at element slot i
+        T *sg = reinterpret_cast<T *>(base + kOffG);
+        for (int e = threadIdx.x; e < (int)ne; e += TH) {
+            const E P = ld_matq<T, Q>(py + e * G::QQ);
+            const E lam = ld_matq<T, Q>(sg + e * G::QQ);
 #pragma unroll
-                for (int r = 0; r < Q; ++r) {
+            for (int r = 0; r < Q; ++r) {
 #pragma unroll
-                    for (int j = 0; j < Q; ++j) {
-                        T g = P.a[r] * lam.a[j];
+                for (int j = 0; j < Q; ++j) {
+                    T g = P.a[r] * lam.a[j];
 #pragma unroll
-                        for (int q = 1; q < Q; ++q) g += P.a[Q * q + r] * lam.a[Q * q + j];
-                        sg[k * G::QQ + Q * r + j] = g;
-                    }
+                    for (int q = 1; q < Q; ++q) g += P.a[Q * q + r] * lam.a[Q * q + j];
+                    sg[e * G::QQ + Q * r + j] = g;
                 }
             }
         }
-        __syncthreads();  // every run's adjoints are in the stage
-        const int64_t e0 = (c0 / TH) * (int64_t)G::TE;
-        const int64_t ne = (n - e0 < G::TE) ? n - e0 : G::TE;
-        copy_out<T, TH>(reinterpret_cast<T *>(xbar + e0), sg0, ne * G::B, accumulate != 0);
+        __syncthreads();  // every adjoint is in the stage
+        copy_out<T, TH>(reinterpret_cast<T *>(xbar + e0), sg, ne * G::B, accumulate != 0);
+        return true;
     }
 };
 
-// Block size and run length per (type, q, direction): a tile of about 32 KB
-// per array for the vjps (three arrays: two blocks fit an SM's shared
-// memory) and 64 KB for the one-array forwards.  Larger tiles mean fewer
-// look-backs, which bound these scans; measured at n = 1e7 (3x3) / 4e6 (5x5)
-// fp32 over threads x run in {32..256} x {3, 5, 7}: 3x3 forward 256 x 7
-// (0.24 ms; 128 x 7: 0.27), 3x3 vjp 128 x 7 (0.56; 128 x 5: 0.63, 64 x 7:
-// 0.69), 5x5 forward 128 x 5 (0.35; 256 x 3: 0.37), 5x5 vjp 64 x 5 (1.38;
-// 64 x 3 and 32 x 5: 2.1).  The fp64 q = 5 vjp is one warp per block.
+// Block size and run length per (type, q, direction).  Larger tiles mean
+// fewer look-backs, which bound these scans, until shared memory (two staged
+// arrays for the vjps, one for the forwards) or registers leave fewer than
+// two blocks per SM.  Measured at n = 1e7 (3x3) / 4e6 (5x5) fp32 over
+// threads x run in {32..384} x {3, 5, 7}: 3x3 forward 384 x 7 (0.22 ms;
+// 256 x 7: 0.24, 128 x 7: 0.27), 3x3 vjp 224 x 7 (0.40; 192 x 7: 0.44,
+// 128 x 7: 0.51), 5x5 forward 160 x 7 (0.28; 128 x 7: 0.31, 128 x 5: 0.35),
+// 5x5 vjp 96 x 5 (1.03; 64 x 7: 1.09, 64 x 5: 1.31).  fp64 (bound by the FP64 pipe) takes tiles of the
+// same bytes.
 template <typename T, int Q, bool VJP> struct MMQStaged {
-    static constexpr int seg = Q == 3 ? 7 : 5;
-    static constexpr int threads = VJP ? (Q == 3 ? (sizeof(T) == 4 ? 128 : 64) : (sizeof(T) == 4 ? 64 : 32))
-                                       : (Q == 3 ? (sizeof(T) == 4 ? 256 : 128) : (sizeof(T) == 4 ? 128 : 64));
+    static constexpr int seg = Q == 3 || !VJP ? 7 : 5;
+    static constexpr int threads = VJP ? (Q == 3 ? (sizeof(T) == 4 ? 224 : 96) : (sizeof(T) == 4 ? 96 : 32))
+                                       : (Q == 3 ? (sizeof(T) == 4 ? 384 : 128) : (sizeof(T) == 4 ? 160 : 64));
 };
 
 }  // namespace adc
