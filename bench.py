@@ -560,7 +560,8 @@ def run_families(dev, peak):
     """The workloads beside the headline, each timed on its own at full size:
     the small reduce-by-index workload (n = 1e5), the scans (n = 1e8 fp32,
     1e7 fp64), the specialised reduces at 1e8, the 2x2 matrix scan and
-    reduce at 1e7, and linFnComp reduce-by-index at 1e7 / m = 1000.  Inputs are
+    reduce at 1e7, the 3x3 (1e7) and 5x5 (4e6) matrix scans, and linFnComp
+    reduce-by-index at 1e7 / m = 1000.  Inputs are
     seeded and drawn on the device with the workloads' distributions."""
     import torch
 
@@ -652,6 +653,16 @@ def run_families(dev, peak):
     b = time_calls(lambda: adcomb.reduce_vjp("mm2", x, yr, rs, ybr, xbar=xb, ws=ws), flush)
     gen_fam["reduce_mm2"] = family_entry(n, f, b, 16 * n, 32 * n, 16 * n, peak)
     del x, y, yb, xb
+    # q x q matrix scans (Sec. 5.3.4's q > 2 case): 3x3 at 1e7, 5x5 at 4e6, entries U(-1, 1) / sqrt(q)
+    for op, nq, q in (("mm3", 10_000_000, 3), ("mm5", 4_000_000, 5)):
+        x = (U((nq, q * q), -1, 1) / np.sqrt(q)).contiguous()
+        y = adcomb.scan_fwd(op, x, ws=ws)
+        yb, xb = Nrm(x.shape), torch.empty_like(x)
+        f = time_calls(lambda: adcomb.scan_fwd(op, x, y, ws=ws), flush)
+        b = time_calls(lambda: adcomb.scan_vjp(op, x, y, yb, xbar=xb, ws=ws), flush)
+        es = 4 * q * q  # bytes per matrix
+        gen_fam[f"scan_{op}"] = family_entry(nq, f, b, 2 * es * nq, 4 * es * nq, 2 * es * nq, peak)
+        del x, y, yb, xb
     m = 1000
     k = torch.randint(0, m, (n,), generator=gen, device=dev, dtype=torch.int32)
     v = scan_x("lin", n, torch.float32)
