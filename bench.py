@@ -879,7 +879,7 @@ def run_kernels(args):
                 row(f"bench {op} m={m} fwd", NB, 8 * NB,
                     timeit(lambda: adcomb.hist_fwd(op, m, k, v, None, h, saved, ws=ws)))
                 if op != "mul" and 200 * 1024 < m * 8 <= 8 * 200 * 1024:
-                    for strat, label in [(2, "global"), (6, "cluster"), (7, "two passes")]:
+                    for strat, label in [(2, "global"), (6, "cluster"), (7, "two passes"), (8, "pairs")]:
                         adcomb.debug_force_hist_strategy(strat)
                         ws.get(adcomb.workspace_bytes("hist", op, torch.float32, NB, m), dev)
                         row(f"bench {op} m={m} fwd [{label}]", NB, 8 * NB,

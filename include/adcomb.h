@@ -452,7 +452,9 @@ void adc_debug_set_batched_items(int items);
  * range into shared-memory-sized buckets, 5: lifted fp32 min/max split over
  * 2-4 block tables, 6: lifted fp32 min/max spread over the shared memory of a
  * 2-8 block cluster, 7: lifted fp32 min/max by per-block value tables and an
- * index pass) where the histogram fits it; -1
+ * index pass, 8: lifted fp32 min/max by pairs of blocks holding half the bins
+ * as value and index tables, never chosen automatically) where the histogram
+ * fits it; -1
  * (default) chooses automatically from m and the operator.  The choice also
  * applies to the original primal (saved == NULL).
  */

@@ -11,7 +11,10 @@ fp64 oracle over the whole input (marked slow).
 * the specialised reduces (Sec. 3.2) at n = 1e8, where every block of the
   single-pass reduce folds many tiles and the last-block combine folds one
   partial per block;
-* linFnComp reduce-by-index (Sec. 4.1, Fig. 4) at n = 1e7, m = 1000, with hist0.
+* linFnComp reduce-by-index (Sec. 4.1, Fig. 4) at n = 1e7, m = 1000, with hist0;
+* the q x q matrix scans (Sec. 5.3.4) at the bench's sizes, 3x3 at n = 1e7 and
+  5x5 at n = 4e6 (thousands of bulk-staged tiles, so the look-back runs over
+  many steps), forward and vjp with accumulate.
 """
 import numpy as np
 import pytest
@@ -23,6 +26,7 @@ from tests._gpu import dev, ensure_lib, host
 from tests._tol import assert_tol, prefix_max, rowabs, rtol_for, suffix_max
 from tests.test_gpu_hist import bin_stats, lin_bin_scales
 from tests.test_gpu_reduce import suffix_partials
+from tests.test_gpu_scan import check_scan
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -151,3 +155,12 @@ def test_hist_lin_full():
     vr, h0r = oracle.hist_vjp("lin", m, k, v, hb, h0)
     assert_tol("hist lin vjp", host(vb), vr, pop[k] + 1, 3 * A[k] * R[k] * rowabs(hb)[k], rtol)
     assert_tol("hist lin hist0bar", host(h0b), h0r, pop + 1, 3 * A * R * rowabs(hb), rtol)
+
+
+@pytest.mark.parametrize("op,n", [("mm3", 10_000_000), ("mm5", 4_000_000)])
+def test_mmq_scan_full(op, n):
+    """Forward and vjp (with accumulate) against the oracle over the whole input,
+    in the launch configuration the bench times (the automatic choice)."""
+    g = np.random.default_rng(150 + len(op))
+    x = synth.scan_values(g, op + "_orth", n)
+    check_scan(op, x, synth.normal(g, x.shape, np.float32), np.float32, accumulate=True)

@@ -56,8 +56,8 @@ def bin_partial_products(k, v, m):
     return np.exp(out)
 
 
-STRATS = [-1, 0, 1, 2, 3, 4, 5, 6, 7]  # auto, per-warp, per-block, global, per-thread, partitioned, split,
-                                       # cluster, two passes
+STRATS = [-1, 0, 1, 2, 3, 4, 5, 6, 7, 8]  # auto, per-warp, per-block, global, per-thread, partitioned, split,
+                                          # cluster, two passes, block pairs
 
 
 def fits(op, dt, m, s):
@@ -72,7 +72,7 @@ def fits(op, dt, m, s):
         return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 4 * 200 * 1024
     if s == 6:  # the same spread over the blocks of a 2-8 block cluster
         return op in ("min", "max") and sz == 4 and 200 * 1024 < m * 8 <= 8 * 200 * 1024
-    if s == 7:  # value tables per block, then an index pass
+    if s in (7, 8):  # value tables per block, then an index pass; block pairs with value and index tables
         return op in ("min", "max") and sz == 4 and m * 8 > 200 * 1024 and m * 4 <= 200 * 1024
     e = {"add": sz, "mul": sz + 4, "min": 8, "max": 8}[op]
     if s == 3:
@@ -84,9 +84,10 @@ def fits(op, dt, m, s):
     return True
 
 
-# the last case is large enough for the automatic choice to partition by bin range
+# the last case is large enough for the automatic choice to partition by bin range; m = 25,601 and
+# 51,199 bound the range where lifted fp32 min/max tables need two blocks (odd halves), n = 5 the tail
 CASES = [(0, 7), (1, 1), (33, 5), (4097, 31), (100_003, 401), (100_003, 5000), (300_001, 50_000),
-         (3_000_001, 2_000_003)]
+         (5, 30_000), (100_001, 25_601), (400_003, 51_199), (3_000_001, 2_000_003)]
 
 
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
