@@ -98,6 +98,11 @@ adc_status vreduce_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void
 adc_status vreduce_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *saved,
                        const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s);
 adc_status vscan_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s);
+// rows of d equal lin / sumOfProd / 2x2 elements, scanned per element column
+size_t velem_ws_bytes(adc_op op, adc_dtype dt, int64_t d);
+adc_status velem_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s);
+adc_status velem_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
+                     void *xbar, int accumulate, void *ws, cudaStream_t s);
 adc_status vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
                      void *xbar, int accumulate, void *ws, cudaStream_t s);
 adc_status vhist_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t m, int64_t d, const int32_t *keys, const void *vals,

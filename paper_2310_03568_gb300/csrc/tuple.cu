@@ -207,9 +207,20 @@ static bool uniform_scalar(int k, const adc_op *ops) {
     return true;
 }
 
+// Rows whose k blocks are all lin, all sumOfProd or all 2x2 matrix products
+// are k element columns: the vectorised direct form scans them in place too.
+static bool uniform_elem(int k, const adc_op *ops) {
+    const adc_op op = ops[0];
+    if (op != ADC_OP_LIN && op != ADC_OP_SOP && op != ADC_OP_MM2) return false;
+    for (int c = 1; c < k; ++c)
+        if (ops[c] != op) return false;
+    return true;
+}
+
 size_t tscan_ws_bytes(int k, const adc_op *ops, adc_dtype dt, int64_t n, bool rows) {
     if (rows && k == 1) return scan_ws_bytes(ops[0], dt, n);
     if (rows && uniform_scalar(k, ops)) return vws_bytes(ADC_SCAN, ops[0], dt, n, 0, k);
+    if (rows && uniform_elem(k, ops)) return velem_ws_bytes(ops[0], dt, k);
     return tlayout(k, ops, dt, n, rows).bytes;
 }
 
@@ -325,6 +336,7 @@ adc_status tscan_fwd_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, con
                           cudaStream_t s) {
     if (k == 1) return scan_fwd(ops[0], dt, n, x, y, ws, s);  // one block: the rows are its elements
     if (uniform_scalar(k, ops)) return vscan_fwd(ops[0], dt, n, k, x, y, ws, s);
+    if (uniform_elem(k, ops)) return n > 0 ? velem_fwd(ops[0], dt, n, k, x, y, ws, s) : ADC_OK;
     char *w = static_cast<char *>(ws);
     const TLayout L = tlayout(k, ops, dt, n, true);
     const TupleDesc d = tdesc(k, ops, L);
@@ -345,6 +357,7 @@ adc_status tscan_vjp_rows(int k, const adc_op *ops, adc_dtype dt, int64_t n, con
                           const void *ybar, void *xbar, int accumulate, void *ws, cudaStream_t s) {
     if (k == 1) return scan_vjp(ops[0], dt, n, x, y, ybar, xbar, accumulate, ws, s);
     if (uniform_scalar(k, ops)) return vscan_vjp(ops[0], dt, n, k, x, y, ybar, xbar, accumulate, ws, s);
+    if (uniform_elem(k, ops)) return n > 0 ? velem_vjp(ops[0], dt, n, k, x, y, ybar, xbar, accumulate, ws, s) : ADC_OK;
     char *w = static_cast<char *>(ws);
     const TLayout L = tlayout(k, ops, dt, n, true);
     const TupleDesc d = tdesc(k, ops, L);

@@ -14,6 +14,7 @@
 // kernels on the d contiguous columns and transpose the results back.
 // Operators: ADD, MUL, MIN, MAX (scalar elements).
 #include <atomic>
+#include <cstring>
 #include "common.cuh"
 #include "hist_common.cuh"
 #include "internal.h"
@@ -141,8 +142,8 @@ static size_t vhist_direct_ws(int64_t m, int64_t d) {
 // each) per unit (a warp, or a block when d > 32): the unit folds and their
 // exclusive prefixes.
 constexpr int kVScanMaxBlocksPerSM = 8;
-static size_t vscan_states_bytes(int64_t d) {
-    return align_up((size_t)num_sms() * kVScanMaxBlocksPerSM * 8 * (size_t)d * 16, 256);
+static size_t vscan_states_bytes(int64_t d, size_t state_bytes = 16) {
+    return align_up((size_t)num_sms() * kVScanMaxBlocksPerSM * 8 * (size_t)d * state_bytes, 256);
 }
 static size_t vscan_direct_ws(int64_t d) { return kWsHeader + 2 * vscan_states_bytes(d); }
 
@@ -514,6 +515,151 @@ template <typename T, int K> struct VScanVjpAff {  // K: 1 mul, 2 min, 3 max
     }
 };
 
+// ---- rows of k equal multi-word elements (tuple scans whose blocks are all
+// lin, all sumOfProd or all 2x2 matrix products): the direct form above over
+// the k element columns of each row, with the element operator's state.  The
+// formulas are the scalar scans' (Sec. 5.3.2-5.3.4 and Fig. 7's general rule
+// for sumOfProd), written per element: x_{i+1} and y_{i-1} are the elements
+// one row after and before (f + d, f - d).
+template <typename E> __device__ __forceinline__ E ld_elem(const E *p) {
+    static_assert(sizeof(E) % 8 == 0 && sizeof(E) <= 32, "8-, 16- or 32-byte elements");
+    E e;
+    if constexpr (sizeof(E) == 8) {
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(p));
+        memcpy(&e, &v, 8);
+    } else {
+        float4 v[sizeof(E) / 16];
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(E) / 16); ++q) v[q] = __ldg(reinterpret_cast<const float4 *>(p) + q);
+        memcpy(&e, v, sizeof(E));
+    }
+    return e;
+}
+template <typename E> __device__ __forceinline__ void st_elem(E *p, const E &e) {
+    if constexpr (sizeof(E) == 8) {
+        float2 v;
+        memcpy(&v, &e, 8);
+        *reinterpret_cast<float2 *>(p) = v;
+    } else {
+        float4 v[sizeof(E) / 16];
+        memcpy(v, &e, sizeof(E));
+#pragma unroll
+        for (int q = 0; q < (int)(sizeof(E) / 16); ++q) reinterpret_cast<float4 *>(p)[q] = v[q];
+    }
+}
+
+template <typename T> struct ElemLin {  // linFnComp: (b, c): x -> b + c x
+    using E = Pair<T>;
+    static __device__ E identity() { return {T(0), T(1)}; }
+    static __device__ E combine(const E &a, const E &b) { return {b.b + b.c * a.b, b.c * a.c}; }
+};
+template <typename T> struct ElemSop {  // sumOfProd (Fig. 8)
+    using E = Pair<T>;
+    static __device__ E identity() { return {T(0), T(0)}; }
+    static __device__ E combine(const E &a, const E &b) { return {a.b + b.b + a.c * b.c, a.c + b.c}; }
+};
+template <typename T> struct ElemMM2 {  // 2x2 matrix product
+    using E = Mat2<T>;
+    static __device__ E identity() { return mat_eye<T>(); }
+    static __device__ E combine(const E &a, const E &b) { return mat_mul(a, b); }
+};
+
+template <typename T, class EO> struct VScanFwdE {
+    using E = typename EO::E;
+    using S = E;
+    struct Aux {};
+    static constexpr bool kRev = false, kHaloChunk = false;
+    const E *__restrict__ x;
+    E *__restrict__ y;
+    int64_t d;
+    __device__ S identity() const { return EO::identity(); }
+    __device__ S combine(const S &a, const S &b) const { return EO::combine(a, b); }
+    __device__ S state(int64_t, int64_t f, Aux &) const { return ld_elem(x + f); }
+    __device__ void store(int64_t f, const S &inc, const Aux &) const { st_elem(y + f, inc); }
+};
+
+// lin vjp: lambda_i = ybar_i + c(x_{i+1}) lambda_i+1 (a 2-vector), xbar_i =
+// (lambda.b, lambda.b b(y_{i-1}) + lambda.c c(y_{i-1})), y_{-1} = (0, 1).
+template <typename T> struct VAffP { T vb, vc, c; };
+template <typename T> struct VScanVjpLinE {
+    using E = Pair<T>;
+    using S = VAffP<T>;
+    struct Aux { E yprev, old; };
+    static constexpr bool kRev = true, kHaloChunk = false;
+    const E *__restrict__ x, *__restrict__ y, *__restrict__ ybar;
+    E *__restrict__ xbar;
+    int64_t n, d;
+    int accumulate;
+    __device__ S identity() const { return {T(0), T(0), T(1)}; }
+    __device__ S combine(const S &acc, const S &e) const {
+        return {e.vb + e.c * acc.vb, e.vc + e.c * acc.vc, e.c * acc.c};
+    }
+    __device__ S state(int64_t i, int64_t f, Aux &a) const {
+        a.old = accumulate ? xbar[f] : E{T(0), T(0)};
+        a.yprev = i > 0 ? ld_elem(y + f - d) : E{T(0), T(1)};
+        const E yb = ld_elem(ybar + f);
+        return {yb.b, yb.c, i + 1 < n ? ld_elem(x + f + d).c : T(1)};
+    }
+    __device__ void store(int64_t f, const S &inc, const Aux &a) const {
+        const T gb = inc.vb, gc = gb * a.yprev.b + inc.vc * a.yprev.c;
+        st_elem(xbar + f, accumulate ? E{a.old.b + gb, a.old.c + gc} : E{gb, gc});
+    }
+};
+
+// sumOfProd vjp by the general rule (unit upper-triangular Jacobians: the
+// composed map is (vp, vs, sig)); xbar_i = (lambda.p, s(y_{i-1}) lambda.p + lambda.s).
+template <typename T> struct VAffU { T vp, vs, sig; };
+template <typename T> struct VScanVjpSopE {
+    using E = Pair<T>;
+    using S = VAffU<T>;
+    struct Aux { T sprev; E old; };
+    static constexpr bool kRev = true, kHaloChunk = false;
+    const E *__restrict__ x, *__restrict__ y, *__restrict__ ybar;
+    E *__restrict__ xbar;
+    int64_t n, d;
+    int accumulate;
+    __device__ S identity() const { return {T(0), T(0), T(0)}; }
+    __device__ S combine(const S &acc, const S &e) const {
+        return {e.vp + acc.vp, e.vs + e.sig * acc.vp + acc.vs, acc.sig + e.sig};
+    }
+    __device__ S state(int64_t i, int64_t f, Aux &a) const {
+        a.old = accumulate ? xbar[f] : E{T(0), T(0)};
+        a.sprev = i > 0 ? ld_elem(y + f - d).c : T(0);
+        const E yb = ld_elem(ybar + f);
+        return {yb.b, yb.c, i + 1 < n ? ld_elem(x + f + d).c : T(0)};
+    }
+    __device__ void store(int64_t f, const S &inc, const Aux &a) const {
+        const T gp = inc.vp, gs = a.sprev * inc.vp + inc.vs;
+        st_elem(xbar + f, accumulate ? E{a.old.b + gp, a.old.c + gs} : E{gp, gs});
+    }
+};
+
+// 2x2 vjp: f_i(L) = Ybar_i + L M_{i+1}^T, Mbar_i = P_{i-1}^T lambda_i, P_{-1} = I.
+template <typename T> struct VAffM { Mat2<T> v, c; };
+template <typename T> struct VScanVjpMM2E {
+    using E = Mat2<T>;
+    using S = VAffM<T>;
+    struct Aux { E yprev, old; };
+    static constexpr bool kRev = true, kHaloChunk = false;
+    const E *__restrict__ x, *__restrict__ y, *__restrict__ ybar;
+    E *__restrict__ xbar;
+    int64_t n, d;
+    int accumulate;
+    __device__ S identity() const { return {mat_zero<T>(), mat_eye<T>()}; }
+    __device__ S combine(const S &acc, const S &e) const {
+        return {mat_add(e.v, mat_mul(acc.v, e.c)), mat_mul(acc.c, e.c)};
+    }
+    __device__ S state(int64_t i, int64_t f, Aux &a) const {
+        a.old = accumulate ? ld_elem(xbar + f) : mat_zero<T>();
+        a.yprev = i > 0 ? ld_elem(y + f - d) : mat_eye<T>();
+        return {ld_elem(ybar + f), i + 1 < n ? mat_t(ld_elem(x + f + d)) : mat_eye<T>()};
+    }
+    __device__ void store(int64_t f, const S &inc, const Aux &a) const {
+        const E g = mat_mul(mat_t(a.yprev), inc.v);
+        st_elem(xbar + f, accumulate ? mat_add(a.old, g) : g);
+    }
+};
+
 // Block b's logical rows [l0, l1): the G blocks split n as evenly as possible.
 __device__ __forceinline__ void vscan_range(int64_t n, int64_t b, int64_t G, int64_t *l0, int64_t *l1) {
     const int64_t per = n / G, extra = n % G;
@@ -856,7 +1002,7 @@ template <class Op, int RP> static adc_status vscan_run(const Op &op, int64_t n,
     using S = typename Op::S;
     if (n == 0) return ADC_OK;
     S *agg = reinterpret_cast<S *>(ws + kWsHeader);
-    S *pre = reinterpret_cast<S *>(ws + kWsHeader + vscan_states_bytes(d));
+    S *pre = reinterpret_cast<S *>(ws + kWsHeader + vscan_states_bytes(d, sizeof(S) > 16 ? sizeof(S) : 16));
     if (d <= kWarp) {
         const int64_t U = vscan_units<Op, RP, true>(n);
         const unsigned blocks = (unsigned)((U + kVScanWarps - 1) / kVScanWarps);
@@ -913,6 +1059,64 @@ adc_status vscan_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *
                                    static_cast<const double *>(ybar), static_cast<double *>(xbar), accumulate, w, s);
     return vscan_vjp_t<float>(op, n, d, static_cast<const float *>(x), static_cast<const float *>(y),
                               static_cast<const float *>(ybar), static_cast<float *>(xbar), accumulate, w, s);
+}
+
+// Rows of d equal lin / sumOfProd / 2x2 elements (the tuple scans' uniform
+// multi-word rows), in the direct form; workspace from velem_ws_bytes.
+size_t velem_ws_bytes(adc_op op, adc_dtype dt, int64_t d) {
+    const size_t s = dt == ADC_F64 ? 8 : 4;
+    const size_t sb = op == ADC_OP_MM2 ? 8 * s : 4 * s;  // the largest state: the vjp's (v, c) / 3 words rounded
+    return kWsHeader + 2 * vscan_states_bytes(d, sb > 16 ? sb : 16);
+}
+template <typename T>
+static adc_status velem_fwd_t(adc_op op, int64_t n, int64_t d, const void *x, void *y, char *ws, cudaStream_t s) {
+    switch (op) {
+    case ADC_OP_LIN:
+        return vscan_run<VScanFwdE<T, ElemLin<T>>, 8>(
+            {static_cast<const Pair<T> *>(x), static_cast<Pair<T> *>(y), d}, n, d, ws, s);
+    case ADC_OP_SOP:
+        return vscan_run<VScanFwdE<T, ElemSop<T>>, 8>(
+            {static_cast<const Pair<T> *>(x), static_cast<Pair<T> *>(y), d}, n, d, ws, s);
+    case ADC_OP_MM2:
+        return vscan_run<VScanFwdE<T, ElemMM2<T>>, 4>(
+            {static_cast<const Mat2<T> *>(x), static_cast<Mat2<T> *>(y), d}, n, d, ws, s);
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+template <typename T>
+static adc_status velem_vjp_t(adc_op op, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
+                              void *xbar, int acc, char *ws, cudaStream_t s) {
+    switch (op) {
+    case ADC_OP_LIN: {
+        using E = Pair<T>;
+        return vscan_run<VScanVjpLinE<T>, 4>({static_cast<const E *>(x), static_cast<const E *>(y),
+                                              static_cast<const E *>(ybar), static_cast<E *>(xbar), n, d, acc},
+                                             n, d, ws, s);
+    }
+    case ADC_OP_SOP: {
+        using E = Pair<T>;
+        return vscan_run<VScanVjpSopE<T>, 4>({static_cast<const E *>(x), static_cast<const E *>(y),
+                                              static_cast<const E *>(ybar), static_cast<E *>(xbar), n, d, acc},
+                                             n, d, ws, s);
+    }
+    case ADC_OP_MM2: {
+        using E = Mat2<T>;
+        return vscan_run<VScanVjpMM2E<T>, 2>({static_cast<const E *>(x), static_cast<const E *>(y),
+                                              static_cast<const E *>(ybar), static_cast<E *>(xbar), n, d, acc},
+                                             n, d, ws, s);
+    }
+    default: return ADC_ERR_UNSUPPORTED;
+    }
+}
+adc_status velem_fwd(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, void *y, void *ws, cudaStream_t s) {
+    char *w = static_cast<char *>(ws);
+    return dt == ADC_F64 ? velem_fwd_t<double>(op, n, d, x, y, w, s) : velem_fwd_t<float>(op, n, d, x, y, w, s);
+}
+adc_status velem_vjp(adc_op op, adc_dtype dt, int64_t n, int64_t d, const void *x, const void *y, const void *ybar,
+                     void *xbar, int accumulate, void *ws, cudaStream_t s) {
+    char *w = static_cast<char *>(ws);
+    return dt == ADC_F64 ? velem_vjp_t<double>(op, n, d, x, y, ybar, xbar, accumulate, w, s)
+                         : velem_vjp_t<float>(op, n, d, x, y, ybar, xbar, accumulate, w, s);
 }
 
 // -------------------------------------------- reduce_by_index, direct form --

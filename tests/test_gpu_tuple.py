@@ -12,11 +12,13 @@ from tests.test_gpu_scan import IDENT, make_x
 
 pytestmark = pytest.mark.gpu
 
-# uniform scalar rows (("add", "add"), ("add",) * 64, ("max",) * 5, ("mul",) * 3)
-# take the vectorised scan's direct form; the others split into planes
+# uniform scalar rows (("add", "add"), ("add",) * 64, ("max",) * 5, ("mul",) * 3) and uniform lin /
+# sumOfProd / 2x2 rows (("sop",) * 3, ("sop",) * 16, ("lin",) * 5, ("mm2",) * 3, and the widest rows
+# the ABI takes, 64 values: ("lin",) * 32, ("mm2",) * 16) take the vectorised scan's direct form; the
+# others split into planes
 MIXES = [("add", "mul", "lin", "sop", "mm2", "min"), ("sop", "sop", "sop"), ("mm3", "max", "lin"), ("lin",),
          ("add", "add"), ("sop",) * 16, ("add",) * 64, ("mm5", "mm5"), ("mul", "mm3"), ("max",) * 5, ("mul",) * 3,
-         ("min",) * 7]
+         ("min",) * 7, ("lin",) * 5, ("mm2",) * 3, ("lin",) * 32, ("mm2",) * 16]
 SIZES = [0, 1, 2, 33, 1025, 4097, 100_003]
 
 
