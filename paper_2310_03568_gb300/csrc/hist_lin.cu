@@ -171,32 +171,38 @@ __device__ __forceinline__ Pair<T> lblock_excl(Pair<T> a, Pair<T> *s_w) {
 }
 
 // One block per bin j: L[j][c], R[j][c], hist[j], A[j] from the row P[j][.].
-// The row goes through shared memory in segments of kRowSeg entries (loads
-// and stores coalesced); within a segment thread t composes its 8 consecutive
-// entries and a block scan gives what lies before (L) or after (R) them.
-constexpr int kRowItems = 8;
-constexpr int kRowSeg = kLThreads * kRowItems;
+// The row goes through shared memory in segments of RI entries per thread
+// (loads and stores coalesced); within a segment thread t composes its RI
+// consecutive entries and a block scan gives what lies before (L) or after
+// (R) them.  A row that fits one segment is loaded once: the reverse pass
+// reuses each thread's entries from registers (fp32 takes 16 entries per
+// thread, so rows of up to 4096 chunks, n <= 16.7M, are one segment).
+template <typename T> constexpr int row_items() { return sizeof(T) == 4 ? 16 : 8; }
 
 template <typename T>
 __global__ void __launch_bounds__(kLThreads)
 k_linh_rows(const Pair<T> *__restrict__ P, const Pair<T> *__restrict__ h0, const int64_t nc,
             Pair<T> *__restrict__ L, Pair<T> *__restrict__ R, Pair<T> *__restrict__ hist, Pair<T> *__restrict__ A) {
-    __shared__ Pair<T> s_seg[kRowSeg];
+    constexpr int RI = row_items<T>();
+    constexpr int SEG = kLThreads * RI;
+    __shared__ Pair<T> s_seg[SEG];
     __shared__ Pair<T> s_w[kLWarps];
     __shared__ Pair<T> s_tot;
     const int tid = threadIdx.x;
     const int64_t j = blockIdx.x;
     const Pair<T> *row = P + j * nc;
+    const bool one = nc <= SEG;  // the whole row in one segment
+    Pair<T> v[RI], agg = lf_id<T>();
     // forward: L = hist0 . the entries before
     Pair<T> carry = h0 ? h0[j] : lf_id<T>();
-    for (int64_t s0 = 0; s0 < nc; s0 += kRowSeg) {
-        const int len = (int)((nc - s0) < kRowSeg ? (nc - s0) : kRowSeg);
+    for (int64_t s0 = 0; s0 < nc; s0 += SEG) {
+        const int len = (int)((nc - s0) < SEG ? (nc - s0) : SEG);
         for (int e = tid; e < len; e += kLThreads) s_seg[e] = row[s0 + e];
         __syncthreads();
-        Pair<T> v[kRowItems], agg = lf_id<T>();
+        agg = lf_id<T>();
 #pragma unroll
-        for (int k = 0; k < kRowItems; ++k) {
-            const int idx = tid * kRowItems + k;
+        for (int k = 0; k < RI; ++k) {
+            const int idx = tid * RI + k;
             v[k] = idx < len ? s_seg[idx] : lf_id<T>();
             agg = lf(agg, v[k]);
         }
@@ -204,8 +210,8 @@ k_linh_rows(const Pair<T> *__restrict__ P, const Pair<T> *__restrict__ h0, const
         if (tid == kLThreads - 1) s_tot = lf(ex, agg);
         Pair<T> run = lf(carry, ex);
 #pragma unroll
-        for (int k = 0; k < kRowItems; ++k) {
-            const int idx = tid * kRowItems + k;
+        for (int k = 0; k < RI; ++k) {
+            const int idx = tid * RI + k;
             if (idx < len) {
                 s_seg[idx] = run;
                 run = lf(run, v[k]);
@@ -219,23 +225,25 @@ k_linh_rows(const Pair<T> *__restrict__ P, const Pair<T> *__restrict__ h0, const
     if (tid == 0) hist[j] = carry;
     // reverse: R = the entries after, from the last segment down
     Pair<T> rcarry = lf_id<T>();
-    for (int64_t s0 = (nc - 1) / kRowSeg * kRowSeg; s0 >= 0; s0 -= kRowSeg) {
-        const int len = (int)((nc - s0) < kRowSeg ? (nc - s0) : kRowSeg);
-        for (int e = tid; e < len; e += kLThreads) s_seg[e] = row[s0 + e];
-        __syncthreads();
-        Pair<T> v[kRowItems], agg = lf_id<T>();
+    for (int64_t s0 = (nc - 1) / SEG * SEG; s0 >= 0; s0 -= SEG) {
+        const int len = (int)((nc - s0) < SEG ? (nc - s0) : SEG);
+        if (!one) {  // a single segment's entries are still in v
+            for (int e = tid; e < len; e += kLThreads) s_seg[e] = row[s0 + e];
+            __syncthreads();
+            agg = lf_id<T>();
 #pragma unroll
-        for (int k = 0; k < kRowItems; ++k) {
-            const int idx = tid * kRowItems + k;
-            v[k] = idx < len ? s_seg[idx] : lf_id<T>();
-            agg = lf(agg, v[k]);
+            for (int k = 0; k < RI; ++k) {
+                const int idx = tid * RI + k;
+                v[k] = idx < len ? s_seg[idx] : lf_id<T>();
+                agg = lf(agg, v[k]);
+            }
         }
         const Pair<T> rex = lblock_excl<T, true>(agg, s_w);  // the later threads' entries
         if (tid == 0) s_tot = lf(agg, rex);
         Pair<T> rrun = lf(rex, rcarry);
 #pragma unroll
-        for (int k = kRowItems - 1; k >= 0; --k) {
-            const int idx = tid * kRowItems + k;
+        for (int k = RI - 1; k >= 0; --k) {
+            const int idx = tid * RI + k;
             if (idx < len) {
                 s_seg[idx] = rrun;
                 rrun = lf(v[k], rrun);

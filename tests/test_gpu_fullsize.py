@@ -11,7 +11,8 @@ fp64 oracle over the whole input (marked slow).
 * the specialised reduces (Sec. 3.2) at n = 1e8, where every block of the
   single-pass reduce folds many tiles and the last-block combine folds one
   partial per block;
-* linFnComp reduce-by-index (Sec. 4.1, Fig. 4) at n = 1e7, m = 1000, with hist0;
+* linFnComp reduce-by-index (Sec. 4.1, Fig. 4) at n = 1e7, m = 1000, with hist0,
+  and with per-bin rows of chunk folds longer than one scan segment;
 * the q x q matrix scans (Sec. 5.3.4) at the bench's sizes, 3x3 at n = 1e7 and
   5x5 at n = 4e6 (thousands of bulk-staged tiles, so the look-back runs over
   many steps), forward and vjp with accumulate.
@@ -146,6 +147,30 @@ def test_hist_lin_full():
     g = np.random.default_rng(160)
     h0 = synth.scan_values(g, "lin", m)
     rtol = rtol_for(np.float32)
+    h, saved = adcomb.hist_fwd("lin", m, dev(k), dev(v), dev(h0))
+    ref = oracle.hist_fwd("lin", m, k, v, h0)
+    pop, _ = bin_stats(k, v[:, 0], m)
+    A, R = lin_bin_scales(k, v, m, h0)
+    assert_tol("hist lin fwd", host(h), ref, pop + 1, A, rtol)
+    vb, h0b = adcomb.hist_vjp("lin", m, dev(k), dev(v), dev(h0), h, saved, dev(hb), want_hist0bar=True)
+    vr, h0r = oracle.hist_vjp("lin", m, k, v, hb, h0)
+    assert_tol("hist lin vjp", host(vb), vr, pop[k] + 1, 3 * A[k] * R[k] * rowabs(hb)[k], rtol)
+    assert_tol("hist lin hist0bar", host(h0b), h0r, pop + 1, 3 * A * R * rowabs(hb), rtol)
+
+
+@pytest.mark.parametrize("dt,n", [(np.float32, 17_000_001), (np.float64, 5_000_003)])
+def test_hist_lin_multi_segment_rows(dt, n):
+    """linFnComp reduce_by_index with more chunk folds per bin than one
+    shared-memory segment of the per-bin row scan holds (fp32: 4151 chunks of
+    4096 elements against 4096 per segment; fp64: 2442 chunks of 2048 against
+    2048), so the row scans carry across segments; m = 97, hist0."""
+    g = np.random.default_rng(161)
+    m = 97
+    rtol = rtol_for(dt)
+    k = g.integers(0, m, n).astype(np.int32)
+    v = synth.scan_values(g, "lin", n, dt)
+    h0 = synth.scan_values(g, "lin", m, dt)
+    hb = synth.normal(g, (m, 2), dt)
     h, saved = adcomb.hist_fwd("lin", m, dev(k), dev(v), dev(h0))
     ref = oracle.hist_fwd("lin", m, k, v, h0)
     pop, _ = bin_stats(k, v[:, 0], m)
