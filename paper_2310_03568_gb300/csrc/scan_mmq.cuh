@@ -9,15 +9,17 @@
 // threads then walk their runs in shared memory (build: the run's state;
 // store: the re-walk from the run's exclusive prefix, the results written in
 // place), and the block copies the results out with consecutive 16-byte
-// stores.  Why: a q x q element is 36 / 100 bytes (fp32), so a thread that
+// stores (the vjp's third input, y, needed only for its last step, follows
+// in finish() into the space its re-walk freed).  Why: a q x q element is
+// 36 / 100 bytes (fp32), so a thread that
 // walks its own run in global memory makes every warp access touch 32
 // different lines, and the loads of a tile are spread over a long dependent
 // walk; a bulk copy puts the whole tile in flight at once and the walks run
 // at shared-memory latency.
 //
 // Geometry: SEG * q * q is odd, so 32 consecutive runs start in 32 distinct
-// banks (conflict-free walks for 4- and 8-byte words); TH is a multiple of 4,
-// so a tile (TH * SEG elements) is a whole number of 16-byte words and every
+// banks (conflict-free walks for 4- and 8-byte words); TH is whole warps (a
+// multiple of 4), so a tile (TH * SEG elements) is whole 16-byte words and every
 // tile starts 16-byte aligned (the API requires 16-byte aligned arrays).
 // Elements outside the array are never read from it: the vjp's x_n (after the
 // last element) and y_{-1} (before the first) are the identity, written into
