@@ -76,6 +76,17 @@ def test_tuple_size_queries(L):
         for k in (2, 16, 64):
             assert L.adc_tscan_workspace_bytes(k, codes(*[op] * k), f32, 1000, 1) == \
                 L.adc_vworkspace_bytes(1, op, f32, 1000, 0, k) > 0
+    # rows of k equal lin (4) / 2x2 (5) / sumOfProd (6) blocks are scanned in place as element
+    # columns: per-column states only, no planes, so the workspace does not grow with n
+    for op, width in ((4, 2), (5, 4), (6, 2)):
+        for k in (2, 16, 64 // width):
+            for dt in (0, 1):
+                small = L.adc_tscan_workspace_bytes(k, codes(*[op] * k), dt, 1000, 1)
+                assert small > 0
+                assert L.adc_tscan_workspace_bytes(k, codes(*[op] * k), dt, 10 ** 7, 1) == small
+    # mixed rows split into planes: their workspace grows with n
+    assert L.adc_tscan_workspace_bytes(2, codes(4, 6), f32, 10 ** 7, 1) > \
+        L.adc_tscan_workspace_bytes(2, codes(4, 6), f32, 1000, 1)
 
 
 def test_tuple_host_validation(L):
