@@ -560,8 +560,9 @@ def run_families(dev, peak):
     """The workloads beside the headline, each timed on its own at full size:
     the small reduce-by-index workload (n = 1e5), the scans (n = 1e8 fp32,
     1e7 fp64), the specialised reduces at 1e8, the 2x2 matrix scan and
-    reduce at 1e7, the 3x3 (1e7) and 5x5 (4e6) matrix scans, and linFnComp
-    reduce-by-index at 1e7 / m = 1000.  Inputs are
+    reduce at 1e7, the 3x3 (1e7) and 5x5 (4e6) matrix scans, linFnComp
+    reduce-by-index at 1e7 / m = 1000, and tuple-scan rows of 16 sumOfProd
+    blocks at 1e7.  Inputs are
     seeded and drawn on the device with the workloads' distributions."""
     import torch
 
@@ -674,6 +675,21 @@ def run_families(dev, peak):
     gen_fam["hist_lin_m1000"] = family_entry(n, f, b, 12 * n, 20 * n, 3 * 8 * n + 8 * n, peak)
     out["general_n1e7"] = gen_fam
     del k, v, vb
+    # tuple scan rows of 16 equal sumOfProd blocks (D = 32 values a row, U(-1, 1)), scanned in place;
+    # a failure here is recorded in the line instead of ending the run
+    try:
+        n = 10_000_000
+        ops16 = ("sop",) * 16
+        x = U((n, 32), -1, 1).contiguous()
+        y = adcomb.tscan_fwd(ops16, x, ws=ws)
+        yb, xb = Nrm(tuple(x.shape)), torch.empty_like(x)
+        f = time_calls(lambda: adcomb.tscan_fwd(ops16, x, y, ws=ws), flush)
+        b = time_calls(lambda: adcomb.tscan_vjp(ops16, x, y, yb, xbar=xb, ws=ws), flush)
+        out["tuple_rows_n1e7"] = {"sop_x16": family_entry(n, f, b, 2 * 32 * 4 * n, 4 * 32 * 4 * n,
+                                                          2 * 32 * 4 * n, peak)}
+        del x, y, yb, xb
+    except Exception as e:  # noqa: BLE001
+        out["tuple_rows_n1e7"] = {"error": f"{type(e).__name__}: {e}"}
     torch.cuda.empty_cache()
     out["timing"] = ("CUDA events on the launching stream around each call, mean of 10 after 3 warm-ups, "
                      "a 256 MB L2 flush before each call; frac of the measured copy bandwidth")
