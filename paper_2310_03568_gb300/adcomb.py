@@ -273,11 +273,16 @@ def debug_set_sel_vjp_form(form):
 
 
 def debug_force_hist_strategy(strategy):
+    """-1 automatic; 0 per-warp, 1 per-block, 3 per-thread shared-memory tables, 2 global atomics,
+    4 partition by bin range, and for lifted fp32 min/max 5 split, 6 cluster, 7 two passes,
+    8 block pairs (see adc_debug_force_hist_strategy)."""
     lib().adc_debug_force_hist_strategy(int(strategy))
 
 
 def debug_set_scan_engine(engine):
-    """0 automatic, 1 per-tile look-back only, 2 range-partitioned wherever it applies."""
+    """0 automatic, 1 per-tile look-back only, 2 range-partitioned wherever it applies, 3 TMA-staged
+    ranges, 4 TMA-staged tiles, 5 ranges with 16 bytes per thread per tile, 6 the bulk-staged matrix
+    segment forms (see adc_debug_set_scan_engine)."""
     lib().adc_debug_set_scan_engine(int(engine))
 
 
